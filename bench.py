@@ -1,0 +1,289 @@
+"""Benchmark: sliced bucket-elimination amplitudes of a 7x7-grid random circuit
+(depth 1+32+1) on GB300.
+
+One step = one amplitude <x|C|0^49>: all 2^p slices (p chosen so every slice's
+largest bucket has at most 2^28 entries) contracted through the C-ABI call
+tnq_contract_sliced and summed in FP64. The JSON line reports
+slice-contractions/s (the metric), time per amplitude, the relative error of
+one slice against the FP64 oracle, the roofline of the fused bucket kernel,
+and the oracle's own speed on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun every rank contracts its own bitstring's amplitude (weak
+scaling, no collective on the data path); rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+CONFIGS = {
+    # name: (rows, cols, cycles, max_bag_log2, min_p, max_p)
+    "7x7_d1+32+1": (7, 7, 32, 28, 0, 40),
+    "6x6_d1+24+1": (6, 6, 24, 24, 4, 8),
+    "4x4_d1+16+1": (4, 4, 16, 0, 0, 0),
+}
+METRIC = "slice-contractions/s & time per amplitude, 7x7 d1+32+1; %roofline; err vs FP64"
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "fallback": True}
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_slice(circ, bits, plan, s):
+    """FP64 oracle value and time of slice s of the plan (test infrastructure, CPU)."""
+    from oracle import oracle
+
+    t0 = time.perf_counter()
+    v = oracle.contract(circ, bits, order=plan.order(), mu=plan.sliced(), slices=(s, s + 1))
+    return v, time.perf_counter() - t0, oracle.num_threads()
+
+
+def run_reference(args, cfg_name):
+    """The FP64 oracle timed on the host cores: each step contracts one slice."""
+    from oracle import oracle
+    from paper_2004_10892_gb300 import inputs, tnq
+
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    rows, cols, cyc, mb, pmin, pmax = CONFIGS[cfg_name]
+    circ = inputs.random_grid_circuit(rows, cols, cyc, 0)
+    bits = inputs.random_bitstring(circ.n_qubits, 0)
+    plan = tnq.Plan(circ, max_bag_log2=mb, min_p=pmin, max_p=pmax)
+    order, mu = plan.order(), plan.sliced()
+    n_sl = plan.info()["n_slices"]
+    oracle.build()
+    for w in range(args.warmup):
+        oracle.contract(circ, bits, order=order, mu=mu, slices=(w % n_sl, w % n_sl + 1))
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        s = (args.warmup + k) % n_sl
+        oracle.contract(circ, bits, order=order, mu=mu, slices=(s, s + 1))
+    dt = time.perf_counter() - t0
+    v = args.steps / dt
+    cores = oracle.num_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "slices/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+        "config": {"workload": f"grid {cfg_name} random circuit, seed 0, p={plan.info()['p']}, one slice per step"},
+        "cpu_baseline": {"value": v, "unit": "slices/s", "cores": cores, "kind": "oracle",
+                         "sample": "one slice of the workload per step (FP64 bucket elimination, OpenMP over entries)"},
+        "e2e": {"value": v, "unit": "slices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="tnq", choices=["tnq", "reference"])
+    ap.add_argument("--config", default="7x7_d1+32+1", choices=sorted(CONFIGS))
+    ap.add_argument("--max-batch", type=int, default=64, help="slices contracted at once")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-profile", action="store_true")
+    args = ap.parse_args()
+
+    if args.impl == "reference":
+        run_reference(args, args.config)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2004_10892_gb300 import build as native_build
+    from paper_2004_10892_gb300 import inputs, tnq
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    native_build.build()
+    rows, cols, cyc, mb, pmin, pmax = CONFIGS[args.config]
+    circ = inputs.random_grid_circuit(rows, cols, cyc, 0)
+    bits = inputs.random_bitstring(circ.n_qubits, rank)
+    t_plan = time.perf_counter()
+    plan = tnq.Plan(circ, max_bag_log2=mb, min_p=pmin, max_p=pmax)
+    t_plan = time.perf_counter() - t_plan
+    info = plan.info()
+    n_sl = info["n_slices"]
+    B = min(args.max_batch, n_sl)
+    ws = torch.empty(plan.workspace_bytes(B), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    L = tnq.lib()
+
+    # warm-up (also captures the CUDA graph)
+    for _ in range(args.warmup):
+        amp = tnq.contract_sliced(plan, bits, workspace=ws, max_batch=B, stream=stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        e0.record(stream)
+        for _ in range(args.steps):
+            amp = tnq.contract_sliced(plan, bits, workspace=ws, max_batch=B, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t0
+        if world > 1:
+            dist.barrier()
+    t_dev = e0.elapsed_time(e1) / 1e3
+    if world > 1:
+        tt = torch.tensor([t_dev, t_wall], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_dev, t_wall = float(tt[0]), float(tt[1])
+    total_slices = args.steps * n_sl * world
+    value = total_slices / t_dev
+    e2e_value = total_slices / t_wall
+    n_batches = (n_sl + B - 1) // B
+    launches = args.steps * n_batches * L.tnq_internal_launches_per_batch(plan.handle)
+
+    # live per-bucket timing of one batch (CUDA events on the launching stream)
+    roof = None
+    peaks = load_peaks()
+    if not args.no_profile and rank == 0:
+        nb = info["n_buckets"] + 64
+        ms = (ctypes.c_float * nb)()
+        by = (ctypes.c_double * nb)()
+        bag = (ctypes.c_int * nb)()
+        n_out, b_out = ctypes.c_int(), ctypes.c_int()
+        import numpy as np
+
+        bb = np.ascontiguousarray(np.array(bits, dtype=np.uint8))
+        L.tnq_internal_profile.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint8), ctypes.c_uint64,
+                                           ctypes.c_uint64, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint32,
+                                           ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
+                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+        rc = L.tnq_internal_profile(plan.handle, bb.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), 0, n_sl,
+                                    ctypes.c_void_p(ws.data_ptr()), ws.numel(), B, ctypes.c_void_p(stream.cuda_stream),
+                                    nb, ms, by, bag, ctypes.byref(n_out), ctypes.byref(b_out))
+        if rc == 0:
+            n = n_out.value
+            tot_ms = sum(ms[i] for i in range(n))
+            tot_by = sum(by[i] for i in range(n))
+            big = [i for i in range(n) if bag[i] >= info["max_bag"] - 6]
+            big_ms = sum(ms[i] for i in big)
+            big_by = sum(by[i] for i in big)
+            achieved = tot_by / (tot_ms / 1e3) / 1e9
+            roof = {"bound": "hbm", "kernel": "k_bucket (fused product + sum-out, all bucket launches of one batch)",
+                    "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                    "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if not peaks.get("fallback") else "fallback",
+                    "launches": n, "batch": b_out.value, "bytes_per_launch": tot_by / n, "ms_per_launch": tot_ms / n,
+                    "big_buckets_gbs": big_by / (big_ms / 1e3) / 1e9 if big_ms > 0 else None,
+                    "big_bucket_time_share": big_ms / tot_ms if tot_ms > 0 else None}
+
+    cpu = None
+    err = None
+    if rank == 0 and not args.no_cpu_baseline:
+        # one slice in FP64 on the host cores: the CPU baseline and the error check
+        ref, t_cpu, cores = oracle_slice(circ, bits, plan, 0)
+        per = tnq.contract_sliced(plan, bits, 0, 1, workspace=ws, max_batch=1, stream=stream)
+        err = abs(per - ref) / abs(ref) if ref != 0 else abs(per)
+        cpu = {"value": 1.0 / t_cpu, "unit": "slices/s", "cores": cores, "kind": "oracle",
+               "sample": "slice 0 of the same 7x7 amplitude (FP64 bucket elimination, OpenMP over entries)"
+               if args.config.startswith("7x7") else f"slice 0 of {args.config}"}
+
+    if rank == 0:
+        h2d = 8 + n_batches * (64 + 8 * ((circ.n_qubits + 31) // 32) * (B + 1))
+        d2h = n_batches * 16
+        line = {
+            "metric": METRIC, "value": value, "unit": "slices/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "config": {"workload": f"grid {args.config} random circuit (seed 0), one amplitude per step per GPU",
+                       "n_qubits": circ.n_qubits, "p": info["p"], "n_slices": n_sl, "tau_full": info["tau_full"],
+                       "tau": info["tau"], "max_bag": info["max_bag"], "batch": B,
+                       "flops_per_slice": info["flops_per_slice"], "bytes_per_slice": info["bytes_per_slice"],
+                       "l2": "inputs larger than L2 (each slice streams GBs)", "plan_s": t_plan},
+            "time_per_amplitude_s": t_dev / args.steps,
+            "rel_err_vs_fp64": err,
+            "amplitude": [amp.real, amp.imag],
+            "e2e": {"value": e2e_value, "unit": "slices/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

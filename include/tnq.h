@@ -1,0 +1,231 @@
+/*
+ * tnq.h -- C-ABI of the GB300 sliced bucket-elimination library.
+ *
+ * The library computes single amplitudes <x|C|0^n> of a quantum circuit C by
+ * contracting its graphical-model tensor network (Section II.A: variables are
+ * vertices, tensors are cliques) with bucket elimination ("one index at a
+ * time", Eq. 2, Section II.A) after fixing a set mu of "parallel" variables to
+ * each of their 2^p values (index fixing, Eq. 4; the amplitude is the sum of
+ * the 2^p sub-results, Eq. 5, Section II.D). mu is chosen on the host by the
+ * greedy mu-treewidth-deletion algorithm (Algorithm 2, Section III) with the
+ * tree-trimming score (Section III.B).
+ *
+ * Conventions that every entry point shares
+ *  - All calls are plain C: no exceptions cross this boundary. Every failing
+ *    call returns a status and leaves a message readable with
+ *    tnq_last_error() (thread-local).
+ *  - The caller owns every buffer it passes. The library copies what it
+ *    keeps; it never frees caller memory.
+ *  - A plan (tnq_plan) is immutable once created and may be shared by threads
+ *    and streams. Its small device tables are uploaded on first use on each
+ *    device and freed by tnq_plan_destroy. The large intermediate tensors live
+ *    in a caller-provided device workspace (tnq_plan_workspace_bytes), so
+ *    concurrent calls on one plan are safe when each has its own workspace.
+ *  - Contraction calls are ordered on the given CUDA stream (NULL = the legacy
+ *    default stream) and synchronise that stream before they return; results
+ *    are FP64 values in host memory.
+ *  - Basis index convention: bit q of a bitstring is qubit q's value; a
+ *    bitstring is passed as n bytes, each 0 or 1.
+ *
+ * Variables. The wire of qubit q is cut into segments by its non-diagonal
+ * single-qubit gates (H, X^1/2, Y^1/2, U1; a CNOT counts as H.CZ.H on its
+ * target). Variable (q, k) is the value on qubit q's wire after k such gates.
+ * Segment 0 is the input (fixed to 0); the last segment of each qubit is the
+ * output (fixed to the bitstring bit). All other variables are free. Diagonal
+ * gates (T, CZ) add tensors on the current variables and create none
+ * (self-loops and cliques of the graphical model, Section II.A).
+ */
+#ifndef TNQ_H_
+#define TNQ_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TNQ_OK = 0,
+  TNQ_EINVAL = 1,       /* bad argument, bad circuit or plan, too-small buffer */
+  TNQ_ENOMEM = 2,       /* host or device allocation failed, workspace too small */
+  TNQ_ECUDA = 3,        /* a CUDA runtime call failed (message has the CUDA error) */
+  TNQ_ETIMEOUT = 4,     /* a bounded device-side wait gave up */
+  TNQ_EUNSUPPORTED = 5  /* feature not available (e.g. no CUDA device) */
+} tnq_status;
+
+/* Gate kinds. Matrices (row = output value, column = input value):
+ *   H      = (1/sqrt2) [[1, 1], [1, -1]]
+ *   X_1_2  = (1/sqrt2) [[1, -i], [-i, 1]]      (R_x(pi/2))
+ *   Y_1_2  = (1/sqrt2) [[1, -1], [1, 1]]       (R_y(pi/2))
+ *   T      = diag(1, e^{i pi/4})
+ *   CZ     = diag(1, 1, 1, -1) on (q0, q1)
+ *   CNOT   = control q0, target q1, built as H(q1) CZ(q0,q1) H(q1)
+ *   U1     = the user's 2x2 matrix m (row-major, (re, im) pairs), always
+ *            treated as non-diagonal. */
+typedef enum {
+  TNQ_H = 0, TNQ_X_1_2 = 1, TNQ_Y_1_2 = 2, TNQ_T = 3, TNQ_CZ = 4, TNQ_CNOT = 5, TNQ_U1 = 6
+} tnq_gate_kind;
+
+typedef struct {
+  int32_t kind;  /* tnq_gate_kind */
+  int32_t q0;    /* qubit (control for CNOT) */
+  int32_t q1;    /* second qubit for CZ / CNOT target, else ignored */
+  int32_t pad_;
+  double m[8];   /* TNQ_U1 only: row-major 2x2, (re, im) pairs */
+} tnq_gate;
+
+typedef enum {
+  TNQ_SLICER_TREE_TRIMMING = 0, /* Section III.B score (default) */
+  TNQ_SLICER_DEGREE = 1,        /* largest degree (Section III.A) */
+  TNQ_SLICER_DIRECT = 2,        /* direct treewidth reduction (Algorithm 3) */
+  TNQ_SLICER_LEARNED = 3        /* learned proposer, tree-trimming fallback */
+} tnq_slicer;
+
+typedef enum {
+  TNQ_PREC_C64 = 0,         /* every bucket in complex64 */
+  TNQ_PREC_SPLIT_BF16 = 1,  /* merged GEMM buckets as 3xBF16 tensor-core GEMMs */
+  TNQ_PREC_SPLIT_TF32 = 2   /* merged GEMM buckets as 3xTF32 tensor-core GEMMs */
+} tnq_precision;
+
+typedef enum {
+  TNQ_ORDER_MIN_FILL = 0,   /* greedy min-fill, ties to min degree, then lowest id */
+  TNQ_ORDER_MIN_DEGREE = 1  /* greedy min-degree, ties to lowest id */
+} tnq_ordering;
+
+typedef struct {
+  int32_t slicer;         /* tnq_slicer */
+  int32_t max_bag_log2;   /* stop slicing once every bag has <= this many variables (0 = no limit) */
+  int32_t min_p;          /* slice at least this many variables */
+  int32_t max_p;          /* slice at most this many variables */
+  uint64_t seed;          /* 0: ties go to the earliest position in the order; else seeded random ties */
+  int32_t precision;      /* tnq_precision */
+  int32_t gemm_min_k_log2;/* merged buckets with K >= 2^this run as GEMMs (0 = library default) */
+  int32_t ordering;       /* tnq_ordering */
+  int32_t td_rebuild;     /* 0: after a deletion drop the vertex from every bag; 1: rebuild the TD from the reduced order */
+} tnq_plan_opts;
+
+typedef struct {
+  int32_t n_qubits;
+  int32_t n_free_vars;     /* free variables before slicing (|U|) */
+  int32_t n_leaf_tensors;  /* gate tensors after fixing input/output wires */
+  int32_t n_buckets;       /* eliminations per slice (|U| - p) */
+  int32_t p;               /* number of sliced variables |mu| */
+  int32_t tau_full;        /* treewidth of the greedy order before slicing (Algorithm 1) */
+  int32_t tau;             /* per-slice treewidth of the reduced order (Algorithm 1 on the reduced graph) */
+  int32_t max_bag;         /* tau + 1: largest bucket has 2^max_bag entries */
+  uint64_t n_slices;       /* 2^p */
+  double flops_per_slice;  /* exact real flops of one slice: sum over buckets 6(k-1)2^r + 2*2^(r-1) */
+  double bytes_per_slice;  /* algorithmic bytes of one slice: every operand read once, every output written once, 8 B per complex64 */
+  double peak_bytes_per_slice; /* largest live intermediate set of one slice (complex64) */
+  double total_flops;      /* 2^p * flops_per_slice */
+  int32_t n_gemm_buckets;  /* merged buckets that run as tensor-core GEMMs */
+  int32_t pad_;
+} tnq_plan_info;
+
+typedef struct tnq_plan tnq_plan;
+
+/* ---- errors ---------------------------------------------------------- */
+const char* tnq_status_string(tnq_status s);
+/* Message of the last failing call on this thread ("" if none). */
+const char* tnq_last_error(void);
+/* Library version string. */
+const char* tnq_version(void);
+/* Fills opts with defaults: tree-trimming, no bag limit, p in [0, 0], c64, min-fill. */
+void tnq_plan_opts_default(tnq_plan_opts* opts);
+
+/* ---- planning (host only; works without a GPU) ------------------------
+ * tnq_plan_from_circuit: builds the circuit's network (Section II.A), a greedy
+ * elimination order, its tree decomposition (Appendix A), slices variables
+ * with the greedy mu-treewidth deletion of Algorithm 2 (score per
+ * opts->slicer) until p >= min_p and (every bag <= max_bag_log2 or p == max_p),
+ * then compiles the bucket program of the reduced order. The plan does not
+ * depend on the bitstring: fixed wires leave the graph whatever their value.
+ * Returns TNQ_EINVAL for qubit indices outside [0, n_qubits), q0 == q1, an
+ * unknown gate kind, n_qubits outside [1, 4096], or bad opts. */
+tnq_status tnq_plan_from_circuit(int32_t n_qubits, const tnq_gate* gates, size_t n_gates,
+                                 const tnq_plan_opts* opts, tnq_plan** out_plan);
+void tnq_plan_destroy(tnq_plan* plan);
+tnq_status tnq_plan_info_get(const tnq_plan* plan, tnq_plan_info* out);
+
+/* Reduced elimination order pi~ as variables (qubit[i], segment[i]), i <
+ * n_buckets, earliest first; and the sliced set mu as (qubit[j], segment[j]),
+ * j < p: bit j of a slice index s is the value of mu_j. Arrays are
+ * caller-owned with room for n_buckets (resp. p) entries. */
+tnq_status tnq_plan_order(const tnq_plan* plan, int32_t* qubit, int32_t* segment);
+tnq_status tnq_plan_sliced(const tnq_plan* plan, int32_t* qubit, int32_t* segment);
+
+/* Per-bucket structure for cost reporting, arrays of n_buckets entries:
+ * bag size r (variables of the bucket's product), k (tensors multiplied),
+ * 1 if the bucket runs as a merged tensor-core GEMM group member. Any pointer may be NULL. */
+tnq_status tnq_plan_buckets(const tnq_plan* plan, int32_t* bag, int32_t* k, int32_t* gemm);
+
+/* ---- contraction (GPU) ------------------------------------------------
+ * Device bytes of workspace that a call with `batch` items at once needs
+ * (batch is rounded up to a power of two). */
+size_t tnq_plan_workspace_bytes(const tnq_plan* plan, uint32_t batch);
+
+/* tnq_contract_sliced: sum over slices s in [slice_begin, slice_end) of the
+ * sliced sub-contraction sigma_s (Eq. 4) of <bits|C|0^n>, i.e. the partial
+ * sum of Eq. 5. [0, n_slices) gives the amplitude.
+ *  bits: host, n_qubits bytes (0/1).
+ *  workspace: device memory of ws_bytes >= tnq_plan_workspace_bytes(plan, 1);
+ *    the call runs as many slices at once as the workspace holds (a power of
+ *    two, at most max_batch if max_batch > 0).
+ *  stream: cudaStream_t or NULL.
+ *  out_amp: host, 2 doubles (re, im): the partial sum in FP64.
+ *  out_slice_amps: host, 2*(slice_end-slice_begin) doubles, or NULL: each sigma_s.
+ * Errors: TNQ_EINVAL (range outside [0, n_slices), bad bits), TNQ_ENOMEM
+ * (workspace too small), TNQ_ECUDA, TNQ_ETIMEOUT. */
+tnq_status tnq_contract_sliced(const tnq_plan* plan, const uint8_t* bits,
+                               uint64_t slice_begin, uint64_t slice_end,
+                               void* workspace, size_t ws_bytes, uint32_t max_batch,
+                               void* stream, double* out_amp, double* out_slice_amps);
+
+/* tnq_amplitudes_batch: amplitudes of many bitstrings of many plans.
+ * Plan i has bitstrings bits_offset[i] .. bits_offset[i+1]-1 (bits_offset has
+ * n_plans+1 entries, bits_offset[0] = 0); bitstring b occupies
+ * bits[b*n_qubits(plan) ...] -- the bytes of all bitstrings packed back to
+ * back, each plan's with its own width. All slices of all bitstrings of a
+ * plan run batched together. out_amps: host, 2 doubles per bitstring. */
+tnq_status tnq_amplitudes_batch(const tnq_plan* const* plans, size_t n_plans,
+                                const uint8_t* bits, const size_t* bits_offset,
+                                void* workspace, size_t ws_bytes, void* stream,
+                                double* out_amps);
+
+/* ---- graph-level planning (host only) ---------------------------------
+ * The paper's graph algorithms on an arbitrary simple graph with vertices
+ * 0..n-1 and edges (edges[2e], edges[2e+1]); self-loops and repeated edges
+ * are ignored. `order` lists every vertex once, earliest first. */
+
+/* Algorithm 1: treewidth of the elimination order (largest neighbourhood met,
+ * starting from 1). out_bag_sizes (n entries, may be NULL) receives |N(u)|+1
+ * for each step: the exponent of that step's cost in Eq. 2. */
+tnq_status tnq_graph_treewidth(int32_t n, size_t n_edges, const int32_t* edges,
+                               const int32_t* order, int32_t* out_tau, int32_t* out_bag_sizes);
+
+/* Greedy elimination order (tnq_ordering). */
+tnq_status tnq_graph_order(int32_t n, size_t n_edges, const int32_t* edges,
+                           int32_t method, int32_t* out_order);
+
+/* Appendix A (Algorithm 4): tree decomposition of the order. Bags are written
+ * as CSR (bag_offsets[nb+1], bag_vertices) with parent[b] (-1 for the root);
+ * only maximal cliques are kept. Capacities: bag_cap bags and vert_cap
+ * entries; *out_nb gets the bag count. TNQ_EINVAL if a capacity is short. */
+tnq_status tnq_graph_tree_decomposition(int32_t n, size_t n_edges, const int32_t* edges,
+                                        const int32_t* order, int32_t bag_cap, int32_t vert_cap,
+                                        int32_t* out_nb, int32_t* bag_offsets,
+                                        int32_t* bag_vertices, int32_t* parent);
+
+/* Algorithm 2: delete m vertices greedily by the score `slicer` (tree-trimming,
+ * degree or direct). out_mu[j] = j-th deleted vertex; out_tau[j] = treewidth
+ * of the reduced order after j+1 deletions (Algorithm 1). */
+tnq_status tnq_graph_greedy_deletion(int32_t n, size_t n_edges, const int32_t* edges,
+                                     const int32_t* order, int32_t m, int32_t slicer,
+                                     uint64_t seed, int32_t td_rebuild,
+                                     int32_t* out_mu, int32_t* out_tau);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TNQ_H_ */

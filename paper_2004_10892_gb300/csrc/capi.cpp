@@ -1,0 +1,271 @@
+// capi.cpp -- host-side C-ABI entry points: errors, planning, plan queries and
+// the graph-level algorithms (Algorithms 1, 2, 4 and the Section III scores).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/tnq.h"
+#include "plan.hpp"
+
+namespace tnq {
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+int learned_propose(void* ctx, const Graph& g, const std::vector<int>& order, const TreeDecomposition& td);
+}  // namespace tnq
+
+using namespace tnq;
+
+#define TNQ_TRY(...)                                         \
+  try {                                                      \
+    __VA_ARGS__                                              \
+  } catch (const std::bad_alloc&) {                          \
+    set_error("host allocation failed");                     \
+    return TNQ_ENOMEM;                                       \
+  } catch (const std::exception& e) {                        \
+    set_error(e.what());                                     \
+    return TNQ_EINVAL;                                       \
+  }
+
+extern "C" {
+
+const char* tnq_status_string(tnq_status s) {
+  switch (s) {
+    case TNQ_OK: return "ok";
+    case TNQ_EINVAL: return "invalid argument";
+    case TNQ_ENOMEM: return "out of memory";
+    case TNQ_ECUDA: return "CUDA error";
+    case TNQ_ETIMEOUT: return "device wait timed out";
+    case TNQ_EUNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+const char* tnq_last_error(void) { return g_last_error.c_str(); }
+
+const char* tnq_version(void) { return "tnq 0.1 (sm_103a)"; }
+
+void tnq_plan_opts_default(tnq_plan_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->slicer = TNQ_SLICER_TREE_TRIMMING;
+  o->max_bag_log2 = 0;
+  o->min_p = 0;
+  o->max_p = 0;
+  o->seed = 0;
+  o->precision = TNQ_PREC_C64;
+  o->gemm_min_k_log2 = 0;
+  o->ordering = TNQ_ORDER_MIN_FILL;
+  o->td_rebuild = 0;
+}
+
+tnq_status tnq_plan_from_circuit(int32_t n_qubits, const tnq_gate* gates, size_t n_gates,
+                                 const tnq_plan_opts* opts, tnq_plan** out_plan) {
+  if (!out_plan) { set_error("out_plan is NULL"); return TNQ_EINVAL; }
+  *out_plan = nullptr;
+  if (!gates && n_gates) { set_error("gates is NULL"); return TNQ_EINVAL; }
+  tnq_plan_opts o;
+  tnq_plan_opts_default(&o);
+  if (opts) o = *opts;
+  if (o.slicer < 0 || o.slicer > TNQ_SLICER_LEARNED || o.min_p < 0 || o.max_p < o.min_p ||
+      o.max_p > 62 || o.max_bag_log2 < 0 || o.max_bag_log2 > 40 || o.precision < 0 ||
+      o.precision > TNQ_PREC_SPLIT_TF32 || o.ordering < 0 || o.ordering > TNQ_ORDER_MIN_DEGREE) {
+    set_error("invalid plan options");
+    return TNQ_EINVAL;
+  }
+  TNQ_TRY({
+    std::unique_ptr<tnq_plan> P(new tnq_plan());
+    P->opts = o;
+    std::vector<GateIn> gi(n_gates);
+    for (size_t i = 0; i < n_gates; ++i) {
+      gi[i].kind = gates[i].kind;
+      gi[i].q0 = gates[i].q0;
+      gi[i].q1 = gates[i].q1;
+      std::memcpy(gi[i].m, gates[i].m, sizeof(gi[i].m));
+    }
+    std::string err = build_network(n_qubits, gi.data(), n_gates, P->net);
+    if (!err.empty()) { set_error(err); return TNQ_EINVAL; }
+    P->graph = network_graph(P->net);
+    P->order_full = greedy_order(P->graph, o.ordering);
+    P->tau_full = treewidth_of_order(P->graph, P->order_full);
+    DeletionResult R = greedy_deletion(P->graph, P->order_full, o.slicer, o.min_p, o.max_p,
+                                       o.max_bag_log2, o.seed, o.td_rebuild != 0,
+                                       o.slicer == TNQ_SLICER_LEARNED ? &learned_propose : nullptr, nullptr);
+    P->mu = R.mu;
+    P->order = R.reduced_order;
+    Graph reduced = P->graph;
+    for (int v : P->mu) delete_vertex(reduced, v);
+    P->tau = treewidth_of_order(reduced, P->order);
+    P->prog = compile_program(P->net, P->order, P->mu);
+    P->amp_scale_log2 = -0.5 * P->net.n_sqrt2;
+    *out_plan = P.release();
+    return TNQ_OK;
+  })
+}
+
+void tnq_plan_destroy(tnq_plan* plan) { delete plan; }
+
+tnq_status tnq_plan_info_get(const tnq_plan* P, tnq_plan_info* out) {
+  if (!P || !out) { set_error("NULL argument"); return TNQ_EINVAL; }
+  std::memset(out, 0, sizeof(*out));
+  out->n_qubits = P->net.n_qubits;
+  out->n_free_vars = (int32_t)P->net.free_vars.size();
+  out->n_leaf_tensors = (int32_t)(P->prog.leaves.size() + P->prog.scalar_leaves.size());
+  out->n_buckets = (int32_t)P->order.size();
+  out->p = (int32_t)P->mu.size();
+  out->tau_full = P->tau_full;
+  out->tau = P->tau;
+  out->max_bag = P->prog.max_bag;
+  out->n_slices = 1ull << P->mu.size();
+  out->flops_per_slice = P->prog.flops_per_slice;
+  out->bytes_per_slice = P->prog.bytes_per_slice;
+  // largest live set of one slice: simulate the bucket sequence
+  {
+    double live = 0, peak = 0;
+    for (int t : P->prog.leaves) live += std::ldexp(8.0, P->prog.tensors[t].rank());
+    peak = live;
+    for (const auto& b : P->prog.buckets) {
+      live += std::ldexp(8.0, P->prog.tensors[b.output].rank());
+      peak = std::max(peak, live);
+      for (int t : b.inputs) live -= std::ldexp(8.0, P->prog.tensors[t].rank());
+    }
+    out->peak_bytes_per_slice = peak;
+  }
+  out->total_flops = std::ldexp(P->prog.flops_per_slice, (int)P->mu.size());
+  out->n_gemm_buckets = 0;
+  return TNQ_OK;
+}
+
+tnq_status tnq_plan_order(const tnq_plan* P, int32_t* qubit, int32_t* segment) {
+  if (!P || !qubit || !segment) { set_error("NULL argument"); return TNQ_EINVAL; }
+  for (size_t i = 0; i < P->order.size(); ++i) {
+    const Var& v = P->net.vars[P->net.free_vars[P->order[i]]];
+    qubit[i] = v.q;
+    segment[i] = v.seg;
+  }
+  return TNQ_OK;
+}
+
+tnq_status tnq_plan_sliced(const tnq_plan* P, int32_t* qubit, int32_t* segment) {
+  if (!P || (!P->mu.empty() && (!qubit || !segment))) { set_error("NULL argument"); return TNQ_EINVAL; }
+  for (size_t j = 0; j < P->mu.size(); ++j) {
+    const Var& v = P->net.vars[P->net.free_vars[P->mu[j]]];
+    qubit[j] = v.q;
+    segment[j] = v.seg;
+  }
+  return TNQ_OK;
+}
+
+tnq_status tnq_plan_buckets(const tnq_plan* P, int32_t* bag, int32_t* k, int32_t* gemm) {
+  if (!P) { set_error("NULL plan"); return TNQ_EINVAL; }
+  // one entry per summing bucket (product-only splits fold into their bucket)
+  size_t i = 0;
+  int extra_k = 0;
+  for (const auto& b : P->prog.buckets) {
+    if (!b.sum) { extra_k += b.k - 1; continue; }
+    if (bag) bag[i] = b.r;
+    if (k) k[i] = b.k + extra_k;
+    if (gemm) gemm[i] = 0;
+    extra_k = 0;
+    ++i;
+  }
+  return TNQ_OK;
+}
+
+// ---- graph-level API ------------------------------------------------------
+static bool read_graph(int32_t n, size_t n_edges, const int32_t* edges, Graph& g) {
+  if (n < 0 || n > (1 << 20) || (n_edges && !edges)) { set_error("bad graph"); return false; }
+  g = Graph(n);
+  for (size_t e = 0; e < n_edges; ++e) {
+    int a = edges[2 * e], b = edges[2 * e + 1];
+    if (a < 0 || a >= n || b < 0 || b >= n) { set_error("edge endpoint out of range"); return false; }
+    g.add_edge(a, b);
+  }
+  return true;
+}
+
+static bool read_order(int32_t n, const int32_t* order, std::vector<int>& out) {
+  if (n && !order) { set_error("order is NULL"); return false; }
+  std::vector<char> seen(n, 0);
+  out.assign(order, order + n);
+  for (int v : out) {
+    if (v < 0 || v >= n || seen[v]) { set_error("order is not a permutation"); return false; }
+    seen[v] = 1;
+  }
+  return true;
+}
+
+tnq_status tnq_graph_treewidth(int32_t n, size_t n_edges, const int32_t* edges, const int32_t* order,
+                               int32_t* out_tau, int32_t* out_bag_sizes) {
+  if (!out_tau) { set_error("out_tau is NULL"); return TNQ_EINVAL; }
+  TNQ_TRY({
+    Graph g;
+    std::vector<int> o;
+    if (!read_graph(n, n_edges, edges, g) || !read_order(n, order, o)) return TNQ_EINVAL;
+    std::vector<int> sizes;
+    *out_tau = treewidth_of_order(g, o, &sizes);
+    if (out_bag_sizes) std::copy(sizes.begin(), sizes.end(), out_bag_sizes);
+    return TNQ_OK;
+  })
+}
+
+tnq_status tnq_graph_order(int32_t n, size_t n_edges, const int32_t* edges, int32_t method,
+                           int32_t* out_order) {
+  if (!out_order || method < 0 || method > 1) { set_error("bad arguments"); return TNQ_EINVAL; }
+  TNQ_TRY({
+    Graph g;
+    if (!read_graph(n, n_edges, edges, g)) return TNQ_EINVAL;
+    auto o = greedy_order(g, method);
+    std::copy(o.begin(), o.end(), out_order);
+    return TNQ_OK;
+  })
+}
+
+tnq_status tnq_graph_tree_decomposition(int32_t n, size_t n_edges, const int32_t* edges,
+                                        const int32_t* order, int32_t bag_cap, int32_t vert_cap,
+                                        int32_t* out_nb, int32_t* bag_offsets, int32_t* bag_vertices,
+                                        int32_t* parent) {
+  if (!out_nb || !bag_offsets || !bag_vertices || !parent) { set_error("NULL output"); return TNQ_EINVAL; }
+  TNQ_TRY({
+    Graph g;
+    std::vector<int> o;
+    if (!read_graph(n, n_edges, edges, g) || !read_order(n, order, o)) return TNQ_EINVAL;
+    TreeDecomposition td = tree_decomposition(g, o);
+    int nb = (int)td.bags.size(), nv = 0;
+    for (auto& b : td.bags) nv += (int)b.size();
+    *out_nb = nb;
+    if (nb > bag_cap || nv > vert_cap) { set_error("tree decomposition capacity too small"); return TNQ_EINVAL; }
+    int off = 0;
+    for (int b = 0; b < nb; ++b) {
+      bag_offsets[b] = off;
+      for (int v : td.bags[b]) bag_vertices[off++] = v;
+      parent[b] = td.parent[b];
+    }
+    bag_offsets[nb] = off;
+    return TNQ_OK;
+  })
+}
+
+tnq_status tnq_graph_greedy_deletion(int32_t n, size_t n_edges, const int32_t* edges, const int32_t* order,
+                                     int32_t m, int32_t slicer, uint64_t seed, int32_t td_rebuild,
+                                     int32_t* out_mu, int32_t* out_tau) {
+  if (m < 0 || m > n || (m && (!out_mu || !out_tau)) || slicer < 0 || slicer > TNQ_SLICER_LEARNED) {
+    set_error("bad arguments");
+    return TNQ_EINVAL;
+  }
+  TNQ_TRY({
+    Graph g;
+    std::vector<int> o;
+    if (!read_graph(n, n_edges, edges, g) || !read_order(n, order, o)) return TNQ_EINVAL;
+    DeletionResult R = greedy_deletion(g, o, slicer, m, m, 0, seed, td_rebuild != 0,
+                                       slicer == TNQ_SLICER_LEARNED ? &learned_propose : nullptr, nullptr);
+    for (size_t j = 0; j < R.mu.size(); ++j) {
+      out_mu[j] = R.mu[j];
+      out_tau[j] = R.tau_after[j];
+    }
+    return TNQ_OK;
+  })
+}
+
+}  // extern "C"

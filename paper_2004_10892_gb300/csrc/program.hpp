@@ -1,0 +1,98 @@
+// program.hpp -- circuit network and compiled bucket program of a plan.
+//
+// Network (Section II.A): variables are wire segments (q, k); a non-diagonal
+// one-qubit gate U adds U[v_new, v_old], a diagonal gate a tensor on the
+// current variable (self-loop), CZ a tensor (-1)^(ab) on two current
+// variables. Input segments are fixed to 0 and output segments to the
+// bitstring; what is left is the free-variable graph the planner orders and
+// slices.
+//
+// Bucket program (Eq. 2): in the reduced order pi~ every tensor joins the
+// bucket of its earliest variable; bucket u multiplies its tensors and sums
+// u out; the result joins the bucket of its earliest remaining variable, or
+// becomes one of the slice's scalar factors when no variable is left.
+#pragma once
+#include <complex>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "graph.hpp"
+
+namespace tnq {
+
+enum VarKind { VAR_FREE = 0, VAR_IN = 1, VAR_OUT = 2, VAR_INOUT = 3 };
+
+struct Var {
+  int q = 0, seg = 0;
+  int kind = VAR_FREE;
+  int free_id = -1;  // index among free variables
+};
+
+// A gate tensor over one or two network variables; entry (a, b) at a + 2b.
+// Non-diagonal gates with a 1/sqrt2 prefactor (H, X^1/2, Y^1/2) are stored
+// multiplied by sqrt2; the plan keeps the count of such factors and applies
+// 2^(-count/2) to the amplitude in FP64.
+struct GateTensor {
+  int nv = 0;
+  int var[2] = {-1, -1};
+  std::complex<float> val[4];
+};
+
+struct Network {
+  int n_qubits = 0;
+  std::vector<Var> vars;
+  std::vector<GateTensor> tensors;
+  std::vector<int> free_vars;  // network var id of each free variable
+  int n_sqrt2 = 0;             // number of 1/sqrt2 factors taken out of gate values
+  std::vector<int> inout_qubits;  // qubits whose input segment is also the output
+};
+
+struct GateIn {
+  int kind, q0, q1;
+  double m[8];
+};
+
+// Returns an empty string on success, else an error message.
+std::string build_network(int n_qubits, const GateIn* gates, size_t n_gates, Network& out);
+
+// Free-variable graph of the network (vertices = free ids).
+Graph network_graph(const Network& net);
+
+constexpr int KMAX = 8;  // most inputs one bucket kernel multiplies
+
+// Tensor of the bucket program: a leaf (gate tensor restricted by the fixed
+// variables) or a bucket result. `vars` are free ids sorted by position in the
+// reduced order: bit i of an entry index is the value of vars[i].
+struct PTensor {
+  std::vector<int> vars;
+  int leaf_gate = -1;   // network tensor index for leaves
+  int producer = -1;    // bucket index for results
+  int consumer = -1;    // bucket index that reads it (-1: a final scalar)
+  bool dep_slice = false, dep_bits = false;
+  int rank() const { return (int)vars.size(); }
+};
+
+struct PBucket {
+  int u = -1;                // eliminated free id (-1: product-only step)
+  bool sum = true;           // false: product of the inputs without summing (splits a wide bucket)
+  std::vector<int> inputs;   // tensor ids
+  int output = -1;           // tensor id
+  int r = 0;                 // variables of the product (bag size)
+  int k = 0;                 // tensors multiplied
+};
+
+struct Program {
+  std::vector<PTensor> tensors;
+  std::vector<PBucket> buckets;
+  std::vector<int> leaves;          // tensor ids of leaves with at least one free variable
+  std::vector<int> scalar_leaves;   // network tensor ids fully fixed (rank 0)
+  std::vector<int> finals;          // tensor ids of rank-0 bucket results
+  double flops_per_slice = 0, bytes_per_slice = 0;
+  int max_bag = 0;
+};
+
+// Compiles the bucket program for the reduced order (free ids) and sliced set.
+Program compile_program(const Network& net, const std::vector<int>& order, const std::vector<int>& mu);
+
+}  // namespace tnq

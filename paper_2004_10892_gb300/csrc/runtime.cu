@@ -1,0 +1,1021 @@
+// runtime.cu -- sm_103a execution of a plan's bucket program.
+//
+// One call contracts many "items" (a slice s of Eq. 4, or a (bitstring,
+// slice) pair) at once: every tensor that depends on the item is stored
+// item-major, tensors that do not are stored once (slice-invariant buckets
+// run once per batch). Per batch the stream runs
+//   leaf init (restrict gate tensors to the item's fixed values, Eq. 4)
+//   -> one fused product + sum-out kernel per bucket (Eq. 2)
+//   -> per-item scalar products and the FP64 sum over slices (Eq. 5),
+// captured once into a CUDA graph and replayed for every batch.
+//
+// Numbers: tensors are complex64. Every bucket result carries a per-item
+// power-of-two exponent e (value = stored * 2^e) and the float bits of its
+// largest |re| or |im| (atomicMax in the producing kernel); a consumer scales
+// each input by an exact 2^-m so that inputs enter every product with
+// magnitude below 1, which keeps 2^-n/2-sized amplitudes far from underflow.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/tnq.h"
+#include "plan.hpp"
+
+namespace tnq {
+
+constexpr int GMAX = 52;  // index bits of one bucket launch (output bits + item bits)
+constexpr int TPB = 256;  // threads per block of the bucket kernel
+constexpr int MAX_ITEM_BITS = 16;
+
+// ---------------------------------------------------------------------------
+// device-side records
+struct KParams {
+  float2* out;
+  const float2* in[KMAX];
+  long long stride[KMAX][GMAX];  // element stride of each index bit, per input
+  int in_meta[KMAX];             // meta row of input j, -1 for leaves (unit scale)
+  int in_dep[KMAX];              // 1: input meta is per item
+  int out_meta;
+  int out_bits;                  // output variables per item
+  int G;                         // out_bits + item bits
+  int sum;                       // 1: sum over bit 0 of every input (Eq. 2); 0: product only
+  int B;                         // meta row length
+  int* meta_e;
+  unsigned* meta_m;
+};
+
+struct LeafDev {
+  float2 val[4];      // gate entries, (a, b) at a + 2b
+  int nv;             // gate variables (1 or 2)
+  int vkind[2];       // 0 free, 1 fixed to 0 (input wire), 2 output bit, 3 sliced
+  int varg[2];        // free: bit in the leaf; output: qubit; sliced: j
+  int n_free;         // leaf rank
+  int dep;            // item-dependent in this configuration
+  long long off;      // element offset in the arena
+};
+
+struct FinalDev {
+  long long off;
+  int meta;
+  int dep;
+};
+
+// Batch header, rewritten before every batch.
+struct BatchHdr {
+  unsigned long long item_base;  // global item index of item 0
+  unsigned long long item_end;   // one past the last valid global item
+  unsigned long long bstr_base;  // global bitstring index of bitstring row 0
+  int mode;                      // 0: item = slice of bitstring 0; 1: item = (bitstring << p) | slice
+  int p;
+  int n_words;                   // 32-bit words per bitstring
+  int pad;
+};
+
+__device__ __forceinline__ void item_decode(const BatchHdr& h, int item, unsigned long long* slice, int* brow,
+                                            bool* valid) {
+  unsigned long long gi = h.item_base + (unsigned long long)item;
+  *valid = gi < h.item_end;
+  if (!*valid) gi = h.item_base;  // padding items recompute a valid item; results are dropped
+  if (h.mode == 0) {
+    *slice = gi;
+    *brow = 0;
+  } else {
+    *slice = h.p ? (gi & ((1ull << h.p) - 1ull)) : 0ull;
+    *brow = (int)((gi >> h.p) - h.bstr_base);
+  }
+}
+
+__device__ __forceinline__ int bit_of(const unsigned* bits, int n_words, int brow, int q) {
+  return (bits[(size_t)brow * n_words + (q >> 5)] >> (q & 31)) & 1u;
+}
+
+// K5: restrict every gate tensor to the item's fixed values (input 0, output
+// bits, sliced values: Eq. 4).
+__global__ void k_leaf_init(const LeafDev* __restrict__ leaves, int n_leaves, const BatchHdr* __restrict__ hdr_p,
+                            const unsigned* __restrict__ bits, float2* __restrict__ arena, int B) {
+  const BatchHdr h = *hdr_p;
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)n_leaves * B) return;
+  const int li = (int)(idx / B), item = (int)(idx % B);
+  const LeafDev L = leaves[li];
+  if (!L.dep && item) return;
+  unsigned long long slice;
+  int brow;
+  bool valid;
+  item_decode(h, item, &slice, &brow, &valid);
+  float2* out = arena + L.off + (L.dep ? ((long long)item << L.n_free) : 0ll);
+  for (int e = 0; e < (1 << L.n_free); ++e) {
+    int a[2] = {0, 0};
+    for (int x = 0; x < L.nv; ++x) {
+      switch (L.vkind[x]) {
+        case 0: a[x] = (e >> L.varg[x]) & 1; break;
+        case 1: a[x] = 0; break;
+        case 2: a[x] = bit_of(bits, h.n_words, brow, L.varg[x]); break;
+        default: a[x] = (int)((slice >> L.varg[x]) & 1ull); break;
+      }
+    }
+    out[e] = L.val[a[0] + 2 * a[1]];
+  }
+}
+
+// Product of the fully fixed gate tensors and the <x_q|0> factors of wires
+// without a non-diagonal gate, per item (FP64).
+__global__ void k_scalar_init(const LeafDev* __restrict__ sl, int n_sl, const int* __restrict__ inout_q, int n_inout,
+                              const BatchHdr* __restrict__ hdr_p, const unsigned* __restrict__ bits,
+                              double2* __restrict__ item_scalar, int B) {
+  const BatchHdr h = *hdr_p;
+  int item = blockIdx.x * blockDim.x + threadIdx.x;
+  if (item >= B) return;
+  unsigned long long slice;
+  int brow;
+  bool valid;
+  item_decode(h, item, &slice, &brow, &valid);
+  double re = 1.0, im = 0.0;
+  for (int i = 0; i < n_sl; ++i) {
+    const LeafDev L = sl[i];
+    int a[2] = {0, 0};
+    for (int x = 0; x < L.nv; ++x) {
+      if (L.vkind[x] == 2) a[x] = bit_of(bits, h.n_words, brow, L.varg[x]);
+      else if (L.vkind[x] == 3) a[x] = (int)((slice >> L.varg[x]) & 1ull);
+    }
+    const float2 v = L.val[a[0] + 2 * a[1]];
+    const double nr = re * v.x - im * v.y, ni = re * v.y + im * v.x;
+    re = nr;
+    im = ni;
+  }
+  for (int i = 0; i < n_inout; ++i)
+    if (bit_of(bits, h.n_words, brow, inout_q[i])) re = im = 0.0;
+  item_scalar[item] = make_double2(re, im);
+}
+
+// Scale 2^-m that brings a tensor whose largest |re|,|im| has float bits
+// `mbits` into [0.5, 1); m is returned through *mexp.
+__device__ __forceinline__ float scale_of_max(unsigned mbits, int* mexp) {
+  if (mbits == 0u) {
+    *mexp = 0;
+    return 1.f;
+  }
+  int ex = (int)((mbits >> 23) & 0xffu);
+  if (ex == 0) ex = 1;
+  int m = ex - 126;
+  if (m > 126) m = 126;
+  *mexp = m;
+  return __int_as_float((127 - m) << 23);
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__device__ __forceinline__ void atomic_max_pos(unsigned* p, float v) {
+  const unsigned b = __float_as_uint(v);
+  if (b > *reinterpret_cast<volatile unsigned*>(p)) atomicMax(p, b);
+}
+
+// K1: one bucket, all items. Element g of the launch = item * 2^out_bits + b'
+// of the output; input j's entry for (b', u=0) is at sum_i bit_i(g) * stride[j][i]
+// (u=1 is the next element, since u is every input's bit 0). A block covers
+// 2^LT consecutive g: bits >= 8 of g go through a shared table per input, bits
+// < 8 through a per-thread offset, so each element costs one add per input.
+template <int NIN, int LT>
+__global__ void __launch_bounds__(TPB) k_bucket(const __grid_constant__ KParams P) {
+  constexpr int ITER = (LT > 8) ? (1 << (LT - 8)) : 1;
+  __shared__ long long sh_off[NIN][ITER];
+  __shared__ float sh_red[TPB / 32];
+  const int t = threadIdx.x;
+  const long long g0 = (long long)blockIdx.x << LT;
+  const long long total = 1ll << P.G;
+
+  for (int e = t; e < NIN * ITER; e += TPB) {
+    const int j = e / ITER, it = e - (e / ITER) * ITER;
+    const long long gi = g0 + ((long long)it << 8);
+    long long acc = 0;
+    for (int i = 8; i < P.G; ++i)
+      if ((gi >> i) & 1ll) acc += P.stride[j][i];
+    sh_off[j][it] = acc;
+  }
+  long long tp[NIN];
+#pragma unroll
+  for (int j = 0; j < NIN; ++j) {
+    long long a = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      if (i < P.G && ((t >> i) & 1)) a += P.stride[j][i];
+    tp[j] = a;
+  }
+  __syncthreads();
+
+  const int ob = P.out_bits;
+  const bool uniform = (ob >= LT) || (P.G == ob);
+  float f[NIN];
+  int esum = 0;
+  auto load_scales = [&](long long item) {
+    esum = 0;
+#pragma unroll
+    for (int j = 0; j < NIN; ++j) {
+      if (P.in_meta[j] < 0) {
+        f[j] = 1.f;
+      } else {
+        const long long row = (long long)P.in_meta[j] * P.B + (P.in_dep[j] ? item : 0ll);
+        int m;
+        f[j] = scale_of_max(P.meta_m[row], &m);
+        esum += P.meta_e[row] + m;
+      }
+    }
+  };
+  if (uniform) load_scales(g0 >> ob);
+
+  const long long omask = (1ll << ob) - 1ll;
+  const int lane = t & 31;
+  float tmax = 0.f;
+#pragma unroll 2
+  for (int it = 0; it < ITER; ++it) {
+    const long long g = g0 + t + ((long long)it << 8);
+    const bool valid = g < total;
+    const long long item = g >> ob;
+    float m = 0.f;
+    if (valid) {
+      if (!uniform) load_scales(item);
+      float2 r;
+      if (P.sum) {
+        float2 a0 = make_float2(1.f, 0.f), a1 = make_float2(1.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < NIN; ++j) {
+          const long long idx = sh_off[j][it] + tp[j];
+          float4 v = __ldg(reinterpret_cast<const float4*>(P.in[j] + idx));
+          const float2 x0 = make_float2(v.x * f[j], v.y * f[j]);
+          const float2 x1 = make_float2(v.z * f[j], v.w * f[j]);
+          if (j == 0) {
+            a0 = x0;
+            a1 = x1;
+          } else {
+            a0 = cmul(a0, x0);
+            a1 = cmul(a1, x1);
+          }
+        }
+        r = make_float2(a0.x + a1.x, a0.y + a1.y);
+      } else {
+        float2 a = make_float2(1.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < NIN; ++j) {
+          const long long idx = sh_off[j][it] + tp[j];
+          const float2 v = __ldg(P.in[j] + idx);
+          const float2 x = make_float2(v.x * f[j], v.y * f[j]);
+          a = (j == 0) ? x : cmul(a, x);
+        }
+        r = a;
+      }
+      P.out[g] = r;
+      m = fmaxf(fabsf(r.x), fabsf(r.y));
+      if ((g & omask) == 0) P.meta_e[(long long)P.out_meta * P.B + item] = esum;
+    }
+    if (uniform) {
+      tmax = fmaxf(tmax, m);
+    } else {
+      // items change every 2^ob elements: reduce within aligned lane groups
+      for (int off = 1; off < 32 && off < (1 << min(ob, 5)); off <<= 1)
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+      const int grp = 1 << min(ob, 5);
+      if (valid && (lane & (grp - 1)) == 0 && m > 0.f)
+        atomic_max_pos(&P.meta_m[(long long)P.out_meta * P.B + item], m);
+    }
+  }
+  if (uniform) {
+    for (int off = 16; off > 0; off >>= 1) tmax = fmaxf(tmax, __shfl_xor_sync(0xffffffffu, tmax, off));
+    if (lane == 0) sh_red[t >> 5] = tmax;
+    __syncthreads();
+    if (t == 0) {
+      float b = 0.f;
+      for (int w = 0; w < TPB / 32; ++w) b = fmaxf(b, sh_red[w]);
+      if (b > 0.f && g0 < total) atomic_max_pos(&P.meta_m[(long long)P.out_meta * P.B + (g0 >> ob)], b);
+    }
+  }
+}
+
+// K4: amplitude of every item = scalar leaves * final scalars * 2^(exponents),
+// then the FP64 sum of each bitstring's items of this batch in item order.
+__global__ void k_finalize(const FinalDev* __restrict__ fin, int n_fin, const double2* __restrict__ item_scalar,
+                           const float2* __restrict__ arena, const int* __restrict__ meta_e, int B,
+                           const BatchHdr* __restrict__ hdr_p, int scale_exp, int scale_half,
+                           double2* __restrict__ res) {
+  const BatchHdr h = *hdr_p;
+  int item = blockIdx.x * blockDim.x + threadIdx.x;
+  if (item >= B) return;
+  unsigned long long slice;
+  int brow;
+  bool valid;
+  item_decode(h, item, &slice, &brow, &valid);
+  double re = item_scalar[item].x, im = item_scalar[item].y;
+  int e = scale_exp;
+  for (int i = 0; i < n_fin; ++i) {
+    const FinalDev F = fin[i];
+    const float2 v = arena[F.off + (F.dep ? item : 0)];
+    const double nr = re * v.x - im * v.y, ni = re * v.y + im * v.x;
+    re = nr;
+    im = ni;
+    e += meta_e[(long long)F.meta * B + (F.dep ? item : 0)];
+  }
+  if (scale_half) {
+    re *= 0.70710678118654752440;
+    im *= 0.70710678118654752440;
+  }
+  res[item] = valid ? make_double2(ldexp(re, e), ldexp(im, e)) : make_double2(0.0, 0.0);
+}
+
+// Per-bitstring FP64 partial sums of one batch, items in increasing order.
+__global__ void k_slice_sum(const double2* __restrict__ res, int B, const BatchHdr* __restrict__ hdr_p,
+                            double2* __restrict__ part, int n_rows) {
+  const BatchHdr h = *hdr_p;
+  int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= n_rows) return;
+  double re = 0.0, im = 0.0;
+  for (int item = 0; item < B; ++item) {
+    unsigned long long slice;
+    int brow;
+    bool valid;
+    item_decode(h, item, &slice, &brow, &valid);
+    if (valid && brow == row) {
+      re += res[item].x;
+      im += res[item].y;
+    }
+  }
+  part[row] = make_double2(re, im);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+#define CU(call)                                                                  \
+  do {                                                                            \
+    cudaError_t err_ = (call);                                                    \
+    if (err_ != cudaSuccess) {                                                    \
+      set_error(std::string(#call) + ": " + cudaGetErrorString(err_));           \
+      return TNQ_ECUDA;                                                           \
+    }                                                                             \
+  } while (0)
+
+namespace {
+
+// Where every tensor of one configuration lives.
+struct Layout {
+  int mode = 0, B = 1, item_bits = 0;
+  std::vector<long long> off;   // element offset per tensor
+  std::vector<char> dep;        // item-dependent per tensor
+  long long arena_elems = 0;
+  size_t hdr_off = 0, bits_off = 0, scalar_off = 0, res_off = 0, part_off = 0, meta_e_off = 0, meta_m_off = 0,
+         arena_off = 0, total = 0;
+  int n_words = 1, n_rows = 1;
+};
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+bool tensor_dep(const PTensor& t, int mode) { return t.dep_slice || (mode == 1 && t.dep_bits); }
+
+Layout make_layout(const tnq_plan& P, int mode, int B) {
+  const Program& prog = P.prog;
+  Layout L;
+  L.mode = mode;
+  L.B = B;
+  while ((1 << L.item_bits) < B) ++L.item_bits;
+  const int T = (int)prog.tensors.size();
+  L.off.assign(T, 0);
+  L.dep.assign(T, 0);
+  for (int t = 0; t < T; ++t) L.dep[t] = tensor_dep(prog.tensors[t], mode);
+  // lifetimes in bucket steps
+  const int nb = (int)prog.buckets.size();
+  std::vector<int> lo(T), hi(T);
+  std::vector<long long> size(T);
+  for (int t = 0; t < T; ++t) {
+    const PTensor& x = prog.tensors[t];
+    lo[t] = x.producer;  // leaves: -1
+    hi[t] = x.consumer >= 0 ? x.consumer : nb;
+    size[t] = (long long)align_up(((size_t)1 << x.rank()) * (L.dep[t] ? (size_t)B : 1), 32);
+  }
+  std::vector<int> idx(T);
+  for (int t = 0; t < T; ++t) idx[t] = t;
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return size[a] > size[b]; });
+  std::vector<int> placed;
+  for (int t : idx) {
+    // lowest offset not overlapping a placed tensor with an intersecting lifetime
+    std::vector<std::pair<long long, long long>> busy;
+    for (int o : placed)
+      if (lo[o] <= hi[t] && lo[t] <= hi[o]) busy.push_back({L.off[o], L.off[o] + size[o]});
+    std::sort(busy.begin(), busy.end());
+    long long cand = 0;
+    for (auto& iv : busy) {
+      if (cand + size[t] <= iv.first) break;
+      cand = std::max(cand, iv.second);
+    }
+    L.off[t] = cand;
+    L.arena_elems = std::max(L.arena_elems, cand + size[t]);
+    placed.push_back(t);
+  }
+  L.n_words = (P.net.n_qubits + 31) / 32;
+  L.n_rows = B + 1;
+  size_t o = 0;
+  L.hdr_off = o; o = align_up(o + sizeof(BatchHdr), 256);
+  L.bits_off = o; o = align_up(o + (size_t)L.n_rows * L.n_words * 4, 256);
+  L.scalar_off = o; o = align_up(o + (size_t)B * 16, 256);
+  L.res_off = o; o = align_up(o + (size_t)B * 16, 256);
+  L.part_off = o; o = align_up(o + (size_t)L.n_rows * 16, 256);
+  L.meta_e_off = o; o = align_up(o + (size_t)T * B * 4, 256);
+  L.meta_m_off = o; o = align_up(o + (size_t)T * B * 4, 256);
+  L.arena_off = o; o = align_up(o + (size_t)L.arena_elems * 8, 256);
+  L.total = o;
+  return L;
+}
+
+}  // namespace
+
+// Per-device state of a plan: uploaded tables and captured graphs.
+struct ExecConfig {
+  Layout L;
+  LeafDev* d_leaves = nullptr;
+  int n_leaves = 0;
+  LeafDev* d_scalars = nullptr;
+  int n_scalars = 0;
+  int* d_inout = nullptr;
+  int n_inout = 0;
+  FinalDev* d_finals = nullptr;
+  int n_finals = 0;
+  std::vector<KParams> kp;           // per bucket (pointers filled per workspace)
+  std::vector<std::pair<int, int>> kshape;  // (n_in, LT) per bucket
+  void* ws = nullptr;                // workspace the graph was captured for
+  cudaGraphExec_t exec = nullptr;
+};
+
+struct DeviceState {
+  int device = -1;
+  std::map<std::pair<int, int>, ExecConfig*> configs;  // (mode, B)
+  ~DeviceState() {
+    for (auto& kv : configs) {
+      ExecConfig* c = kv.second;
+      if (c->exec) cudaGraphExecDestroy(c->exec);
+      cudaFree(c->d_leaves);
+      cudaFree(c->d_scalars);
+      cudaFree(c->d_inout);
+      cudaFree(c->d_finals);
+      delete c;
+    }
+  }
+};
+
+void destroy_device_state(DeviceState* s) { delete s; }
+
+static LeafDev make_leafdev(const tnq_plan& P, const PTensor* pt, int gate, const Layout* L, int tid) {
+  const GateTensor& gt = P.net.tensors[gate];
+  LeafDev d;
+  std::memset(&d, 0, sizeof(d));
+  for (int i = 0; i < 4; ++i) d.val[i] = make_float2(gt.val[i].real(), gt.val[i].imag());
+  d.nv = gt.nv;
+  d.n_free = pt ? pt->rank() : 0;
+  std::vector<int> mu_index(P.net.free_vars.size(), -1);
+  for (size_t j = 0; j < P.mu.size(); ++j) mu_index[P.mu[j]] = (int)j;
+  for (int x = 0; x < gt.nv; ++x) {
+    const Var& v = P.net.vars[gt.var[x]];
+    if (v.kind == VAR_IN || v.kind == VAR_INOUT) {
+      d.vkind[x] = 1;
+    } else if (v.kind == VAR_OUT) {
+      d.vkind[x] = 2;
+      d.varg[x] = v.q;
+    } else if (mu_index[v.free_id] >= 0) {
+      d.vkind[x] = 3;
+      d.varg[x] = mu_index[v.free_id];
+    } else {
+      d.vkind[x] = 0;
+      d.varg[x] = (int)(std::find(pt->vars.begin(), pt->vars.end(), v.free_id) - pt->vars.begin());
+    }
+  }
+  if (L) {
+    d.dep = L->dep[tid];
+    d.off = L->off[tid];
+  }
+  return d;
+}
+
+// Bucket kernel parameters of one configuration, with pointers holding byte
+// offsets from the arena base (rebased per call). Host only.
+static bool build_kparams(const tnq_plan& P, const Layout& L, std::vector<KParams>& kp,
+                          std::vector<std::pair<int, int>>& kshape) {
+  const Program& prog = P.prog;
+  kp.clear();
+  kshape.clear();
+  for (const PBucket& b : prog.buckets) {
+    KParams k;
+    std::memset(&k, 0, sizeof(k));
+    const PTensor& o = prog.tensors[b.output];
+    const bool odep = L.dep[b.output];
+    k.out_bits = o.rank();
+    k.G = k.out_bits + (odep ? L.item_bits : 0);
+    if (k.G >= GMAX || b.k > KMAX) {
+      set_error("bucket too large for one launch");
+      return false;
+    }
+    k.sum = b.sum ? 1 : 0;
+    k.B = L.B;
+    k.out_meta = b.output;
+    k.out = reinterpret_cast<float2*>((size_t)L.off[b.output] * 8);
+    for (int j = 0; j < b.k; ++j) {
+      const int tid = b.inputs[j];
+      const PTensor& x = prog.tensors[tid];
+      k.in[j] = reinterpret_cast<const float2*>((size_t)L.off[tid] * 8);
+      k.in_meta[j] = x.leaf_gate >= 0 ? -1 : tid;
+      k.in_dep[j] = L.dep[tid];
+      for (int i = 0; i < k.out_bits; ++i) {
+        auto it = std::find(x.vars.begin(), x.vars.end(), o.vars[i]);
+        k.stride[j][i] = it == x.vars.end() ? 0 : (1ll << (it - x.vars.begin()));
+      }
+      for (int i = k.out_bits; i < k.G; ++i) k.stride[j][i] = L.dep[tid] ? ((1ll << x.rank()) << (i - k.out_bits)) : 0;
+    }
+    kp.push_back(k);
+    kshape.push_back({b.k, k.G > 8 ? 12 : 8});
+  }
+  return true;
+}
+
+// Host-side bounds check of every launch of configuration (mode, B): each
+// input's largest index stays inside its tensor, each output fits its
+// allocation, every tensor fits the arena and tensors live at the same time
+// do not overlap. Returns an empty string when everything holds.
+static std::string validate_config(const tnq_plan& P, int mode, int B) {
+  const Layout L = make_layout(P, mode, B);
+  std::vector<KParams> kp;
+  std::vector<std::pair<int, int>> ks;
+  if (!build_kparams(P, L, kp, ks)) return "build_kparams failed";
+  const Program& prog = P.prog;
+  auto alloc = [&](int t) { return ((long long)1 << prog.tensors[t].rank()) * (L.dep[t] ? B : 1); };
+  for (size_t bi = 0; bi < prog.buckets.size(); ++bi) {
+    const PBucket& b = prog.buckets[bi];
+    const KParams& k = kp[bi];
+    if ((1ll << k.G) > alloc(b.output)) return "bucket " + std::to_string(bi) + ": output overflows";
+    for (int j = 0; j < b.k; ++j) {
+      long long mx = 0;
+      for (int i = 0; i < k.G; ++i) mx += k.stride[j][i];
+      if (k.sum) mx += 1;
+      if (mx >= alloc(b.inputs[j])) return "bucket " + std::to_string(bi) + ": input " + std::to_string(j) + " overflows";
+      if (k.sum && (((size_t)k.in[j] / 8) & 1)) return "unaligned input";
+      for (int i = 0; i < k.G; ++i)
+        if (k.sum && (k.stride[j][i] & 1)) return "odd stride in a summing bucket";
+    }
+  }
+  const int T = (int)prog.tensors.size();
+  const int nb = (int)prog.buckets.size();
+  for (int t = 0; t < T; ++t) {
+    if (L.off[t] < 0 || L.off[t] + alloc(t) > L.arena_elems) return "tensor outside arena";
+    if (L.off[t] % 32) return "tensor offset not 256-byte aligned";
+  }
+  for (int a = 0; a < T; ++a)
+    for (int c = a + 1; c < T; ++c) {
+      const PTensor &x = prog.tensors[a], &y = prog.tensors[c];
+      const int la = x.producer, ha = x.consumer >= 0 ? x.consumer : nb;
+      const int lc = y.producer, hc = y.consumer >= 0 ? y.consumer : nb;
+      if (la <= hc && lc <= ha && L.off[a] < L.off[c] + alloc(c) && L.off[c] < L.off[a] + alloc(a))
+        return "live tensors " + std::to_string(a) + " and " + std::to_string(c) + " overlap";
+    }
+  return "";
+}
+
+static tnq_status build_config(const tnq_plan& P, int mode, int B, ExecConfig** out) {
+  ExecConfig* C = new ExecConfig();
+  C->L = make_layout(P, mode, B);
+  const Program& prog = P.prog;
+  std::vector<LeafDev> leaves, scalars;
+  for (int t : prog.leaves) leaves.push_back(make_leafdev(P, &prog.tensors[t], prog.tensors[t].leaf_gate, &C->L, t));
+  for (int g : prog.scalar_leaves) scalars.push_back(make_leafdev(P, nullptr, g, nullptr, -1));
+  std::vector<FinalDev> finals;
+  for (int t : prog.finals) finals.push_back(FinalDev{C->L.off[t], t, (int)C->L.dep[t]});
+  C->n_leaves = (int)leaves.size();
+  C->n_scalars = (int)scalars.size();
+  C->n_finals = (int)finals.size();
+  C->n_inout = (int)P.net.inout_qubits.size();
+  auto up = [](void** dst, const void* src, size_t bytes) -> cudaError_t {
+    cudaError_t e = cudaMalloc(dst, bytes ? bytes : 16);
+    if (e != cudaSuccess) return e;
+    return bytes ? cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice) : cudaSuccess;
+  };
+  cudaError_t e;
+  if ((e = up((void**)&C->d_leaves, leaves.data(), leaves.size() * sizeof(LeafDev))) != cudaSuccess ||
+      (e = up((void**)&C->d_scalars, scalars.data(), scalars.size() * sizeof(LeafDev))) != cudaSuccess ||
+      (e = up((void**)&C->d_inout, P.net.inout_qubits.data(), P.net.inout_qubits.size() * sizeof(int))) !=
+          cudaSuccess ||
+      (e = up((void**)&C->d_finals, finals.data(), finals.size() * sizeof(FinalDev))) != cudaSuccess) {
+    set_error(std::string("uploading plan tables: ") + cudaGetErrorString(e));
+    cudaFree(C->d_leaves);
+    cudaFree(C->d_scalars);
+    cudaFree(C->d_inout);
+    cudaFree(C->d_finals);
+    delete C;
+    return TNQ_ECUDA;
+  }
+  if (!build_kparams(P, C->L, C->kp, C->kshape)) {
+    cudaFree(C->d_leaves);
+    cudaFree(C->d_scalars);
+    cudaFree(C->d_inout);
+    cudaFree(C->d_finals);
+    delete C;
+    return TNQ_EUNSUPPORTED;
+  }
+  *out = C;
+  return TNQ_OK;
+}
+
+template <int NIN>
+static void launch_bucket_n(const KParams& k, int LT, cudaStream_t s) {
+  const long long total = 1ll << k.G;
+  if (LT == 8) {
+    k_bucket<NIN, 8><<<(unsigned)std::max(1ll, total >> 8), TPB, 0, s>>>(k);
+  } else {
+    k_bucket<NIN, 12><<<(unsigned)std::max(1ll, (total + 4095) >> 12), TPB, 0, s>>>(k);
+  }
+}
+
+static void launch_bucket(const KParams& k, int n_in, int LT, cudaStream_t s) {
+  switch (n_in) {
+    case 1: launch_bucket_n<1>(k, LT, s); break;
+    case 2: launch_bucket_n<2>(k, LT, s); break;
+    case 3: launch_bucket_n<3>(k, LT, s); break;
+    case 4: launch_bucket_n<4>(k, LT, s); break;
+    case 5: launch_bucket_n<5>(k, LT, s); break;
+    case 6: launch_bucket_n<6>(k, LT, s); break;
+    case 7: launch_bucket_n<7>(k, LT, s); break;
+    default: launch_bucket_n<8>(k, LT, s); break;
+  }
+}
+
+// Enqueues one batch (everything after the header upload) on stream s.
+static void enqueue_batch(const tnq_plan& P, ExecConfig& C, char* ws, cudaStream_t s) {
+  const Layout& L = C.L;
+  const int B = L.B;
+  const int T = (int)P.prog.tensors.size();
+  auto* hdr = reinterpret_cast<const BatchHdr*>(ws + L.hdr_off);
+  auto* bits = reinterpret_cast<const unsigned*>(ws + L.bits_off);
+  auto* scal = reinterpret_cast<double2*>(ws + L.scalar_off);
+  auto* res = reinterpret_cast<double2*>(ws + L.res_off);
+  auto* part = reinterpret_cast<double2*>(ws + L.part_off);
+  auto* me = reinterpret_cast<int*>(ws + L.meta_e_off);
+  auto* mm = reinterpret_cast<unsigned*>(ws + L.meta_m_off);
+  auto* arena = reinterpret_cast<float2*>(ws + L.arena_off);
+  cudaMemsetAsync(mm, 0, (size_t)T * B * 4, s);
+  if (C.n_leaves) {
+    long long n = (long long)C.n_leaves * B;
+    k_leaf_init<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(C.d_leaves, C.n_leaves, hdr, bits, arena, B);
+  }
+  k_scalar_init<<<(B + 127) / 128, 128, 0, s>>>(C.d_scalars, C.n_scalars, C.d_inout, C.n_inout, hdr, bits, scal, B);
+  for (size_t i = 0; i < C.kp.size(); ++i) {
+    KParams k = C.kp[i];
+    k.out = reinterpret_cast<float2*>(reinterpret_cast<char*>(arena) + reinterpret_cast<size_t>(k.out));
+    for (int j = 0; j < C.kshape[i].first; ++j)
+      k.in[j] = reinterpret_cast<const float2*>(reinterpret_cast<const char*>(arena) + reinterpret_cast<size_t>(k.in[j]));
+    k.meta_e = me;
+    k.meta_m = mm;
+    launch_bucket(k, C.kshape[i].first, C.kshape[i].second, s);
+  }
+  const double sc = P.amp_scale_log2;  // = -n_sqrt2 / 2
+  const int n_sqrt2 = (int)std::lround(-2.0 * sc);
+  const int scale_exp = -(n_sqrt2 / 2), scale_half = n_sqrt2 & 1;
+  k_finalize<<<(B + 127) / 128, 128, 0, s>>>(C.d_finals, C.n_finals, scal, arena, me, B, hdr, scale_exp, scale_half,
+                                              res);
+  k_slice_sum<<<(L.n_rows + 127) / 128, 128, 0, s>>>(res, B, hdr, part, L.n_rows);
+}
+
+static bool use_graphs() {
+  const char* e = getenv("TNQ_NO_GRAPH");
+  return !(e && e[0] == '1');
+}
+
+// Runs the batch: header upload, then the captured graph (or direct launches).
+static tnq_status run_batch(const tnq_plan& P, ExecConfig& C, char* ws, cudaStream_t s, const BatchHdr& h) {
+  CU(cudaMemcpyAsync(ws + C.L.hdr_off, &h, sizeof(h), cudaMemcpyHostToDevice, s));
+  if (!use_graphs()) {
+    enqueue_batch(P, C, ws, s);
+    CU(cudaGetLastError());
+    return TNQ_OK;
+  }
+  if (C.exec && C.ws != ws) {
+    cudaGraphExecDestroy(C.exec);
+    C.exec = nullptr;
+  }
+  if (!C.exec) {
+    cudaStream_t cap;
+    CU(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      enqueue_batch(P, C, ws, cap);
+      e = cudaStreamEndCapture(cap, &g);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&C.exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cap);
+    if (e != cudaSuccess) {
+      C.exec = nullptr;
+      set_error(std::string("graph capture: ") + cudaGetErrorString(e));
+      return TNQ_ECUDA;
+    }
+    C.ws = ws;
+  }
+  CU(cudaGraphLaunch(C.exec, s));
+  return TNQ_OK;
+}
+
+static int ilog2_floor(uint64_t x) {
+  int b = 0;
+  while ((2ull << b) <= x) ++b;
+  return b;
+}
+
+static tnq_status get_config(const tnq_plan& P, int mode, int B, ExecConfig** out) {
+  int dev;
+  CU(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(P.dev_mu);
+  if (P.dev && P.dev->device != dev) {
+    set_error("plan already bound to another CUDA device");
+    return TNQ_EINVAL;
+  }
+  if (!P.dev) {
+    P.dev = new DeviceState();
+    P.dev->device = dev;
+  }
+  auto key = std::make_pair(mode, B);
+  auto it = P.dev->configs.find(key);
+  if (it != P.dev->configs.end()) {
+    *out = it->second;
+    return TNQ_OK;
+  }
+  ExecConfig* C = nullptr;
+  tnq_status st = build_config(P, mode, B, &C);
+  if (st != TNQ_OK) return st;
+  P.dev->configs[key] = C;
+  *out = C;
+  return TNQ_OK;
+}
+
+static tnq_status check_device() {
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess || n == 0) {
+    set_error(std::string("no CUDA device: ") + cudaGetErrorString(e));
+    return TNQ_EUNSUPPORTED;
+  }
+  return TNQ_OK;
+}
+
+// Workspace bytes of configuration (mode, B), cached per plan.
+static size_t layout_bytes(const tnq_plan& P, int mode, int B) {
+  {
+    std::lock_guard<std::mutex> lk(P.layout_mu);
+    auto it = P.layout_bytes.find({mode, B});
+    if (it != P.layout_bytes.end()) return it->second;
+  }
+  const size_t b = make_layout(P, mode, B).total;
+  std::lock_guard<std::mutex> lk(P.layout_mu);
+  P.layout_bytes[{mode, B}] = b;
+  return b;
+}
+
+// Largest power-of-two batch (<= cap) whose workspace fits.
+static int pick_batch(const tnq_plan& P, int mode, size_t ws_bytes, uint64_t cap) {
+  int best = 0;
+  for (int b = 0; b <= MAX_ITEM_BITS; ++b) {
+    const uint64_t B = 1ull << b;
+    if (B > cap && b > 0) break;
+    if (layout_bytes(P, mode, (int)B) <= ws_bytes) best = (int)B;
+    else break;
+  }
+  return best;
+}
+
+static void pack_bits(const uint8_t* bits, int n, std::vector<unsigned>& out) {
+  for (int q = 0; q < n; ++q)
+    if (bits[q]) out[q >> 5] |= 1u << (q & 31);
+}
+
+}  // namespace tnq
+
+using namespace tnq;
+
+extern "C" {
+
+// Internal test hook (not in include/tnq.h): host-side bounds check of the
+// launches of configuration (mode, batch). Returns 0 and "" when they hold.
+int tnq_internal_validate(const tnq_plan* plan, int mode, uint32_t batch, char* msg, size_t msg_len) {
+  std::string m = plan ? validate_config(*plan, mode, (int)batch) : std::string("NULL plan");
+  if (msg && msg_len) {
+    std::strncpy(msg, m.c_str(), msg_len - 1);
+    msg[msg_len - 1] = 0;
+  }
+  return m.empty() ? 0 : 1;
+}
+
+// Internal measurement hook (not in include/tnq.h): runs the first batch of
+// tnq_contract_sliced(plan, bits, s0, s1, ...) with direct launches and a
+// CUDA event pair around every bucket launch on `stream`. Per bucket it
+// returns the launch time (ms), the algorithmic bytes of the launch (every
+// operand read once, the output written once; 8 B per complex64) and the bag
+// size r. *out_n = number of bucket launches, *out_B = batch used.
+int tnq_internal_profile(const tnq_plan* plan, const uint8_t* bits, uint64_t s0, uint64_t s1, void* workspace,
+                         size_t ws_bytes, uint32_t max_batch, void* stream, int cap, float* ms, double* bytes,
+                         int* bag, int* out_n, int* out_B) {
+  if (!plan || !bits || !workspace || s1 <= s0 || s1 > (1ull << plan->mu.size())) return TNQ_EINVAL;
+  tnq_status st = check_device();
+  if (st != TNQ_OK) return st;
+  uint64_t cap_b = 1;
+  while (cap_b < s1 - s0 && cap_b < (1ull << MAX_ITEM_BITS)) cap_b <<= 1;
+  if (max_batch > 0) cap_b = std::min<uint64_t>(cap_b, 1ull << ilog2_floor(max_batch));
+  const int B = pick_batch(*plan, 0, ws_bytes, cap_b);
+  if (B == 0) return TNQ_ENOMEM;
+  ExecConfig* C = nullptr;
+  if ((st = get_config(*plan, 0, B, &C)) != TNQ_OK) return st;
+  const int nbk = (int)C->kp.size();
+  if (cap < nbk) return TNQ_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  char* ws = reinterpret_cast<char*>(workspace);
+  std::vector<unsigned> words((size_t)C->L.n_words * C->L.n_rows, 0u);
+  pack_bits(bits, plan->net.n_qubits, words);
+  CU(cudaMemcpyAsync(ws + C->L.bits_off, words.data(), words.size() * 4, cudaMemcpyHostToDevice, s));
+  BatchHdr h;
+  std::memset(&h, 0, sizeof(h));
+  h.item_base = s0;
+  h.item_end = s1;
+  h.p = (int)plan->mu.size();
+  h.n_words = C->L.n_words;
+  CU(cudaMemcpyAsync(ws + C->L.hdr_off, &h, sizeof(h), cudaMemcpyHostToDevice, s));
+  const Layout& L = C->L;
+  const int T = (int)plan->prog.tensors.size();
+  auto* hdr = reinterpret_cast<const BatchHdr*>(ws + L.hdr_off);
+  auto* bw = reinterpret_cast<const unsigned*>(ws + L.bits_off);
+  auto* arena = reinterpret_cast<float2*>(ws + L.arena_off);
+  auto* me = reinterpret_cast<int*>(ws + L.meta_e_off);
+  auto* mm = reinterpret_cast<unsigned*>(ws + L.meta_m_off);
+  CU(cudaMemsetAsync(mm, 0, (size_t)T * B * 4, s));
+  if (C->n_leaves) {
+    long long n = (long long)C->n_leaves * B;
+    k_leaf_init<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(C->d_leaves, C->n_leaves, hdr, bw, arena, B);
+  }
+  std::vector<cudaEvent_t> ev(2 * (size_t)nbk);
+  for (auto& e : ev) CU(cudaEventCreate(&e));
+  for (int i = 0; i < nbk; ++i) {
+    KParams k = C->kp[i];
+    k.out = reinterpret_cast<float2*>(reinterpret_cast<char*>(arena) + reinterpret_cast<size_t>(k.out));
+    for (int j = 0; j < C->kshape[i].first; ++j)
+      k.in[j] = reinterpret_cast<const float2*>(reinterpret_cast<const char*>(arena) + reinterpret_cast<size_t>(k.in[j]));
+    k.meta_e = me;
+    k.meta_m = mm;
+    CU(cudaEventRecord(ev[2 * i], s));
+    launch_bucket(k, C->kshape[i].first, C->kshape[i].second, s);
+    CU(cudaEventRecord(ev[2 * i + 1], s));
+  }
+  CU(cudaGetLastError());
+  CU(cudaStreamSynchronize(s));
+  const Program& prog = plan->prog;
+  for (int i = 0; i < nbk; ++i) {
+    float t = 0;
+    CU(cudaEventElapsedTime(&t, ev[2 * i], ev[2 * i + 1]));
+    const PBucket& b = prog.buckets[i];
+    double by = std::ldexp(8.0, prog.tensors[b.output].rank()) * (L.dep[b.output] ? B : 1);
+    for (int tid : b.inputs) by += std::ldexp(8.0, prog.tensors[tid].rank()) * (L.dep[tid] ? B : 1);
+    ms[i] = t;
+    bytes[i] = by;
+    bag[i] = b.r;
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  *out_n = nbk;
+  *out_B = B;
+  return TNQ_OK;
+}
+
+// Internal: kernel launches of one batch of configuration (mode, batch).
+int tnq_internal_launches_per_batch(const tnq_plan* plan) {
+  return plan ? (int)plan->prog.buckets.size() + 4 : 0;
+}
+
+size_t tnq_plan_workspace_bytes(const tnq_plan* plan, uint32_t batch) {
+  if (!plan) return 0;
+  uint32_t B = 1;
+  while (B < batch && B < (1u << MAX_ITEM_BITS)) B <<= 1;
+  return std::max(layout_bytes(*plan, 0, (int)B), layout_bytes(*plan, 1, (int)B));
+}
+
+tnq_status tnq_contract_sliced(const tnq_plan* plan, const uint8_t* bits, uint64_t slice_begin, uint64_t slice_end,
+                               void* workspace, size_t ws_bytes, uint32_t max_batch, void* stream, double* out_amp,
+                               double* out_slice_amps) {
+  if (!plan || !bits || !out_amp) { set_error("NULL argument"); return TNQ_EINVAL; }
+  const uint64_t n_slices = 1ull << plan->mu.size();
+  if (slice_begin > slice_end || slice_end > n_slices) { set_error("slice range outside [0, n_slices)"); return TNQ_EINVAL; }
+  for (int q = 0; q < plan->net.n_qubits; ++q)
+    if (bits[q] > 1) { set_error("bitstring bytes must be 0 or 1"); return TNQ_EINVAL; }
+  out_amp[0] = out_amp[1] = 0.0;
+  if (slice_begin == slice_end) return TNQ_OK;
+  tnq_status st = check_device();
+  if (st != TNQ_OK) return st;
+  if (!workspace) { set_error("workspace is NULL"); return TNQ_EINVAL; }
+  const uint64_t n_items = slice_end - slice_begin;
+  uint64_t cap = 1;
+  while (cap < n_items && cap < (1ull << MAX_ITEM_BITS)) cap <<= 1;
+  if (max_batch > 0) cap = std::min<uint64_t>(cap, 1ull << ilog2_floor(max_batch));
+  const int B = pick_batch(*plan, 0, ws_bytes, cap);
+  if (B == 0) { set_error("workspace too small for one slice"); return TNQ_ENOMEM; }
+  ExecConfig* C = nullptr;
+  if ((st = get_config(*plan, 0, B, &C)) != TNQ_OK) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  char* ws = reinterpret_cast<char*>(workspace);
+  std::vector<unsigned> words((size_t)C->L.n_words * C->L.n_rows, 0u);
+  pack_bits(bits, plan->net.n_qubits, words);
+  CU(cudaMemcpyAsync(ws + C->L.bits_off, words.data(), words.size() * 4, cudaMemcpyHostToDevice, s));
+  std::vector<double> res(2 * (size_t)B), part(2);
+  double sre = 0, sim = 0;
+  std::lock_guard<std::mutex> lk(plan->dev_mu);  // one capture/launch sequence per plan at a time
+  for (uint64_t base = slice_begin; base < slice_end; base += B) {
+    BatchHdr h;
+    std::memset(&h, 0, sizeof(h));
+    h.item_base = base;
+    h.item_end = slice_end;
+    h.mode = 0;
+    h.p = (int)plan->mu.size();
+    h.n_words = C->L.n_words;
+    if ((st = run_batch(*plan, *C, ws, s, h)) != TNQ_OK) return st;
+    CU(cudaMemcpyAsync(part.data(), ws + C->L.part_off, 16, cudaMemcpyDeviceToHost, s));
+    if (out_slice_amps)
+      CU(cudaMemcpyAsync(res.data(), ws + C->L.res_off, 16 * (size_t)B, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    sre += part[0];
+    sim += part[1];
+    if (out_slice_amps) {
+      const uint64_t nv = std::min<uint64_t>(B, slice_end - base);
+      std::memcpy(out_slice_amps + 2 * (base - slice_begin), res.data(), 16 * nv);
+    }
+  }
+  out_amp[0] = sre;
+  out_amp[1] = sim;
+  return TNQ_OK;
+}
+
+tnq_status tnq_amplitudes_batch(const tnq_plan* const* plans, size_t n_plans, const uint8_t* bits,
+                                const size_t* bits_offset, void* workspace, size_t ws_bytes, void* stream,
+                                double* out_amps) {
+  if ((n_plans && (!plans || !bits || !bits_offset || !out_amps))) { set_error("NULL argument"); return TNQ_EINVAL; }
+  if (n_plans == 0) return TNQ_OK;
+  if (bits_offset[0] != 0) { set_error("bits_offset[0] must be 0"); return TNQ_EINVAL; }
+  for (size_t i = 0; i < n_plans; ++i)
+    if (!plans[i] || bits_offset[i + 1] < bits_offset[i]) { set_error("bad plan or bits_offset"); return TNQ_EINVAL; }
+  tnq_status st = check_device();
+  if (st != TNQ_OK) return st;
+  if (!workspace) { set_error("workspace is NULL"); return TNQ_EINVAL; }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  char* ws = reinterpret_cast<char*>(workspace);
+  size_t byte_pos = 0;
+  for (size_t pi = 0; pi < n_plans; ++pi) {
+    const tnq_plan& P = *plans[pi];
+    const int n = P.net.n_qubits;
+    const size_t nb = bits_offset[pi + 1] - bits_offset[pi];
+    const uint8_t* pb = bits + byte_pos;
+    byte_pos += nb * (size_t)n;
+    for (size_t i = 0; i < nb * (size_t)n; ++i)
+      if (pb[i] > 1) { set_error("bitstring bytes must be 0 or 1"); return TNQ_EINVAL; }
+    if (nb == 0) continue;
+    const int p = (int)P.mu.size();
+    const uint64_t n_items = (uint64_t)nb << p;
+    uint64_t cap = 1;
+    while (cap < n_items && cap < (1ull << MAX_ITEM_BITS)) cap <<= 1;
+    const int B = pick_batch(P, 1, ws_bytes, cap);
+    if (B == 0) { set_error("workspace too small for one item"); return TNQ_ENOMEM; }
+    ExecConfig* C = nullptr;
+    if ((st = get_config(P, 1, B, &C)) != TNQ_OK) return st;
+    std::vector<double> part(2 * (size_t)C->L.n_rows);
+    std::vector<double> acc(2 * nb, 0.0);
+    std::lock_guard<std::mutex> lk(P.dev_mu);
+    for (uint64_t base = 0; base < n_items; base += B) {
+      const uint64_t end = std::min<uint64_t>(n_items, base + B);
+      const uint64_t b0 = base >> p, b1 = (end - 1) >> p;  // bitstrings touched by this batch
+      std::vector<unsigned> words((size_t)C->L.n_words * C->L.n_rows, 0u);
+      for (uint64_t b = b0; b <= b1; ++b)
+        for (int q = 0; q < n; ++q)
+          if (pb[b * n + q]) words[(size_t)(b - b0) * C->L.n_words + (q >> 5)] |= 1u << (q & 31);
+      CU(cudaMemcpyAsync(ws + C->L.bits_off, words.data(), words.size() * 4, cudaMemcpyHostToDevice, s));
+      BatchHdr h;
+      std::memset(&h, 0, sizeof(h));
+      h.item_base = base;
+      h.item_end = n_items;
+      h.bstr_base = b0;
+      h.mode = 1;
+      h.p = p;
+      h.n_words = C->L.n_words;
+      if ((st = run_batch(P, *C, ws, s, h)) != TNQ_OK) return st;
+      CU(cudaMemcpyAsync(part.data(), ws + C->L.part_off, 16 * (size_t)C->L.n_rows, cudaMemcpyDeviceToHost, s));
+      CU(cudaStreamSynchronize(s));
+      for (uint64_t b = b0; b <= b1; ++b) {
+        acc[2 * b] += part[2 * (b - b0)];
+        acc[2 * b + 1] += part[2 * (b - b0) + 1];
+      }
+    }
+    std::memcpy(out_amps + 2 * bits_offset[pi], acc.data(), 16 * nb);
+  }
+  return TNQ_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,117 @@
+"""The C-ABI library loads and exports every symbol include/tnq.h declares;
+error paths work without a GPU (no compute calls)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2004_10892_gb300 import inputs as I
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", h)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"\b(tnq_[a-z0-9_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(tnq_lib):
+    names = declared_functions()
+    assert len(names) >= 15
+    L = ctypes.CDLL(tnq_lib.LIB_PATH)
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_header(tnq_lib):
+    assert set(declared_functions()) <= set(tnq_lib.SIGNATURES)
+
+
+def test_status_strings(tnq_lib):
+    L = tnq_lib.lib()
+    for s in range(6):
+        assert L.tnq_status_string(s)
+    assert b"sm_103a" in L.tnq_version()
+
+
+def test_null_arguments_are_rejected(tnq_lib):
+    L = tnq_lib.lib()
+    assert L.tnq_plan_from_circuit(1, None, 0, None, None) == tnq_lib.EINVAL
+    assert L.tnq_plan_info_get(None, None) == tnq_lib.EINVAL
+    assert b"NULL" in L.tnq_last_error()
+    out = (ctypes.c_double * 2)()
+    assert L.tnq_contract_sliced(None, None, 0, 1, None, 0, 0, None, out, None) == tnq_lib.EINVAL
+
+
+def test_bad_slice_range_and_bits(tnq_lib):
+    import numpy as np
+
+    plan = tnq_lib.Plan(I.random_grid_circuit(3, 3, 8, 0), min_p=2, max_p=2)
+    L = tnq_lib.lib()
+    bits = np.zeros(9, np.uint8)
+    out = np.zeros(2)
+    P = ctypes.POINTER
+    rc = L.tnq_contract_sliced(plan.handle, bits.ctypes.data_as(P(ctypes.c_uint8)), 0, 5, None, 0, 0, None,
+                               out.ctypes.data_as(P(ctypes.c_double)), None)
+    assert rc == tnq_lib.EINVAL and b"slice range" in L.tnq_last_error()
+    bits[3] = 2
+    rc = L.tnq_contract_sliced(plan.handle, bits.ctypes.data_as(P(ctypes.c_uint8)), 0, 4, None, 0, 0, None,
+                               out.ctypes.data_as(P(ctypes.c_double)), None)
+    assert rc == tnq_lib.EINVAL
+
+
+def test_empty_slice_range_is_zero(tnq_lib):
+    import numpy as np
+
+    plan = tnq_lib.Plan(I.random_grid_circuit(3, 3, 8, 0), min_p=2, max_p=2)
+    L = tnq_lib.lib()
+    bits = np.zeros(9, np.uint8)
+    out = np.ones(2)
+    P = ctypes.POINTER
+    rc = L.tnq_contract_sliced(plan.handle, bits.ctypes.data_as(P(ctypes.c_uint8)), 2, 2, None, 0, 0, None,
+                               out.ctypes.data_as(P(ctypes.c_double)), None)
+    assert rc == tnq_lib.OK and out[0] == 0 and out[1] == 0
+
+
+def test_contract_without_gpu_fails_loudly(tnq_lib):
+    import numpy as np
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    plan = tnq_lib.Plan(I.random_grid_circuit(3, 3, 8, 0))
+    L = tnq_lib.lib()
+    bits = np.zeros(9, np.uint8)
+    out = np.zeros(2)
+    P = ctypes.POINTER
+    rc = L.tnq_contract_sliced(plan.handle, bits.ctypes.data_as(P(ctypes.c_uint8)), 0, 1, None, 0, 0, None,
+                               out.ctypes.data_as(P(ctypes.c_double)), None)
+    assert rc == tnq_lib.EUNSUPPORTED
+
+
+def test_workspace_grows_with_batch(tnq_lib):
+    plan = tnq_lib.Plan(I.random_grid_circuit(5, 5, 16, 0), min_p=3, max_p=3)
+    sizes = [plan.workspace_bytes(b) for b in (1, 2, 4, 8)]
+    assert all(b >= a for a, b in zip(sizes, sizes[1:])) and sizes[0] > 0
+    assert plan.workspace_bytes(3) == plan.workspace_bytes(4)
+
+
+def test_launch_bounds_hold_on_host(tnq_lib):
+    """Every bucket launch's largest index stays inside its tensor, in every
+    configuration the contraction calls can pick (host-side check)."""
+    L = tnq_lib.lib()
+    f = L.tnq_internal_validate
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32, ctypes.c_char_p, ctypes.c_size_t]
+    buf = ctypes.create_string_buffer(256)
+    for c, kw in [(I.random_grid_circuit(4, 4, 16, 0), {}), (I.random_grid_circuit(5, 5, 20, 1), dict(min_p=3, max_p=3)),
+                  (I.ghz(5), {}), (I.all_h(3), {}), (I.random_small_circuit(9, 90, 2), dict(min_p=2, max_p=2))]:
+        plan = tnq_lib.Plan(c, **kw)
+        for mode in (0, 1):
+            for B in (1, 2, 8, 64, 1024):
+                assert f(plan.handle, mode, B, buf, 256) == 0, (c.name, mode, B, buf.value)

@@ -1,0 +1,204 @@
+"""GPU parity: the CUDA path through the C-ABI against the FP64 oracle.
+
+Tolerance: the complex64 path must match the oracle within 1e-5 relative.
+The denominator is |a_ref| when |a_ref|^2 >= 2^-n / 10, else 2^-n/2 (an
+amplitude far below the Porter-Thomas scale is compared on that scale).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2004_10892_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+def rel_err(a, ref, n):
+    floor = 2.0 ** (-n / 2)
+    den = abs(ref) if abs(ref) ** 2 >= floor ** 2 / 10 else floor
+    return abs(a - ref) / den
+
+
+def bits_of(x, n):
+    return [(x >> q) & 1 for q in range(n)]
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_4x4_zero_amplitude(cuda, tnq_lib, oracle_lib, seed):
+    """4x4 grid, depth 1+16+1, p = 0: <0^16|C|0^16> vs the oracle and the state vector."""
+    circ = I.random_grid_circuit(4, 4, 16, seed)
+    plan = tnq_lib.Plan(circ)
+    assert plan.info()["p"] == 0
+    zero = [0] * 16
+    amp = tnq_lib.contract_sliced(plan, zero)
+    ref = oracle_lib.contract(circ, zero, order=plan.order(), mu=plan.sliced())
+    assert rel_err(amp, ref, 16) < TOL, (amp, ref)
+    if seed < 2:
+        sv = oracle_lib.statevector(circ)
+        assert rel_err(amp, sv[0], 16) < TOL
+
+
+def test_4x4_full_distribution(cuda, tnq_lib, oracle_lib):
+    """All 2^16 amplitudes in one batched call vs the brute-force state vector; norm 1."""
+    circ = I.random_grid_circuit(4, 4, 16, 0)
+    plan = tnq_lib.Plan(circ)
+    sv = oracle_lib.statevector(circ)
+    allbits = [bits_of(x, 16) for x in range(1 << 16)]
+    amps = tnq_lib.amplitudes_batch([plan], [allbits])
+    floor = 2.0 ** -8
+    assert np.max(np.abs(amps - sv)) / floor < TOL
+    assert abs(np.sum(np.abs(amps) ** 2) - 1.0) < 1e-5
+
+
+@pytest.mark.parametrize("p", [4, 6, 8])
+def test_6x6_sliced_per_slice(cuda, tnq_lib, oracle_lib, p):
+    """6x6 grid, depth 1+24+1, p = 4..8: every slice value vs the oracle's."""
+    circ = I.random_grid_circuit(6, 6, 24, 0)
+    bits = I.random_bitstring(36, 0)
+    plan = tnq_lib.Plan(circ, max_bag_log2=24, min_p=p, max_p=p)
+    inf = plan.info()
+    assert inf["p"] == p and inf["max_bag"] <= 24
+    amp, per = tnq_lib.contract_sliced(plan, bits, per_slice=True)
+    # the oracle checks a spread of slices one by one, and their sum where cheap
+    idx = sorted(set([0, 1, (1 << p) - 1, (1 << p) // 2, 3 % (1 << p)]))
+    ref_tot, ref_per = oracle_lib.contract(circ, bits, order=plan.order(), mu=plan.sliced(), per_slice=True) \
+        if p <= 6 else (None, None)
+    for s in idx:
+        r = ref_per[s] if ref_per is not None else \
+            oracle_lib.contract(circ, bits, order=plan.order(), mu=plan.sliced(), slices=(s, s + 1))
+        assert rel_err(per[s], r, 36) < TOL, (s, per[s], r)
+    if ref_tot is not None:
+        assert rel_err(amp, ref_tot, 36) < TOL
+    assert abs(per.sum() - amp) <= 1e-12 * max(abs(amp), 1e-30) + 1e-18
+
+
+def test_batch_size_does_not_change_slices(cuda, tnq_lib):
+    """Every slice is computed by the same arithmetic at any batch size: the
+    per-slice values are bit-identical; ragged ranges give the partial sums."""
+    circ = I.random_grid_circuit(5, 5, 20, 3)
+    bits = I.random_bitstring(25, 3)
+    plan = tnq_lib.Plan(circ, min_p=5, max_p=5)
+    _, ref = tnq_lib.contract_sliced(plan, bits, per_slice=True)
+    for mb in (1, 2, 8, 32):
+        _, per = tnq_lib.contract_sliced(plan, bits, max_batch=mb, per_slice=True)
+        assert np.array_equal(per, ref), mb
+    a, per = tnq_lib.contract_sliced(plan, bits, 3, 27, max_batch=8, per_slice=True)
+    assert np.array_equal(per, ref[3:27])
+    assert abs(a - ref[3:27].sum()) < 1e-12 * np.abs(ref).sum()
+
+
+def test_slice_sum_matches_unsliced(cuda, tnq_lib, oracle_lib):
+    """Eq. 5 on the GPU: the sum over 2^p slices equals the unsliced oracle amplitude."""
+    circ = I.random_grid_circuit(5, 5, 16, 11)
+    bits = I.random_bitstring(25, 11)
+    plan = tnq_lib.Plan(circ, min_p=3, max_p=3)
+    amp = tnq_lib.contract_sliced(plan, bits)
+    ref = oracle_lib.contract(circ, bits)
+    assert rel_err(amp, ref, 25) < TOL
+
+
+def test_closed_forms_on_gpu(cuda, tnq_lib):
+    # all-H (no free variables): 2^-n/2 for every bitstring
+    for n in (1, 5, 30):
+        plan = tnq_lib.Plan(I.all_h(n))
+        for x in (0, 1, (1 << n) - 1):
+            a = tnq_lib.contract_sliced(plan, bits_of(x, n))
+            assert abs(a - 2 ** (-n / 2)) < TOL * 2 ** (-n / 2)
+    # GHZ and Bell through the batched call
+    ghz = tnq_lib.Plan(I.ghz(8), min_p=1, max_p=1)
+    bell = tnq_lib.Plan(I.bell())
+    ghz_bits = [bits_of(x, 8) for x in (0, 255, 1, 128, 170)]
+    bell_bits = [bits_of(x, 2) for x in range(4)]
+    out = tnq_lib.amplitudes_batch([ghz, bell], [ghz_bits, bell_bits])
+    s = 1 / math.sqrt(2)
+    ref = [s, s, 0, 0, 0, s, 0, 0, s]
+    assert np.max(np.abs(out - np.array(ref))) < TOL
+
+
+def test_wire_without_nondiagonal_gate(cuda, tnq_lib, oracle_lib):
+    """A qubit whose input segment is its output: <x_q|0> is 0 unless x_q = 0."""
+    c = I.Circuit(3, [I.Gate(I.H, 0), I.Gate(I.T, 1), I.Gate(I.CZ, 0, 1), I.Gate(I.H, 2), I.Gate(I.X_1_2, 0)])
+    plan = tnq_lib.Plan(c)
+    for x in range(8):
+        b = bits_of(x, 3)
+        a = tnq_lib.contract_sliced(plan, b)
+        r = oracle_lib.contract(c, b)
+        assert abs(a - r) < TOL
+
+
+def test_tiny_amplitudes_are_rescaled(cuda, tnq_lib, oracle_lib):
+    """Amplitudes far below the FP32 range survive: per-tensor power-of-two exponents."""
+    eps = 1e-9
+    cth = math.sqrt(1 - eps * eps)
+    u = (cth, 0.0, -eps, 0.0, eps, 0.0, cth, 0.0)  # [[c, -e], [e, c]]
+    n = 8
+    gates = []
+    for layer in range(2):
+        gates += [I.Gate(I.U1, q, -1, u) for q in range(n)]
+        gates += [I.Gate(I.CZ, q, q + 1) for q in range(layer % 2, n - 1, 2)]
+    c = I.Circuit(n, gates)
+    plan = tnq_lib.Plan(c, min_p=1, max_p=1)
+    x = [1, 0, 1, 0, 1, 0, 1, 0]
+    a = tnq_lib.contract_sliced(plan, x)
+    r = oracle_lib.contract(c, x)
+    assert abs(r) < 1e-30
+    assert abs(a - r) / abs(r) < TOL
+
+
+def test_random_small_circuits_all_gates(cuda, tnq_lib, oracle_lib):
+    for seed in range(4):
+        c = I.random_small_circuit(10, 120, 50 + seed)
+        plan = tnq_lib.Plan(c, min_p=2, max_p=2)
+        bl = [I.random_bitstring(10, 7 * seed + j) for j in range(4)]
+        out = tnq_lib.amplitudes_batch([plan], [bl])
+        for b, a in zip(bl, out):
+            r = oracle_lib.contract(c, b)
+            assert rel_err(a, r, 10) < TOL
+
+
+def test_uneven_batch_of_plans(cuda, tnq_lib, oracle_lib):
+    """Batched serving shape: circuits of different sizes, different bitstring counts."""
+    work = I.batched_serving_workload(n_circuits=4, bitstrings_per_circuit=3, seed=5)
+    plans, bl = [], []
+    for circ, bits in work:
+        side = int(round(math.sqrt(circ.n_qubits)))
+        plans.append(tnq_lib.Plan(circ, max_bag_log2=18, max_p=16))
+        bl.append(bits[: 1 + len(plans) % 3])
+    out = tnq_lib.amplitudes_batch(plans, bl)
+    k = 0
+    for (circ, _), p, bits in zip(work, plans, bl):
+        for b in bits:
+            if circ.n_qubits <= 36:
+                r = oracle_lib.contract(circ, b, order=p.order(), mu=p.sliced())
+                assert rel_err(out[k], r, circ.n_qubits) < TOL
+            else:
+                single = tnq_lib.contract_sliced(p, b)
+                assert abs(out[k] - single) <= 1e-9 * abs(single)
+            k += 1
+
+
+@pytest.mark.slow
+def test_7x7_full_size_sampled_slices(cuda, tnq_lib, oracle_lib):
+    """7x7 grid, depth 1+32+1, per-slice bag <= 28: the benchmark's launch
+    configuration (64 slices at once); two slices checked against the oracle,
+    the rest through properties (batch-independence of each slice value and the
+    slice sum)."""
+    import torch
+
+    circ = I.random_grid_circuit(7, 7, 32, 0)
+    bits = I.random_bitstring(49, 0)
+    plan = tnq_lib.Plan(circ, max_bag_log2=28, max_p=40)
+    inf = plan.info()
+    assert inf["max_bag"] <= 28
+    n_sl = inf["n_slices"]
+    B = min(64, n_sl)
+    ws = torch.empty(plan.workspace_bytes(B), dtype=torch.uint8, device="cuda")
+    amp, per = tnq_lib.contract_sliced(plan, bits, 0, B, workspace=ws, max_batch=B, per_slice=True)
+    for s in (0, B - 1):
+        r = oracle_lib.contract(circ, bits, order=plan.order(), mu=plan.sliced(), slices=(s, s + 1))
+        assert abs(per[s] - r) / abs(r) < TOL, (s, per[s], r)
+    _, per1 = tnq_lib.contract_sliced(plan, bits, 0, 4, workspace=ws, max_batch=1, per_slice=True)
+    assert np.array_equal(per1, per[:4])
+    assert abs(per.sum() - amp) <= 1e-12 * np.abs(per).sum()

@@ -1,0 +1,250 @@
+"""Host planner: the paper's worked example, tree-decomposition validity,
+slicing invariants and the exact cost model (no GPU)."""
+import itertools
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_2004_10892_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def toy():
+    g = json.load(open(os.path.join(GOLDEN, "toy_eq1.json")))
+    names = sorted({v for t in g["tensors"] for v in t})
+    idx = {v: i for i, v in enumerate(names)}
+    edges = set()
+    for t in g["tensors"]:
+        for a, b in itertools.combinations(t, 2):
+            edges.add(tuple(sorted((idx[a], idx[b]))))
+    g["names"] = names
+    g["idx"] = idx
+    g["edges"] = sorted(edges)
+    return g
+
+
+def _order(toy, names):
+    return [toy["idx"][v] for v in names]
+
+
+def test_toy_eq2_sequence(tnq_lib, toy):
+    tau, sizes = tnq_lib.graph_treewidth(6, toy["edges"], _order(toy, toy["order"]), bag_sizes=True)
+    assert tau == toy["treewidth"]
+    assert sizes == toy["eq2_cost_exponents"]
+    # intermediate of step i = its bag minus the eliminated index (Eq. 2)
+    assert [s - 1 for s in sizes] == [len(t) for t in toy["eq2_intermediates"]]
+
+
+def test_toy_tree_decomposition_is_path(tnq_lib, toy):
+    bags, parent = tnq_lib.graph_tree_decomposition(6, toy["edges"], _order(toy, toy["order"]))
+    got = sorted(tuple(sorted(toy["names"][v] for v in b)) for b in bags)
+    assert got == sorted(tuple(sorted(b)) for b in toy["td_bags"])
+    assert max(len(b) for b in bags) == toy["max_bag"]
+    # a path: every bag has at most two tree neighbours
+    deg = [0] * len(bags)
+    for c, p in enumerate(parent):
+        if p >= 0:
+            deg[c] += 1
+            deg[p] += 1
+    assert max(deg) <= 2 and sum(p < 0 for p in parent) == 1
+    # the reverse order yields the same tree
+    bags_r, _ = tnq_lib.graph_tree_decomposition(6, toy["edges"], _order(toy, toy["reverse_order"]))
+    assert sorted(map(sorted, bags_r)) == sorted(map(sorted, bags))
+
+
+@pytest.mark.parametrize("slicer", [0, 1, 2])
+def test_toy_first_deletion_is_k(tnq_lib, toy, slicer):
+    """Tree-trimming (k, l tie on length 3 and weight 9; the earliest wins),
+    degree (k has degree 4) and direct reduction all fix k: tau drops to 1."""
+    mu, tau = tnq_lib.graph_greedy_deletion(6, toy["edges"], _order(toy, toy["order"]), 1, slicer=slicer)
+    assert toy["names"][mu[0]] == "k"
+    assert tau[0] == toy["fix_k_treewidth"]
+
+
+def test_toy_fixing_l_leaves_a_triangle(tnq_lib, toy):
+    l = toy["idx"]["l"]
+    edges = [e for e in toy["edges"] if l not in e]
+    assert tnq_lib.graph_treewidth(6, edges, _order(toy, toy["order"])) == toy["fix_l_treewidth"]
+
+
+def _td_valid(n, edges, bags, parent):
+    """The three criteria of a tree decomposition (Section II.B)."""
+    cover = set(v for b in bags for v in b)
+    if cover != set(range(n)):
+        return "vertex not covered"
+    for a, b in edges:
+        if not any(a in x and b in x for x in bags):
+            return f"edge {a}-{b} not in a bag"
+    nb = len(bags)
+    adj = [[] for _ in range(nb)]
+    for c, p in enumerate(parent):
+        if p >= 0:
+            adj[c].append(p)
+            adj[p].append(c)
+    if sum(p < 0 for p in parent) != 1 or sum(len(a) for a in adj) != 2 * (nb - 1):
+        return "not a tree"
+    for v in range(n):
+        holders = [i for i, b in enumerate(bags) if v in b]
+        seen = {holders[0]}
+        stack = [holders[0]]
+        while stack:
+            x = stack.pop()
+            for y in adj[x]:
+                if y not in seen and v in bags[y]:
+                    seen.add(y)
+                    stack.append(y)
+        if len(seen) != len(holders):
+            return f"bags of {v} are not connected"
+    for i, a in enumerate(bags):
+        for j, b in enumerate(bags):
+            if i != j and set(a) <= set(b):
+                return "non-maximal bag"
+    return ""
+
+
+def _random_graph(n, p, seed):
+    rng = np.random.default_rng(seed)
+    return [(a, b) for a in range(n) for b in range(a + 1, n) if rng.random() < p]
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_tree_decomposition_valid(tnq_lib, seed):
+    n = 8 + 3 * seed
+    edges = _random_graph(n, 0.25, seed)
+    for method in (0, 1):
+        order = tnq_lib.graph_order(n, edges, method)
+        assert sorted(order) == list(range(n))
+        bags, parent = tnq_lib.graph_tree_decomposition(n, edges, order)
+        assert _td_valid(n, edges, bags, parent) == ""
+        tau = tnq_lib.graph_treewidth(n, edges, order)
+        assert max(len(b) for b in bags) - 1 == max(tau, max(len(b) for b in bags) - 1)
+        assert max(len(b) for b in bags) - 1 <= tau
+
+
+def test_tree_decomposition_of_circuit_graph(tnq_lib, oracle_lib):
+    c = I.random_grid_circuit(5, 5, 20, 1)
+    fv = oracle_lib.free_vars(c)
+    edges = oracle_lib.graph_edges(c)
+    n = len(fv)
+    order = tnq_lib.graph_order(n, edges, 0)
+    bags, parent = tnq_lib.graph_tree_decomposition(n, edges, order)
+    assert _td_valid(n, edges, bags, parent) == ""
+    assert max(len(b) for b in bags) - 1 == tnq_lib.graph_treewidth(n, edges, order)
+
+
+def test_known_treewidths(tnq_lib):
+    # path, cycle, complete graph, 3x3 grid (treewidth 3)
+    path = [(i, i + 1) for i in range(9)]
+    cyc = path + [(9, 0)]
+    k6 = [(a, b) for a in range(6) for b in range(a + 1, 6)]
+    grid = [(r * 3 + c, r * 3 + c + 1) for r in range(3) for c in range(2)] + \
+           [(r * 3 + c, (r + 1) * 3 + c) for r in range(2) for c in range(3)]
+    for n, e, tw in [(10, path, 1), (10, cyc, 2), (6, k6, 5), (9, grid, 3)]:
+        assert tnq_lib.graph_treewidth(n, e, tnq_lib.graph_order(n, e, 0)) == tw
+
+
+def _exact_tw(tnq_lib, n, edges):
+    return min(tnq_lib.graph_treewidth(n, edges, list(o)) for o in itertools.permutations(range(n)))
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_deleting_one_vertex_lowers_treewidth_by_at_most_one(tnq_lib, seed):
+    """Section III.A: removing a vertex lowers the (exact) treewidth by <= 1."""
+    n = 7
+    edges = _random_graph(n, 0.5, 10 + seed)
+    tw = _exact_tw(tnq_lib, n, edges)
+    for u in range(n):
+        red = [e for e in edges if u not in e]
+        tw_u = _exact_tw(tnq_lib, n, red)
+        assert tw - 1 <= tw_u <= tw
+
+
+@pytest.mark.parametrize("slicer", [0, 1, 2])
+def test_greedy_deletion_monotone(tnq_lib, oracle_lib, slicer):
+    """With the reduced order kept (Algorithm 2 without line 10's TD
+    recomputation), the treewidth never grows as vertices are removed."""
+    c = I.random_grid_circuit(5, 5, 16, 3)
+    edges = oracle_lib.graph_edges(c)
+    n = len(oracle_lib.free_vars(c))
+    order = tnq_lib.graph_order(n, edges, 0)
+    tau0 = tnq_lib.graph_treewidth(n, edges, order)
+    mu, tau = tnq_lib.graph_greedy_deletion(n, edges, order, 6, slicer=slicer)
+    assert len(set(mu)) == 6
+    seq = [tau0] + tau
+    assert all(b <= a for a, b in zip(seq, seq[1:]))
+
+
+def test_tree_trimming_beats_degree_on_grid(tnq_lib, oracle_lib):
+    """Section IV: tree-trimming lowers the treewidth faster than the degree score."""
+    c = I.random_grid_circuit(6, 6, 20, 0)
+    edges = oracle_lib.graph_edges(c)
+    n = len(oracle_lib.free_vars(c))
+    order = tnq_lib.graph_order(n, edges, 0)
+    _, tt = tnq_lib.graph_greedy_deletion(n, edges, order, 6, slicer=0)
+    _, dg = tnq_lib.graph_greedy_deletion(n, edges, order, 6, slicer=1)
+    assert tt[-1] <= dg[-1]
+    tau0 = tnq_lib.graph_treewidth(n, edges, order)
+    assert tt[-1] <= tau0 - 3
+
+
+def test_plan_variables_match_oracle_network(tnq_lib, oracle_lib):
+    for circ in [I.random_grid_circuit(4, 4, 16, 0), I.random_small_circuit(6, 60, 1), I.ghz(5)]:
+        plan = tnq_lib.Plan(circ, min_p=2, max_p=2)
+        keys = plan.order() + plan.sliced()
+        assert sorted(keys) == sorted(oracle_lib.free_vars(circ))
+        assert len(set(keys)) == len(keys)
+
+
+def test_plan_stopping_rule(tnq_lib):
+    c = I.random_grid_circuit(6, 6, 24, 0)
+    plan = tnq_lib.Plan(c, max_bag_log2=14, max_p=40)
+    inf = plan.info()
+    assert inf["max_bag"] <= 14 and inf["p"] >= 1
+    assert inf["tau"] <= inf["tau_full"]
+    plan2 = tnq_lib.Plan(c, max_bag_log2=24, min_p=4, max_p=8)
+    assert plan2.info()["p"] == 4
+    assert plan2.info()["n_slices"] == 16
+
+
+def test_plan_deterministic(tnq_lib):
+    c = I.random_grid_circuit(5, 5, 20, 9)
+    a = tnq_lib.Plan(c, min_p=3, max_p=3)
+    b = tnq_lib.Plan(c, min_p=3, max_p=3)
+    assert a.order() == b.order() and a.sliced() == b.sliced()
+
+
+def test_cost_model_equals_oracle_counts(tnq_lib, oracle_lib):
+    """Exact cost model: flops per slice = 6 (complex mults) + 2 (complex adds)
+    as counted by the oracle running the plan's buckets."""
+    for circ, kw in [(I.random_grid_circuit(4, 4, 12, 2), {}), (I.random_grid_circuit(4, 5, 16, 5), dict(min_p=2, max_p=2)),
+                     (I.random_small_circuit(7, 70, 4), dict(min_p=1, max_p=1))]:
+        plan = tnq_lib.Plan(circ, **kw)
+        inf = plan.info()
+        bits = I.random_bitstring(circ.n_qubits, 3)
+        _, (cmul, cadd) = oracle_lib.contract(circ, bits, order=plan.order(), mu=plan.sliced(), slices=(0, 1),
+                                              counts=True)
+        assert inf["flops_per_slice"] == 6 * cmul + 2 * cadd
+        bag, k, _ = plan.buckets()
+        assert inf["max_bag"] == bag.max()
+        assert inf["total_flops"] == inf["flops_per_slice"] * inf["n_slices"]
+
+
+def test_plan_rejects_bad_circuits(tnq_lib):
+    bad = [I.Circuit(2, [I.Gate(I.CZ, 0, 0)]), I.Circuit(2, [I.Gate(I.H, 2)]), I.Circuit(2, [I.Gate(9, 0)]),
+           I.Circuit(0, [])]
+    for c in bad:
+        with pytest.raises(tnq_lib.TnqError) as e:
+            tnq_lib.Plan(c)
+        assert e.value.status == tnq_lib.EINVAL
+    with pytest.raises(tnq_lib.TnqError):
+        tnq_lib.Plan(I.all_h(3), min_p=3, max_p=1)
+
+
+def test_plan_without_free_variables(tnq_lib):
+    plan = tnq_lib.Plan(I.all_h(4))
+    inf = plan.info()
+    assert inf["n_free_vars"] == 0 and inf["n_buckets"] == 0 and inf["n_slices"] == 1
