@@ -269,3 +269,23 @@ tnq_status tnq_graph_greedy_deletion(int32_t n, size_t n_edges, const int32_t* e
 }
 
 }  // extern "C"
+
+// Internal (not in include/tnq.h): bucket structure for analysis and tests.
+// Per bucket 12 ints: r, k, output rank, sum flag, then the ranks of up to
+// 8 inputs (-1 past k); *n gets the bucket count. Returns 1 if cap is short.
+extern "C" int tnq_internal_bucket_detail(const tnq_plan* P, int32_t* out, int cap, int32_t* n) {
+  if (!P || !n) return 1;
+  const auto& prog = P->prog;
+  *n = (int32_t)prog.buckets.size();
+  if (cap < *n * 12) return 1;
+  for (size_t i = 0; i < prog.buckets.size(); ++i) {
+    const auto& b = prog.buckets[i];
+    int32_t* o = out + 12 * i;
+    o[0] = b.r;
+    o[1] = b.k;
+    o[2] = prog.tensors[b.output].rank();
+    o[3] = b.sum ? 1 : 0;
+    for (int j = 0; j < 8; ++j) o[4 + j] = j < b.k ? prog.tensors[b.inputs[j]].rank() : -1;
+  }
+  return 0;
+}
