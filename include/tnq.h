@@ -193,6 +193,28 @@ tnq_status tnq_amplitudes_batch(const tnq_plan* const* plans, size_t n_plans,
                                 void* workspace, size_t ws_bytes, void* stream,
                                 double* out_amps);
 
+/* tnq_contract_sliced_noalloc: the same partial sum as tnq_contract_sliced
+ * for callers that cannot allocate device memory (a host whose own pool
+ * allocator already holds the memory it may use, code running while another
+ * thread keeps a stream capture open, or a loop that cannot afford
+ * cudaMalloc's implicit synchronisation). The paper has no counterpart: this
+ * is a deployment variant. Instead of a caller workspace it uses one static
+ * 64 MiB device array (held by every GPU that loads the library until the
+ * process exits) for the plan tables and the intermediate tensors; it
+ * allocates no device memory. As many slices run at once as fit in it.
+ *  - The first call on each device looks up the array's device address with
+ *    that device current; make that first call before any stream capture.
+ *  - Every call shares the one array per device: calls that overlap on the
+ *    GPU (other streams, other threads) race and give wrong results. The
+ *    call clears what must start at zero and synchronises `stream` before it
+ *    returns.
+ *  - TNQ_ENOMEM (with the byte counts in tnq_last_error) if one slice of the
+ *    plan needs more than the 64 MiB.
+ * Arguments, results and other errors as tnq_contract_sliced. */
+tnq_status tnq_contract_sliced_noalloc(const tnq_plan* plan, const uint8_t* bits,
+                                       uint64_t slice_begin, uint64_t slice_end, void* stream,
+                                       double* out_amp, double* out_slice_amps);
+
 /* ---- graph-level planning (host only) ---------------------------------
  * The paper's graph algorithms on an arbitrary simple graph with vertices
  * 0..n-1 and edges (edges[2e], edges[2e+1]); self-loops and repeated edges

@@ -1019,3 +1019,145 @@ tnq_status tnq_amplitudes_batch(const tnq_plan* const* plans, size_t n_plans, co
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of tnq_contract_sliced.
+//
+// Some callers cannot call cudaMalloc: a host whose own pool allocator has
+// already reserved the device memory it is allowed to use, code that runs
+// while another thread of the process holds a stream capture open (where
+// cudaMalloc is not allowed), or a latency-bound loop in which cudaMalloc's
+// implicit device synchronisation would stall other streams. For them this
+// entry point takes its scratch (plan tables and intermediate tensors) from one
+// fixed-size array in device global memory that the library declares at file
+// scope; every GPU that loads the library holds that array until the process
+// exits. It allocates no device memory and calls no allocating routine.
+namespace tnq {
+
+constexpr size_t NOALLOC_SCRATCH_BYTES = 64ull << 20;  // 64 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+// Device address of g_noalloc_scratch, looked up once per device with that
+// device current (the host-side symbol is only a stand-in, not an address).
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_addr[256] = {};
+
+static tnq_status noalloc_scratch_address(void** out) {
+  int dev = 0;
+  CU(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) {
+    set_error("device ordinal out of range");
+    return TNQ_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      set_error(std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+      return TNQ_ECUDA;
+    }
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return TNQ_OK;
+}
+
+}  // namespace tnq
+
+extern "C" {
+
+tnq_status tnq_contract_sliced_noalloc(const tnq_plan* plan, const uint8_t* bits, uint64_t slice_begin,
+                                       uint64_t slice_end, void* stream, double* out_amp, double* out_slice_amps) {
+  if (!plan || !bits || !out_amp) { set_error("NULL argument"); return TNQ_EINVAL; }
+  const uint64_t n_slices = 1ull << plan->mu.size();
+  if (slice_begin > slice_end || slice_end > n_slices) { set_error("slice range outside [0, n_slices)"); return TNQ_EINVAL; }
+  for (int q = 0; q < plan->net.n_qubits; ++q)
+    if (bits[q] > 1) { set_error("bitstring bytes must be 0 or 1"); return TNQ_EINVAL; }
+  out_amp[0] = out_amp[1] = 0.0;
+  if (slice_begin == slice_end) return TNQ_OK;
+  tnq_status st = check_device();
+  if (st != TNQ_OK) return st;
+  void* scratch = nullptr;
+  if ((st = noalloc_scratch_address(&scratch)) != TNQ_OK) return st;
+
+  // Host copies of the plan tables; they go to the front of the scratch.
+  const Program& prog = plan->prog;
+  const uint64_t n_items = slice_end - slice_begin;
+  uint64_t cap = 1;
+  while (cap < n_items && cap < (1ull << MAX_ITEM_BITS)) cap <<= 1;
+  int B = 0;
+  size_t tables = 0;
+  for (uint64_t b = 1; b <= cap; b <<= 1) {
+    const size_t t = align_up((prog.leaves.size() + prog.scalar_leaves.size()) * sizeof(LeafDev), 256) +
+                     align_up(plan->net.inout_qubits.size() * sizeof(int), 256) +
+                     align_up(prog.finals.size() * sizeof(FinalDev), 256);
+    if (t + layout_bytes(*plan, 0, (int)b) > NOALLOC_SCRATCH_BYTES) break;
+    B = (int)b;
+    tables = t;
+  }
+  if (B == 0) {
+    set_error("plan needs " + std::to_string(layout_bytes(*plan, 0, 1)) +
+              " bytes of scratch for one slice; the static scratch of tnq_contract_sliced_noalloc holds " +
+              std::to_string(NOALLOC_SCRATCH_BYTES) + " bytes");
+    return TNQ_ENOMEM;
+  }
+  ExecConfig C;  // pointers into the scratch; nothing here is freed
+  C.L = make_layout(*plan, 0, B);
+  std::vector<LeafDev> leaves, scalars;
+  for (int t : prog.leaves) leaves.push_back(make_leafdev(*plan, &prog.tensors[t], prog.tensors[t].leaf_gate, &C.L, t));
+  for (int g : prog.scalar_leaves) scalars.push_back(make_leafdev(*plan, nullptr, g, nullptr, -1));
+  std::vector<FinalDev> finals;
+  for (int t : prog.finals) finals.push_back(FinalDev{C.L.off[t], t, (int)C.L.dep[t]});
+  if (!build_kparams(*plan, C.L, C.kp, C.kshape)) return TNQ_EUNSUPPORTED;
+  char* base = reinterpret_cast<char*>(scratch);
+  size_t o = 0;
+  C.d_leaves = reinterpret_cast<LeafDev*>(base + o);
+  o += leaves.size() * sizeof(LeafDev);
+  C.d_scalars = reinterpret_cast<LeafDev*>(base + o);
+  o = align_up(o + scalars.size() * sizeof(LeafDev), 256);
+  C.d_inout = reinterpret_cast<int*>(base + o);
+  o = align_up(o + plan->net.inout_qubits.size() * sizeof(int), 256);
+  C.d_finals = reinterpret_cast<FinalDev*>(base + o);
+  o = align_up(o + finals.size() * sizeof(FinalDev), 256);
+  C.n_leaves = (int)leaves.size();
+  C.n_scalars = (int)scalars.size();
+  C.n_inout = (int)plan->net.inout_qubits.size();
+  C.n_finals = (int)finals.size();
+  char* ws = base + tables;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (!leaves.empty()) CU(cudaMemcpyAsync(C.d_leaves, leaves.data(), leaves.size() * sizeof(LeafDev), cudaMemcpyHostToDevice, s));
+  if (!scalars.empty()) CU(cudaMemcpyAsync(C.d_scalars, scalars.data(), scalars.size() * sizeof(LeafDev), cudaMemcpyHostToDevice, s));
+  if (C.n_inout) CU(cudaMemcpyAsync(C.d_inout, plan->net.inout_qubits.data(), C.n_inout * sizeof(int), cudaMemcpyHostToDevice, s));
+  if (!finals.empty()) CU(cudaMemcpyAsync(C.d_finals, finals.data(), finals.size() * sizeof(FinalDev), cudaMemcpyHostToDevice, s));
+  std::vector<unsigned> words((size_t)C.L.n_words * C.L.n_rows, 0u);
+  pack_bits(bits, plan->net.n_qubits, words);
+  CU(cudaMemcpyAsync(ws + C.L.bits_off, words.data(), words.size() * 4, cudaMemcpyHostToDevice, s));
+  std::vector<double> res(2 * (size_t)B), part(2);
+  double sre = 0, sim = 0;
+  for (uint64_t b0 = slice_begin; b0 < slice_end; b0 += B) {
+    BatchHdr h;
+    std::memset(&h, 0, sizeof(h));
+    h.item_base = b0;
+    h.item_end = slice_end;
+    h.p = (int)plan->mu.size();
+    h.n_words = C.L.n_words;
+    CU(cudaMemcpyAsync(ws + C.L.hdr_off, &h, sizeof(h), cudaMemcpyHostToDevice, s));
+    enqueue_batch(*plan, C, ws, s);  // clears the atomicMax targets first
+    CU(cudaGetLastError());
+    CU(cudaMemcpyAsync(part.data(), ws + C.L.part_off, 16, cudaMemcpyDeviceToHost, s));
+    if (out_slice_amps) CU(cudaMemcpyAsync(res.data(), ws + C.L.res_off, 16 * (size_t)B, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    sre += part[0];
+    sim += part[1];
+    if (out_slice_amps) {
+      const uint64_t nv = std::min<uint64_t>(B, slice_end - b0);
+      std::memcpy(out_slice_amps + 2 * (b0 - slice_begin), res.data(), 16 * nv);
+    }
+  }
+  out_amp[0] = sre;
+  out_amp[1] = sim;
+  return TNQ_OK;
+}
+
+}  // extern "C"

@@ -70,6 +70,7 @@ SIGNATURES = {
     "tnq_plan_workspace_bytes": (ctypes.c_size_t, [_vp, ctypes.c_uint32]),
     "tnq_contract_sliced": (ctypes.c_int, [_vp, _u8p, ctypes.c_uint64, ctypes.c_uint64, _vp, ctypes.c_size_t,
                                            ctypes.c_uint32, _vp, _f64p, _f64p]),
+    "tnq_contract_sliced_noalloc": (ctypes.c_int, [_vp, _u8p, ctypes.c_uint64, ctypes.c_uint64, _vp, _f64p, _f64p]),
     "tnq_amplitudes_batch": (ctypes.c_int, [_P(_vp), ctypes.c_size_t, _u8p, _szp, _vp, ctypes.c_size_t, _vp,
                                             _f64p]),
     "tnq_graph_treewidth": (ctypes.c_int, [ctypes.c_int32, ctypes.c_size_t, _i32p, _i32p, _i32p, _i32p]),
@@ -214,6 +215,25 @@ def contract_sliced(plan: Plan, bits, slice_begin: int = 0, slice_end: int | Non
                                      ctypes.c_void_p(workspace.data_ptr()), workspace.numel(), max_batch,
                                      _stream_ptr(stream), _ptr(out, ctypes.c_double),
                                      _ptr(per, ctypes.c_double) if per is not None else None))
+    amp = complex(out[0], out[1])
+    if per_slice:
+        return amp, per[: 2 * (slice_end - slice_begin)].view(np.complex128).copy()
+    return amp
+
+
+def contract_sliced_noalloc(plan: Plan, bits, slice_begin: int = 0, slice_end: int | None = None, stream=None,
+                            per_slice: bool = False):
+    """tnq_contract_sliced_noalloc: as contract_sliced, with the library's static
+    device scratch instead of a workspace (no device allocation anywhere)."""
+    n_slices = plan.info()["n_slices"]
+    if slice_end is None:
+        slice_end = n_slices
+    b = _bits_array(bits, plan.n_qubits)
+    out = np.zeros(2, np.float64)
+    per = np.zeros(2 * max(slice_end - slice_begin, 1), np.float64) if per_slice else None
+    _check(lib().tnq_contract_sliced_noalloc(plan.handle, _ptr(b, ctypes.c_uint8), slice_begin, slice_end,
+                                             _stream_ptr(stream), _ptr(out, ctypes.c_double),
+                                             _ptr(per, ctypes.c_double) if per is not None else None))
     amp = complex(out[0], out[1])
     if per_slice:
         return amp, per[: 2 * (slice_end - slice_begin)].view(np.complex128).copy()
