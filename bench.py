@@ -146,9 +146,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="tnq", choices=["tnq", "reference"])
     ap.add_argument("--config", default="7x7_d1+32+1", choices=sorted(CONFIGS))
-    ap.add_argument("--max-batch", type=int, default=64, help="slices contracted at once")
+    ap.add_argument("--max-batch", type=int, default=256, help="slices contracted at once")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-profile", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tune-batch", type=int, default=16, help="slices per batch while autotuning")
+    ap.add_argument("--tune-gb", type=int, default=48, help="workspace GiB while autotuning")
     args = ap.parse_args()
 
     if args.impl == "reference":
@@ -174,12 +177,20 @@ def main():
     t_plan = time.perf_counter()
     plan = tnq.Plan(circ, max_bag_log2=mb, min_p=pmin, max_p=pmax)
     t_plan = time.perf_counter() - t_plan
-    info = plan.info()
-    n_sl = info["n_slices"]
-    B = min(args.max_batch, n_sl)
-    ws = torch.empty(plan.workspace_bytes(B), dtype=torch.uint8, device="cuda")
+    n_sl = plan.info()["n_slices"]
     stream = torch.cuda.current_stream()
     L = tnq.lib()
+    # autotune (untimed, part of planning): keep each fused chain only where it measures faster
+    t_tune = time.perf_counter()
+    n_fused = None
+    if not args.no_autotune:
+        tune_ws = torch.empty(args.tune_gb << 30, dtype=torch.uint8, device="cuda")
+        n_fused = plan.autotune(bits, workspace=tune_ws, max_batch=min(args.tune_batch, n_sl), stream=stream)
+        del tune_ws
+    t_tune = time.perf_counter() - t_tune
+    info = plan.info()
+    B = min(args.max_batch, n_sl)
+    ws = torch.empty(plan.workspace_bytes(B), dtype=torch.uint8, device="cuda")
 
     # warm-up (also captures the CUDA graph)
     for _ in range(args.warmup):
@@ -220,6 +231,7 @@ def main():
         ms = (ctypes.c_float * nb)()
         by = (ctypes.c_double * nb)()
         bag = (ctypes.c_int * nb)()
+        kind = (ctypes.c_int * nb)()
         n_out, b_out = ctypes.c_int(), ctypes.c_int()
         import numpy as np
 
@@ -228,10 +240,11 @@ def main():
                                            ctypes.c_uint64, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint32,
                                            ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
                                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
-                                           ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+                                           ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_int)]
         rc = L.tnq_internal_profile(plan.handle, bb.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), 0, n_sl,
                                     ctypes.c_void_p(ws.data_ptr()), ws.numel(), B, ctypes.c_void_p(stream.cuda_stream),
-                                    nb, ms, by, bag, ctypes.byref(n_out), ctypes.byref(b_out))
+                                    nb, ms, by, bag, kind, ctypes.byref(n_out), ctypes.byref(b_out))
         if rc == 0:
             n = n_out.value
             tot_ms = sum(ms[i] for i in range(n))
@@ -246,7 +259,11 @@ def main():
                     "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if not peaks.get("fallback") else "fallback",
                     "launches": n, "batch": b_out.value, "bytes_per_launch": tot_by / n, "ms_per_launch": tot_ms / n,
                     "big_buckets_gbs": big_by / (big_ms / 1e3) / 1e9 if big_ms > 0 else None,
-                    "big_bucket_time_share": big_ms / tot_ms if tot_ms > 0 else None}
+                    "big_bucket_time_share": big_ms / tot_ms if tot_ms > 0 else None,
+                    "top_launches": [{"kind": "group" if kind[i] else "bucket", "buckets": max(1, kind[i]),
+                                      "bag": bag[i], "ms": round(ms[i], 4),
+                                      "gbs": round(by[i] / (ms[i] / 1e3) / 1e9, 1) if ms[i] > 0 else None}
+                                     for i in sorted(range(n), key=lambda i: -ms[i])[:8]]}
 
     cpu = None
     err = None
@@ -270,7 +287,8 @@ def main():
                        "n_qubits": circ.n_qubits, "p": info["p"], "n_slices": n_sl, "tau_full": info["tau_full"],
                        "tau": info["tau"], "max_bag": info["max_bag"], "batch": B,
                        "flops_per_slice": info["flops_per_slice"], "bytes_per_slice": info["bytes_per_slice"],
-                       "l2": "inputs larger than L2 (each slice streams GBs)", "plan_s": t_plan},
+                       "l2": "inputs larger than L2 (each batch streams GBs)", "plan_s": t_plan,
+                       "autotune_s": t_tune, "fused_chains": info["n_fused_groups"]},
             "time_per_amplitude_s": t_dev / args.steps,
             "rel_err_vs_fp64": err,
             "amplitude": [amp.real, amp.imag],

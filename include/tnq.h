@@ -103,6 +103,9 @@ typedef struct {
   int32_t gemm_min_k_log2;/* merged buckets with K >= 2^this run as GEMMs (0 = library default) */
   int32_t ordering;       /* tnq_ordering */
   int32_t td_rebuild;     /* 0: after a deletion drop the vertex from every bag; 1: rebuild the TD from the reduced order */
+  int32_t fuse_min_rank;  /* run chains of buckets whose intermediate results have >= 2^this entries as one
+                             fused kernel (no intermediate reaches HBM); 0 = no fusion; default 12 */
+  int32_t pad_;
 } tnq_plan_opts;
 
 typedef struct {
@@ -120,7 +123,7 @@ typedef struct {
   double peak_bytes_per_slice; /* largest live intermediate set of one slice (complex64) */
   double total_flops;      /* 2^p * flops_per_slice */
   int32_t n_gemm_buckets;  /* merged buckets that run as tensor-core GEMMs */
-  int32_t pad_;
+  int32_t n_fused_groups;  /* chains of buckets fused into one kernel (bytes_per_slice counts them fused) */
 } tnq_plan_info;
 
 typedef struct tnq_plan tnq_plan;
@@ -131,7 +134,8 @@ const char* tnq_status_string(tnq_status s);
 const char* tnq_last_error(void);
 /* Library version string. */
 const char* tnq_version(void);
-/* Fills opts with defaults: tree-trimming, no bag limit, p in [0, 0], c64, min-fill. */
+/* Fills opts with defaults: tree-trimming, no bag limit, p in [0, 0], c64, min-fill, fusion of chains
+ * whose results have >= 2^12 entries. */
 void tnq_plan_opts_default(tnq_plan_opts* opts);
 
 /* ---- planning (host only; works without a GPU) ------------------------
@@ -181,6 +185,17 @@ tnq_status tnq_contract_sliced(const tnq_plan* plan, const uint8_t* bits,
                                uint64_t slice_begin, uint64_t slice_end,
                                void* workspace, size_t ws_bytes, uint32_t max_batch,
                                void* stream, double* out_amp, double* out_slice_amps);
+
+/* tnq_plan_autotune: measures on the current device, for batches of up to
+ * max_batch slices, every fused chain of buckets (see fuse_min_rank) against
+ * the same buckets run one launch each, and keeps the faster form of each
+ * chain. Contraction results do not change (fusion only regroups the same
+ * products). It modifies the plan: call it once, before the plan is shared
+ * between threads. workspace/ws_bytes as for tnq_contract_sliced; bits is the
+ * bitstring used for the trial batch. *out_n_fused (may be NULL) gets the
+ * number of chains kept fused. */
+tnq_status tnq_plan_autotune(tnq_plan* plan, const uint8_t* bits, void* workspace, size_t ws_bytes,
+                             uint32_t max_batch, void* stream, int32_t* out_n_fused);
 
 /* tnq_amplitudes_batch: amplitudes of many bitstrings of many plans.
  * Plan i has bitstrings bits_offset[i] .. bits_offset[i+1]-1 (bits_offset has

@@ -58,6 +58,7 @@ void tnq_plan_opts_default(tnq_plan_opts* o) {
   o->gemm_min_k_log2 = 0;
   o->ordering = TNQ_ORDER_MIN_FILL;
   o->td_rebuild = 0;
+  o->fuse_min_rank = 12;
 }
 
 tnq_status tnq_plan_from_circuit(int32_t n_qubits, const tnq_gate* gates, size_t n_gates,
@@ -70,7 +71,8 @@ tnq_status tnq_plan_from_circuit(int32_t n_qubits, const tnq_gate* gates, size_t
   if (opts) o = *opts;
   if (o.slicer < 0 || o.slicer > TNQ_SLICER_LEARNED || o.min_p < 0 || o.max_p < o.min_p ||
       o.max_p > 62 || o.max_bag_log2 < 0 || o.max_bag_log2 > 40 || o.precision < 0 ||
-      o.precision > TNQ_PREC_SPLIT_TF32 || o.ordering < 0 || o.ordering > TNQ_ORDER_MIN_DEGREE) {
+      o.precision > TNQ_PREC_SPLIT_TF32 || o.ordering < 0 || o.ordering > TNQ_ORDER_MIN_DEGREE ||
+      o.fuse_min_rank < 0 || o.fuse_min_rank > 40) {
     set_error("invalid plan options");
     return TNQ_EINVAL;
   }
@@ -98,6 +100,7 @@ tnq_status tnq_plan_from_circuit(int32_t n_qubits, const tnq_gate* gates, size_t
     for (int v : P->mu) delete_vertex(reduced, v);
     P->tau = treewidth_of_order(reduced, P->order);
     P->prog = compile_program(P->net, P->order, P->mu);
+    fuse_chains(P->prog, P->order, o.fuse_min_rank);
     P->amp_scale_log2 = -0.5 * P->net.n_sqrt2;
     *out_plan = P.release();
     return TNQ_OK;
@@ -134,6 +137,7 @@ tnq_status tnq_plan_info_get(const tnq_plan* P, tnq_plan_info* out) {
   }
   out->total_flops = std::ldexp(P->prog.flops_per_slice, (int)P->mu.size());
   out->n_gemm_buckets = 0;
+  out->n_fused_groups = (int32_t)P->prog.groups.size();
   return TNQ_OK;
 }
 
@@ -286,6 +290,28 @@ extern "C" int tnq_internal_bucket_detail(const tnq_plan* P, int32_t* out, int c
     o[2] = prog.tensors[b.output].rank();
     o[3] = b.sum ? 1 : 0;
     for (int j = 0; j < 8; ++j) o[4 + j] = j < b.k ? prog.tensors[b.inputs[j]].rank() : -1;
+  }
+  return 0;
+}
+
+// Internal: per bucket, the bucket that consumes its result (-1 for a final
+// scalar) and the number of variables of the union of the two bags.
+extern "C" int tnq_internal_bucket_chain(const tnq_plan* P, int32_t* consumer, int32_t* union_size, int cap) {
+  if (!P) return 1;
+  const auto& prog = P->prog;
+  if (cap < (int)prog.buckets.size()) return 1;
+  std::vector<int> pos(P->net.free_vars.size(), -1);
+  for (size_t i = 0; i < prog.buckets.size(); ++i) {
+    const auto& b = prog.buckets[i];
+    const int c = prog.tensors[b.output].consumer;
+    consumer[i] = c;
+    std::vector<int> u;
+    for (int t : b.inputs) u.insert(u.end(), prog.tensors[t].vars.begin(), prog.tensors[t].vars.end());
+    if (c >= 0)
+      for (int t : prog.buckets[c].inputs) u.insert(u.end(), prog.tensors[t].vars.begin(), prog.tensors[t].vars.end());
+    std::sort(u.begin(), u.end());
+    u.erase(std::unique(u.begin(), u.end()), u.end());
+    union_size[i] = (int)u.size();
   }
   return 0;
 }

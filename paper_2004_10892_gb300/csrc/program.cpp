@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <iterator>
 
 namespace tnq {
 
@@ -153,6 +154,10 @@ Program compile_program(const Network& net, const std::vector<int>& order, const
       P.scalar_leaves.push_back((int)gi);
       continue;
     }
+    for (int e = 0; e < 4; ++e) {
+      const float m = std::abs(gt.val[e]);
+      if (m != 0.f && (m < 0.0625f || m > 16.f)) t.wide_range = true;
+    }
     std::sort(t.vars.begin(), t.vars.end(), by_pos);
     t.vars.erase(std::unique(t.vars.begin(), t.vars.end()), t.vars.end());
     P.tensors.push_back(t);
@@ -216,6 +221,121 @@ Program compile_program(const Network& net, const std::vector<int>& order, const
     else place(out);
   }
   return P;
+}
+
+}  // namespace tnq
+
+namespace tnq {
+
+static std::vector<int> bag_of(const Program& P, const PBucket& b) {
+  std::vector<int> u;
+  for (int t : b.inputs) u.insert(u.end(), P.tensors[t].vars.begin(), P.tensors[t].vars.end());
+  std::sort(u.begin(), u.end());
+  u.erase(std::unique(u.begin(), u.end()), u.end());
+  return u;
+}
+
+void fuse_chains(Program& P, const std::vector<int>& order, int min_rank) {
+  const int nb = (int)P.buckets.size();
+  if (P.bytes_unfused == 0) P.bytes_unfused = P.bytes_per_slice;
+  P.groups.clear();
+  P.group_of.assign(nb, -1);
+  if (min_rank <= 0) {
+    set_groups(P, {});
+    return;
+  }
+  std::vector<int> pos(order.size() + 1, 0);
+  {
+    int maxv = 0;
+    for (int v : order) maxv = std::max(maxv, v);
+    pos.assign(maxv + 1, -1);
+    for (size_t i = 0; i < order.size(); ++i) pos[order[i]] = (int)i;
+  }
+  auto by_pos = [&](int a, int b) { return pos[a] < pos[b]; };
+  for (int i = 0; i < nb; ++i) {
+    if (P.group_of[i] >= 0 || !P.buckets[i].sum) continue;
+    std::vector<int> chain{i};
+    std::vector<int> U = bag_of(P, P.buckets[i]);
+    int n_ext = P.buckets[i].k;
+    while ((int)chain.size() < GM_MAX) {
+      const PBucket& last = P.buckets[chain.back()];
+      if (P.tensors[last.output].rank() < min_rank) break;
+      const int c = P.tensors[last.output].consumer;
+      if (c < 0 || !P.buckets[c].sum || P.group_of[c] >= 0) break;
+      std::vector<int> bc = bag_of(P, P.buckets[c]), nu;
+      std::set_union(U.begin(), U.end(), bc.begin(), bc.end(), std::back_inserter(nu));
+      if (nu.size() != U.size()) break;  // a new variable would enter the product space
+      const int ext = n_ext + P.buckets[c].k - 1;
+      if (ext > GIN_MAX) break;
+      bool wide = false;
+      for (int t : P.buckets[c].inputs) wide |= P.tensors[t].wide_range;
+      if (chain.size() == 1)
+        for (int t : P.buckets[chain[0]].inputs) wide |= P.tensors[t].wide_range;
+      if (wide) break;
+      if ((int)chain.size() + 1 + GL_OUT_MIN > GL_MAX) break;  // keep >= GL_OUT_MIN output variables local
+      chain.push_back(c);
+      n_ext = ext;
+    }
+    if (chain.size() < 2) continue;
+    FusedGroup g;
+    g.buckets = chain;
+    g.output = P.buckets[chain.back()].output;
+    std::vector<int> elim;
+    for (int b : chain) elim.push_back(P.buckets[b].u);
+    for (size_t s = 0; s < chain.size(); ++s)
+      for (int t : P.buckets[chain[s]].inputs)
+        if (!(s > 0 && t == P.buckets[chain[s - 1]].output)) g.ext_inputs.push_back(t);
+    std::vector<int> outv = P.tensors[g.output].vars;  // already sorted by position
+    std::vector<int> U2 = U;
+    std::sort(U2.begin(), U2.end(), by_pos);
+    const int n_local = std::min<int>(GL_MAX, (int)U2.size());
+    g.local_vars = elim;
+    for (int v : outv)
+      if ((int)g.local_vars.size() < n_local) g.local_vars.push_back(v);
+      else g.tile_vars.push_back(v);
+    std::sort(g.local_vars.begin(), g.local_vars.end(), by_pos);
+    const int gi = (int)P.groups.size();
+    for (int b : chain) P.group_of[b] = gi;
+    P.groups.push_back(g);
+  }
+  set_groups(P, std::vector<FusedGroup>(P.groups));
+}
+
+void set_groups(Program& P, const std::vector<FusedGroup>& groups) {
+  if (P.bytes_unfused == 0) P.bytes_unfused = P.bytes_per_slice;
+  P.groups = groups;
+  P.group_of.assign(P.buckets.size(), -1);
+  double saved = 0;
+  for (size_t gi = 0; gi < P.groups.size(); ++gi) {
+    const auto& g = P.groups[gi];
+    for (int b : g.buckets) P.group_of[b] = (int)gi;
+    // algorithmic bytes: intermediates inside a group are neither written nor read
+    for (size_t s = 0; s + 1 < g.buckets.size(); ++s)
+      saved += 2 * std::ldexp(8.0, P.tensors[P.buckets[g.buckets[s]].output].rank());
+  }
+  P.bytes_per_slice = P.bytes_unfused - saved;
+}
+
+Liveness tensor_liveness(const Program& P) {
+  const int nb = (int)P.buckets.size();
+  const int T = (int)P.tensors.size();
+  Liveness L;
+  L.lo.assign(T, -1);
+  L.hi.assign(T, nb);
+  L.internal.assign(T, 0);
+  auto eff = [&](int b) {
+    if (b < 0 || b >= nb || P.group_of.empty() || P.group_of[b] < 0) return b;
+    return P.groups[P.group_of[b]].buckets.back();
+  };
+  for (int t = 0; t < T; ++t) {
+    const PTensor& x = P.tensors[t];
+    L.lo[t] = eff(x.producer);
+    L.hi[t] = x.consumer >= 0 ? eff(x.consumer) : nb;
+    if (x.producer >= 0 && !P.group_of.empty() && P.group_of[x.producer] >= 0 &&
+        P.groups[P.group_of[x.producer]].output != t)
+      L.internal[t] = 1;
+  }
+  return L;
 }
 
 }  // namespace tnq

@@ -70,6 +70,7 @@ struct PTensor {
   int producer = -1;    // bucket index for results
   int consumer = -1;    // bucket index that reads it (-1: a final scalar)
   bool dep_slice = false, dep_bits = false;
+  bool wide_range = false;  // leaf with a nonzero entry of magnitude outside [2^-4, 2^4]
   int rank() const { return (int)vars.size(); }
 };
 
@@ -82,17 +83,58 @@ struct PBucket {
   int k = 0;                 // tensors multiplied
 };
 
+// A chain of buckets b_1 -> b_2 -> ... -> b_m (each result consumed by the
+// next) executed as one kernel: a block fixes the tile variables and runs the
+// m eliminations over the local variables in shared memory, so the chain's
+// intermediate results never reach HBM. Exact: Sum_{u_1..u_m} of the product
+// of every tensor the chain reads (Eq. 2 applied m times, regrouped).
+constexpr int GL_MAX = 13;   // local variables of a group (stage outputs have <= 12 local bits)
+constexpr int GM_MAX = 8;    // buckets per group
+constexpr int GL_OUT_MIN = 8;  // output variables a group keeps local (>= one entry per thread in the last stage)
+constexpr int GIN_MAX = 16;  // tensors a group reads from memory
+
+struct FusedGroup {
+  std::vector<int> buckets;     // chain order; the group runs at the last bucket's position
+  std::vector<int> local_vars;  // L: the eliminated variables + the earliest output variables, by position
+  std::vector<int> tile_vars;   // H: the other output variables, by position
+  std::vector<int> ext_inputs;  // tensors read from memory, in stage order
+  int output = -1;              // result of the last bucket
+};
+
 struct Program {
   std::vector<PTensor> tensors;
   std::vector<PBucket> buckets;
+  std::vector<FusedGroup> groups;
+  std::vector<int> group_of;        // per bucket: group index or -1
   std::vector<int> leaves;          // tensor ids of leaves with at least one free variable
   std::vector<int> scalar_leaves;   // network tensor ids fully fixed (rank 0)
   std::vector<int> finals;          // tensor ids of rank-0 bucket results
   double flops_per_slice = 0, bytes_per_slice = 0;
+  double bytes_unfused = 0;  // bytes_per_slice with no fused group
   int max_bag = 0;
 };
 
+// Replaces the program's fused groups (recomputes group_of and bytes_per_slice).
+void set_groups(Program& prog, const std::vector<FusedGroup>& groups);
+
 // Compiles the bucket program for the reduced order (free ids) and sliced set.
 Program compile_program(const Network& net, const std::vector<int>& order, const std::vector<int>& mu);
+
+// Fusion pass (stages inside a group are not renormalised, so chains that
+// read a wide-range leaf stay unfused): chains of summing buckets whose results are at least
+// 2^min_rank entries become fused groups when no new variable enters along
+// the chain (the group's product space stays the first bucket's bag) and the
+// chain fits GM_MAX / GIN_MAX / GL_MAX. Updates bytes_per_slice. min_rank <= 0
+// disables fusion.
+void fuse_chains(Program& prog, const std::vector<int>& order, int min_rank);
+
+// Bucket index at which a tensor is produced / consumed once groups are
+// formed (a group's buckets all count as its last bucket); -1 / n_buckets for
+// leaves / final scalars. `internal` tensors (inside a group) are never stored.
+struct Liveness {
+  std::vector<int> lo, hi;
+  std::vector<char> internal;
+};
+Liveness tensor_liveness(const Program& prog);
 
 }  // namespace tnq

@@ -18,6 +18,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <map>
 #include <string>
@@ -298,6 +299,234 @@ __global__ void __launch_bounds__(TPB) k_bucket(const __grid_constant__ KParams 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Fused chain of buckets (FusedGroup). A block fixes the tile variables H (and
+// the item); stage s eliminates u_s over the local variables in shared memory:
+//   stage_s[c] = sum_{u_s} prod_j in_j[c, u_s],
+// where in_j is a tensor read from memory at the block's H, or the previous
+// stage's buffer. Offsets are linear in the bits of the stage's local index c:
+// bits < 8 via a per-thread table, bits >= 8 via a per-iteration table.
+constexpr int GH_MAX = 48;  // tile bits (output variables outside the block + item bits)
+constexpr int GROUP_SMEM_BYTES = (1 << (GL_MAX - 1)) * 3 / 2 * (int)sizeof(float2);  // regions A + B
+
+struct GIn {
+  const float2* ptr;
+  long long istride;           // per item (0 if the tensor is item-invariant)
+  long long hstride[GH_MAX];   // per tile bit
+  int meta;                    // meta row (-1 for leaves)
+  int dep;
+};
+
+struct GSt {
+  int n_in;
+  int n_var;                   // inputs 0..n_var-1 vary over the local bits; the rest are per-block constants
+  int nbits;                   // local output bits of the stage
+  int src[KMAX];               // -1: previous stage buffer, else index into gin
+  int cstride[KMAX][GL_MAX];   // element stride of local output bit b, per input
+  int ustride[KMAX];           // stride of the eliminated variable, per input
+};
+
+struct GParams {
+  GSt st[GM_MAX];
+  GIn gin[GIN_MAX];
+  float2* out;
+  long long out_istride;
+  long long out_hstride[GH_MAX];
+  int out_cstride[GL_MAX];
+  int n_st, n_gin, n_h, out_meta, out_dep, B;
+  int* meta_e;
+  unsigned* meta_m;
+};
+
+// One stage of a fused group. Inputs n_var.. do not vary over the block's
+// local bits: their (u=0, u=1) pairs, times the stage's power-of-two scales,
+// are multiplied once into a constant pair. Each thread handles local entries
+// c = t + 256 it; per entry only the NV varying operands are loaded (one
+// 16-byte load each: the eliminated variable is bit 0 of every operand).
+template <int NV>
+__device__ __forceinline__ void group_stage(const GParams& P, const GSt& S, int t, const float2* prev, float2* cur,
+                                            bool last, const long long* s_base, const float* s_scale,
+                                            int (*s_hi)[32], const int* s_out_hi, long long out_base, int out_lo,
+                                            float* tmax) {
+  const int nb = S.nbits;
+  const int n_hi = nb > 8 ? (1 << (nb - 8)) : 1;
+  const int nent = 1 << nb;
+  float F = 1.f;
+  for (int j = 0; j < S.n_in; ++j)
+    if (S.src[j] >= 0) F *= s_scale[S.src[j]];
+  float2 k0 = make_float2(F, 0.f), k1 = make_float2(F, 0.f);
+  for (int j = NV; j < S.n_in; ++j) {
+    const float2* p = S.src[j] < 0 ? prev : P.gin[S.src[j]].ptr + s_base[S.src[j]];
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    k0 = cmul(k0, make_float2(v.x, v.y));
+    k1 = cmul(k1, make_float2(v.z, v.w));
+  }
+  const float2* ptr[NV > 0 ? NV : 1];
+  int lo[NV > 0 ? NV : 1];
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    const int src = S.src[j];
+    ptr[j] = src < 0 ? prev : P.gin[src].ptr + s_base[src];
+    int a = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      if (i < nb && ((t >> i) & 1)) a += S.cstride[j][i];
+    lo[j] = a;
+  }
+#pragma unroll 2
+  for (int it = 0; it < n_hi; ++it) {
+    const int c = t + (it << 8);
+    if (c < nent) {
+      float2 p0 = k0, p1 = k1;
+#pragma unroll
+      for (int j = 0; j < NV; ++j) {
+        const float4 v = *reinterpret_cast<const float4*>(ptr[j] + lo[j] + s_hi[j][it]);
+        p0 = cmul(p0, make_float2(v.x, v.y));
+        p1 = cmul(p1, make_float2(v.z, v.w));
+      }
+      const float2 r = make_float2(p0.x + p1.x, p0.y + p1.y);
+      if (last) {
+        P.out[out_base + out_lo + s_out_hi[it]] = r;
+        *tmax = fmaxf(*tmax, fmaxf(fabsf(r.x), fabsf(r.y)));
+      } else {
+        cur[c] = r;
+      }
+    }
+  }
+}
+
+// Persistent fused-group kernel: every block builds the stage tables once,
+// then loops over tiles (item, H assignment) tile = blockIdx.x + k*gridDim.x.
+__global__ void __launch_bounds__(TPB) k_group(const __grid_constant__ GParams P, long long n_tiles) {
+  extern __shared__ float2 g_stage[];  // stage regions A (2^(GL_MAX-1) entries) and B (half of A)
+  __shared__ long long s_hstr[GIN_MAX + 1][GH_MAX];  // row GIN_MAX: the output
+  __shared__ long long s_base[GIN_MAX];
+  __shared__ float s_scale[GIN_MAX];
+  __shared__ int s_e[GIN_MAX];
+  __shared__ int s_hi[GM_MAX][KMAX][32];
+  __shared__ int s_out_hi[32];
+  __shared__ long long s_out_base;
+  __shared__ float s_red[TPB / 32];
+  const int t = threadIdx.x;
+  // tables shared by every tile
+  for (int e = t; e < (GIN_MAX + 1) * GH_MAX; e += TPB) {
+    const int j = e / GH_MAX, i = e - j * GH_MAX;
+    long long v = 0;
+    if (i < P.n_h) v = (j < P.n_gin) ? P.gin[j].hstride[i] : (j == GIN_MAX ? P.out_hstride[i] : 0ll);
+    s_hstr[j][i] = v;
+  }
+  for (int s = 0; s < P.n_st; ++s) {
+    const GSt& S = P.st[s];
+    const int nb = S.nbits;
+    const int n_hi = nb > 8 ? (1 << (nb - 8)) : 1;
+    for (int e = t; e < S.n_var * n_hi; e += TPB) {
+      const int j = e / n_hi, it = e - j * n_hi;
+      int a = 0;
+      for (int i = 8; i < nb; ++i)
+        if ((it >> (i - 8)) & 1) a += S.cstride[j][i];
+      s_hi[s][j][it] = a;
+    }
+  }
+  const GSt& SL = P.st[P.n_st - 1];
+  const int nb_last = SL.nbits;
+  const int n_hi_last = nb_last > 8 ? (1 << (nb_last - 8)) : 1;
+  for (int it = t; it < n_hi_last; it += TPB) {
+    int a = 0;
+    for (int i = 8; i < nb_last; ++i)
+      if ((it >> (i - 8)) & 1) a += P.out_cstride[i];
+    s_out_hi[it] = a;
+  }
+  int out_lo = 0;
+  for (int i = 0; i < 8 && i < nb_last; ++i)
+    if ((t >> i) & 1) out_lo += P.out_cstride[i];
+  const int buf_elems = 1 << (GL_MAX - 1);
+  long long cur_item = -1;
+  float tmax = 0.f;
+  for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const long long item = tile >> P.n_h;
+    const long long h = tile & ((1ll << P.n_h) - 1ll);
+    if (item != cur_item) {
+      if (cur_item >= 0) {  // flush the previous item's max
+        float m = tmax;
+        for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+        __syncthreads();
+        if ((t & 31) == 0) s_red[t >> 5] = m;
+        __syncthreads();
+        if (t == 0) {
+          float b = 0.f;
+          for (int w = 0; w < TPB / 32; ++w) b = fmaxf(b, s_red[w]);
+          if (b > 0.f) atomic_max_pos(&P.meta_m[(long long)P.out_meta * P.B + (P.out_dep ? cur_item : 0ll)], b);
+        }
+      }
+      tmax = 0.f;
+      cur_item = item;
+    }
+    __syncthreads();  // previous tile done with s_base / stage buffers
+    if (t < P.n_gin) {
+      const GIn& g = P.gin[t];
+      long long b = g.dep ? item * g.istride : 0ll;
+      for (int i = 0; i < P.n_h; ++i)
+        if ((h >> i) & 1ll) b += s_hstr[t][i];
+      s_base[t] = b;
+      if (g.meta < 0) {
+        s_scale[t] = 1.f;
+        s_e[t] = 0;
+      } else {
+        const long long row = (long long)g.meta * P.B + (g.dep ? item : 0ll);
+        int m;
+        s_scale[t] = scale_of_max(P.meta_m[row], &m);
+        s_e[t] = P.meta_e[row] + m;
+      }
+    }
+    if (t == TPB - 1) {
+      long long b = P.out_dep ? item * P.out_istride : 0ll;
+      for (int i = 0; i < P.n_h; ++i)
+        if ((h >> i) & 1ll) b += s_hstr[GIN_MAX][i];
+      s_out_base = b;
+    }
+    __syncthreads();
+    // stage s writes region A (even s) or B (odd s); every stage output has at
+    // least one bit fewer than the stage before, so B needs half of A
+    float2* prev = g_stage + buf_elems;
+    float2* cur = g_stage;
+    for (int s = 0; s < P.n_st; ++s) {
+      const GSt& S = P.st[s];
+      const bool last = (s == P.n_st - 1);
+      switch (S.n_var) {
+        case 0: group_stage<0>(P, S, t, prev, cur, last, s_base, s_scale, s_hi[s], s_out_hi, s_out_base, out_lo, &tmax); break;
+        case 1: group_stage<1>(P, S, t, prev, cur, last, s_base, s_scale, s_hi[s], s_out_hi, s_out_base, out_lo, &tmax); break;
+        case 2: group_stage<2>(P, S, t, prev, cur, last, s_base, s_scale, s_hi[s], s_out_hi, s_out_base, out_lo, &tmax); break;
+        case 3: group_stage<3>(P, S, t, prev, cur, last, s_base, s_scale, s_hi[s], s_out_hi, s_out_base, out_lo, &tmax); break;
+        case 4: group_stage<4>(P, S, t, prev, cur, last, s_base, s_scale, s_hi[s], s_out_hi, s_out_base, out_lo, &tmax); break;
+        case 5: group_stage<5>(P, S, t, prev, cur, last, s_base, s_scale, s_hi[s], s_out_hi, s_out_base, out_lo, &tmax); break;
+        case 6: group_stage<6>(P, S, t, prev, cur, last, s_base, s_scale, s_hi[s], s_out_hi, s_out_base, out_lo, &tmax); break;
+        case 7: group_stage<7>(P, S, t, prev, cur, last, s_base, s_scale, s_hi[s], s_out_hi, s_out_base, out_lo, &tmax); break;
+        default: group_stage<8>(P, S, t, prev, cur, last, s_base, s_scale, s_hi[s], s_out_hi, s_out_base, out_lo, &tmax); break;
+      }
+      if (!last) __syncthreads();
+      float2* tmp = prev;
+      prev = cur;
+      cur = tmp;
+    }
+    if (h == 0 && t == 0) {
+      int e = 0;
+      for (int j = 0; j < P.n_gin; ++j) e += s_e[j];
+      P.meta_e[(long long)P.out_meta * P.B + (P.out_dep ? item : 0ll)] = e;
+    }
+  }
+  // flush the last item's max
+  float m = tmax;
+  for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+  __syncthreads();
+  if ((t & 31) == 0) s_red[t >> 5] = m;
+  __syncthreads();
+  if (t == 0 && cur_item >= 0) {
+    float b = 0.f;
+    for (int w = 0; w < TPB / 32; ++w) b = fmaxf(b, s_red[w]);
+    if (b > 0.f) atomic_max_pos(&P.meta_m[(long long)P.out_meta * P.B + (P.out_dep ? cur_item : 0ll)], b);
+  }
+}
+
 // K4: amplitude of every item = scalar leaves * final scalars * 2^(exponents),
 // then the FP64 sum of each bitstring's items of this batch in item order.
 __global__ void k_finalize(const FinalDev* __restrict__ fin, int n_fin, const double2* __restrict__ item_scalar,
@@ -386,18 +615,19 @@ Layout make_layout(const tnq_plan& P, int mode, int B) {
   L.off.assign(T, 0);
   L.dep.assign(T, 0);
   for (int t = 0; t < T; ++t) L.dep[t] = tensor_dep(prog.tensors[t], mode);
-  // lifetimes in bucket steps
-  const int nb = (int)prog.buckets.size();
-  std::vector<int> lo(T), hi(T);
+  // lifetimes in bucket steps (a fused group's tensors live at its last bucket;
+  // the results inside a group are never stored)
+  const Liveness LV = tensor_liveness(prog);
+  const std::vector<int>& lo = LV.lo;
+  const std::vector<int>& hi = LV.hi;
   std::vector<long long> size(T);
   for (int t = 0; t < T; ++t) {
     const PTensor& x = prog.tensors[t];
-    lo[t] = x.producer;  // leaves: -1
-    hi[t] = x.consumer >= 0 ? x.consumer : nb;
-    size[t] = (long long)align_up(((size_t)1 << x.rank()) * (L.dep[t] ? (size_t)B : 1), 32);
+    size[t] = LV.internal[t] ? 0 : (long long)align_up(((size_t)1 << x.rank()) * (L.dep[t] ? (size_t)B : 1), 32);
   }
-  std::vector<int> idx(T);
-  for (int t = 0; t < T; ++t) idx[t] = t;
+  std::vector<int> idx;
+  for (int t = 0; t < T; ++t)
+    if (!LV.internal[t]) idx.push_back(t);
   std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return size[a] > size[b]; });
   std::vector<int> placed;
   for (int t : idx) {
@@ -443,8 +673,13 @@ struct ExecConfig {
   int n_inout = 0;
   FinalDev* d_finals = nullptr;
   int n_finals = 0;
-  std::vector<KParams> kp;           // per bucket (pointers filled per workspace)
-  std::vector<std::pair<int, int>> kshape;  // (n_in, LT) per bucket
+  std::vector<KParams> kp;           // per single-bucket step (pointers filled per workspace)
+  std::vector<std::pair<int, int>> kshape;  // (n_in, LT) per single-bucket step
+  std::vector<GParams> gp;           // per fused-group step
+  std::vector<int> gsmem;            // dynamic shared memory bytes per fused-group step
+  int group_grid = 152 * 4;          // persistent blocks of k_group (SMs x resident blocks)
+  std::vector<std::pair<int, int>> steps;  // (0, index into kp) or (1, index into gp), program order
+  std::vector<double> step_bytes;    // algorithmic bytes of each step (all items)
   void* ws = nullptr;                // workspace the graph was captured for
   cudaGraphExec_t exec = nullptr;
 };
@@ -498,42 +733,206 @@ static LeafDev make_leafdev(const tnq_plan& P, const PTensor* pt, int gate, cons
   return d;
 }
 
-// Bucket kernel parameters of one configuration, with pointers holding byte
-// offsets from the arena base (rebased per call). Host only.
-static bool build_kparams(const tnq_plan& P, const Layout& L, std::vector<KParams>& kp,
-                          std::vector<std::pair<int, int>>& kshape) {
+// Kernel parameters of every step of one configuration (single buckets and
+// fused groups, in program order), with pointers holding byte offsets from the
+// arena base (rebased per call). Host only.
+static KParams single_kparams(const tnq_plan& P, const Layout& L, const PBucket& b, bool* ok) {
   const Program& prog = P.prog;
-  kp.clear();
-  kshape.clear();
-  for (const PBucket& b : prog.buckets) {
-    KParams k;
-    std::memset(&k, 0, sizeof(k));
-    const PTensor& o = prog.tensors[b.output];
-    const bool odep = L.dep[b.output];
-    k.out_bits = o.rank();
-    k.G = k.out_bits + (odep ? L.item_bits : 0);
-    if (k.G >= GMAX || b.k > KMAX) {
-      set_error("bucket too large for one launch");
+  KParams k;
+  std::memset(&k, 0, sizeof(k));
+  const PTensor& o = prog.tensors[b.output];
+  const bool odep = L.dep[b.output];
+  k.out_bits = o.rank();
+  k.G = k.out_bits + (odep ? L.item_bits : 0);
+  *ok = k.G < GMAX && b.k <= KMAX;
+  if (!*ok) return k;
+  k.sum = b.sum ? 1 : 0;
+  k.B = L.B;
+  k.out_meta = b.output;
+  k.out = reinterpret_cast<float2*>((size_t)L.off[b.output] * 8);
+  for (int j = 0; j < b.k; ++j) {
+    const int tid = b.inputs[j];
+    const PTensor& x = prog.tensors[tid];
+    k.in[j] = reinterpret_cast<const float2*>((size_t)L.off[tid] * 8);
+    k.in_meta[j] = x.leaf_gate >= 0 ? -1 : tid;
+    k.in_dep[j] = L.dep[tid];
+    for (int i = 0; i < k.out_bits; ++i) {
+      auto it = std::find(x.vars.begin(), x.vars.end(), o.vars[i]);
+      k.stride[j][i] = it == x.vars.end() ? 0 : (1ll << (it - x.vars.begin()));
+    }
+    for (int i = k.out_bits; i < k.G; ++i) k.stride[j][i] = L.dep[tid] ? ((1ll << x.rank()) << (i - k.out_bits)) : 0;
+  }
+  return k;
+}
+
+static int index_in(const std::vector<int>& v, int x) {
+  auto it = std::find(v.begin(), v.end(), x);
+  return it == v.end() ? -1 : (int)(it - v.begin());
+}
+
+// Local output variables of every stage of a group: (bag_s \ u_s) restricted
+// to the group's local variables, in position order.
+static std::vector<std::vector<int>> group_stage_vars(const Program& prog, const FusedGroup& g) {
+  std::vector<std::vector<int>> sv;
+  for (int b : g.buckets) {
+    const PBucket& B = prog.buckets[b];
+    std::vector<int> v;
+    for (int x : g.local_vars) {  // local_vars is sorted by position
+      if (x == B.u) continue;
+      bool in_bag = false;
+      for (int t : B.inputs) in_bag |= index_in(prog.tensors[t].vars, x) >= 0;
+      if (in_bag) v.push_back(x);
+    }
+    sv.push_back(v);
+  }
+  return sv;
+}
+
+static GParams group_gparams(const tnq_plan& P, const Layout& L, const FusedGroup& g, bool* ok, int* smem) {
+  const Program& prog = P.prog;
+  GParams G;
+  std::memset(&G, 0, sizeof(G));
+  *ok = false;
+  const PTensor& o = prog.tensors[g.output];
+  const int n_h = (int)g.tile_vars.size() + (L.dep[g.output] ? L.item_bits : 0);
+  if ((int)g.tile_vars.size() >= GH_MAX || (int)g.ext_inputs.size() > GIN_MAX || (int)g.buckets.size() > GM_MAX)
+    return G;
+  G.n_h = (int)g.tile_vars.size();  // item index is the tile index above these bits
+  (void)n_h;
+  G.n_st = (int)g.buckets.size();
+  G.n_gin = (int)g.ext_inputs.size();
+  G.B = L.B;
+  G.out_meta = g.output;
+  G.out_dep = L.dep[g.output];
+  G.out = reinterpret_cast<float2*>((size_t)L.off[g.output] * 8);
+  G.out_istride = 1ll << o.rank();
+  for (size_t i = 0; i < g.tile_vars.size(); ++i) {
+    const int p = index_in(o.vars, g.tile_vars[i]);
+    if (p < 0) return G;
+    G.out_hstride[i] = 1ll << p;
+  }
+  for (int j = 0; j < G.n_gin; ++j) {
+    const int tid = g.ext_inputs[j];
+    const PTensor& x = prog.tensors[tid];
+    GIn& gi = G.gin[j];
+    gi.ptr = reinterpret_cast<const float2*>((size_t)L.off[tid] * 8);
+    gi.dep = L.dep[tid];
+    gi.istride = 1ll << x.rank();
+    gi.meta = x.leaf_gate >= 0 ? -1 : tid;
+    for (size_t i = 0; i < g.tile_vars.size(); ++i) {
+      const int p = index_in(x.vars, g.tile_vars[i]);
+      gi.hstride[i] = p < 0 ? 0 : (1ll << p);
+    }
+  }
+  const auto sv = group_stage_vars(prog, g);
+  int maxbits = 0;
+  for (int s = 0; s < G.n_st; ++s) {
+    const PBucket& B = prog.buckets[g.buckets[s]];
+    GSt& S = G.st[s];
+    S.n_in = B.k;
+    S.nbits = (int)sv[s].size();
+    if (S.nbits > GL_MAX - 1 || B.k > KMAX) return G;
+    maxbits = std::max(maxbits, S.nbits);
+    // varying inputs first (any local stride), then the per-block constants
+    std::vector<int> ins(B.inputs.begin(), B.inputs.end());
+    auto varies = [&](int tid) {
+      if (s > 0 && tid == prog.buckets[g.buckets[s - 1]].output) return sv[s].size() > 0;
+      for (int x : sv[s])
+        if (index_in(prog.tensors[tid].vars, x) >= 0) return true;
       return false;
-    }
-    k.sum = b.sum ? 1 : 0;
-    k.B = L.B;
-    k.out_meta = b.output;
-    k.out = reinterpret_cast<float2*>((size_t)L.off[b.output] * 8);
-    for (int j = 0; j < b.k; ++j) {
-      const int tid = b.inputs[j];
-      const PTensor& x = prog.tensors[tid];
-      k.in[j] = reinterpret_cast<const float2*>((size_t)L.off[tid] * 8);
-      k.in_meta[j] = x.leaf_gate >= 0 ? -1 : tid;
-      k.in_dep[j] = L.dep[tid];
-      for (int i = 0; i < k.out_bits; ++i) {
-        auto it = std::find(x.vars.begin(), x.vars.end(), o.vars[i]);
-        k.stride[j][i] = it == x.vars.end() ? 0 : (1ll << (it - x.vars.begin()));
+    };
+    std::stable_partition(ins.begin(), ins.end(), varies);
+    S.n_var = 0;
+    for (int tid : ins) S.n_var += varies(tid) ? 1 : 0;
+    for (int j = 0; j < B.k; ++j) {
+      const int tid = ins[j];
+      if (s > 0 && tid == prog.buckets[g.buckets[s - 1]].output) {
+        S.src[j] = -1;
+        const auto& pv = sv[s - 1];
+        for (int b = 0; b < S.nbits; ++b) {
+          const int p = index_in(pv, sv[s][b]);
+          S.cstride[j][b] = p < 0 ? 0 : (1 << p);
+        }
+        const int pu = index_in(pv, B.u);
+        if (pu < 0) return G;
+        S.ustride[j] = 1 << pu;
+      } else {
+        S.src[j] = index_in(g.ext_inputs, tid);
+        if (S.src[j] < 0) return G;
+        const PTensor& x = prog.tensors[tid];
+        for (int b = 0; b < S.nbits; ++b) {
+          const int p = index_in(x.vars, sv[s][b]);
+          S.cstride[j][b] = p < 0 ? 0 : (1 << p);
+        }
+        const int pu = index_in(x.vars, B.u);
+        if (pu < 0) return G;
+        S.ustride[j] = 1 << pu;
       }
-      for (int i = k.out_bits; i < k.G; ++i) k.stride[j][i] = L.dep[tid] ? ((1ll << x.rank()) << (i - k.out_bits)) : 0;
     }
-    kp.push_back(k);
-    kshape.push_back({b.k, k.G > 8 ? 12 : 8});
+  }
+  const auto& last = sv[G.n_st - 1];
+  for (size_t b = 0; b < last.size(); ++b) {
+    const int p = index_in(o.vars, last[b]);
+    if (p < 0) return G;
+    G.out_cstride[b] = 1 << p;
+  }
+  if (last.size() + g.tile_vars.size() != o.vars.size()) return G;
+  *smem = GROUP_SMEM_BYTES;
+  (void)maxbits;
+  if (getenv("TNQ_DEBUG_GROUPS")) {
+    fprintf(stderr, "group out rank %d tile bits %d ext %d\n", o.rank(), G.n_h, G.n_gin);
+    for (int s2 = 0; s2 < G.n_st; ++s2) {
+      fprintf(stderr, "  stage %d nbits %d:", s2, G.st[s2].nbits);
+      for (int j = 0; j < G.st[s2].n_in; ++j) {
+        const int src = G.st[s2].src[j];
+        fprintf(stderr, " [%s r%d u%d c:", src < 0 ? "chain" : "in", src < 0 ? -1 : prog.tensors[g.ext_inputs[src]].rank(),
+                G.st[s2].ustride[j]);
+        for (int b2 = 0; b2 < G.st[s2].nbits; ++b2) fprintf(stderr, "%d,", G.st[s2].cstride[j][b2]);
+        fprintf(stderr, "]");
+      }
+      fprintf(stderr, "\n");
+    }
+    fprintf(stderr, "  out c:");
+    for (int b2 = 0; b2 < G.st[G.n_st - 1].nbits; ++b2) fprintf(stderr, "%d,", G.out_cstride[b2]);
+    fprintf(stderr, "\n");
+  }
+  *ok = true;
+  return G;
+}
+
+static bool build_steps(const tnq_plan& P, const Layout& L, ExecConfig& C) {
+  const Program& prog = P.prog;
+  C.kp.clear();
+  C.kshape.clear();
+  C.gp.clear();
+  C.gsmem.clear();
+  C.steps.clear();
+  C.step_bytes.clear();
+  auto tbytes = [&](int t) { return std::ldexp(8.0, prog.tensors[t].rank()) * (L.dep[t] ? L.B : 1); };
+  for (size_t bi = 0; bi < prog.buckets.size(); ++bi) {
+    const int gi = prog.group_of.empty() ? -1 : prog.group_of[bi];
+    if (gi < 0) {
+      bool ok;
+      KParams k = single_kparams(P, L, prog.buckets[bi], &ok);
+      if (!ok) { set_error("bucket too large for one launch"); return false; }
+      C.steps.push_back({0, (int)C.kp.size()});
+      C.kp.push_back(k);
+      C.kshape.push_back({prog.buckets[bi].k, k.G > 8 ? 12 : 8});
+      double by = tbytes(prog.buckets[bi].output);
+      for (int t : prog.buckets[bi].inputs) by += tbytes(t);
+      C.step_bytes.push_back(by);
+    } else if ((int)bi == prog.groups[gi].buckets.back()) {
+      bool ok;
+      int smem = 0;
+      GParams g = group_gparams(P, L, prog.groups[gi], &ok, &smem);
+      if (!ok) { set_error("fused group does not fit one launch"); return false; }
+      C.steps.push_back({1, (int)C.gp.size()});
+      C.gp.push_back(g);
+      C.gsmem.push_back(smem);
+      double by = tbytes(prog.groups[gi].output);
+      for (int t : prog.groups[gi].ext_inputs) by += tbytes(t);
+      C.step_bytes.push_back(by);
+    }
   }
   return true;
 }
@@ -544,15 +943,20 @@ static bool build_kparams(const tnq_plan& P, const Layout& L, std::vector<KParam
 // do not overlap. Returns an empty string when everything holds.
 static std::string validate_config(const tnq_plan& P, int mode, int B) {
   const Layout L = make_layout(P, mode, B);
-  std::vector<KParams> kp;
-  std::vector<std::pair<int, int>> ks;
-  if (!build_kparams(P, L, kp, ks)) return "build_kparams failed";
+  ExecConfig C;
+  C.L = L;
+  if (!build_steps(P, L, C)) return "build_steps failed";
   const Program& prog = P.prog;
+  const Liveness LV = tensor_liveness(prog);
   auto alloc = [&](int t) { return ((long long)1 << prog.tensors[t].rank()) * (L.dep[t] ? B : 1); };
+  auto off_of = [&](const void* p) { return (long long)((size_t)p / 8); };
+  int single = 0;
   for (size_t bi = 0; bi < prog.buckets.size(); ++bi) {
+    if (!prog.group_of.empty() && prog.group_of[bi] >= 0) continue;
     const PBucket& b = prog.buckets[bi];
-    const KParams& k = kp[bi];
+    const KParams& k = C.kp[single++];
     if ((1ll << k.G) > alloc(b.output)) return "bucket " + std::to_string(bi) + ": output overflows";
+    if (off_of(k.out) != L.off[b.output]) return "bucket output pointer";
     for (int j = 0; j < b.k; ++j) {
       long long mx = 0;
       for (int i = 0; i < k.G; ++i) mx += k.stride[j][i];
@@ -563,25 +967,89 @@ static std::string validate_config(const tnq_plan& P, int mode, int B) {
         if (k.sum && (k.stride[j][i] & 1)) return "odd stride in a summing bucket";
     }
   }
+  for (size_t gi = 0; gi < C.gp.size(); ++gi) {
+    const GParams& G = C.gp[gi];
+    const FusedGroup& g = prog.groups[gi];
+    const long long items = G.out_dep ? B : 1;
+    // largest index of every memory operand over all tiles, items and stages
+    std::vector<long long> in_max(G.n_gin, 0);
+    for (int j = 0; j < G.n_gin; ++j) {
+      long long m = G.gin[j].dep ? (items - 1) * G.gin[j].istride : 0;
+      for (int i = 0; i < G.n_h; ++i) m += G.gin[j].hstride[i];
+      in_max[j] = m;
+    }
+    std::vector<long long> chain_max(G.n_st, 0);
+    for (int s = 0; s < G.n_st; ++s) {
+      const GSt& S = G.st[s];
+      if (S.nbits > GL_MAX - 1 || S.n_in > KMAX || S.n_in < 1) return "group stage shape";
+      for (int j = 0; j < S.n_in; ++j) {
+        // pair loads: u at bit 0 (stride 1) and every other stride even
+        if (S.ustride[j] != 1) return "group " + std::to_string(gi) + ": eliminated variable not at bit 0";
+        if (j >= S.n_var)
+          for (int b = 0; b < S.nbits; ++b)
+            if (S.cstride[j][b]) return "group " + std::to_string(gi) + ": constant input varies";
+        for (int b = 0; b < S.nbits; ++b)
+          if (S.cstride[j][b] & 1) return "group " + std::to_string(gi) + ": odd local stride";
+        if (S.src[j] >= 0) {
+          const GIn& in = G.gin[S.src[j]];
+          if ((in.istride & 1) || ((size_t)in.ptr / 8) % 2) return "group input base not even";
+          for (int i = 0; i < G.n_h; ++i)
+            if (in.hstride[i] & 1) return "group " + std::to_string(gi) + ": odd tile stride";
+        }
+        long long m = S.ustride[j];
+        for (int b = 0; b < S.nbits; ++b) m += S.cstride[j][b];
+        if (S.src[j] < 0) {
+          if (s == 0) return "chain input in the first stage";
+          if (m >= (1ll << G.st[s - 1].nbits)) return "group " + std::to_string(gi) + ": stage buffer overflow";
+        } else {
+          if (S.src[j] >= G.n_gin) return "group input index";
+          if (in_max[S.src[j]] + m >= alloc(g.ext_inputs[S.src[j]]))
+            return "group " + std::to_string(gi) + ": input " + std::to_string(j) + " overflows";
+        }
+      }
+    }
+    long long om = G.out_dep ? (items - 1) * G.out_istride : 0;
+    for (int i = 0; i < G.n_h; ++i) om += G.out_hstride[i];
+    for (int b = 0; b < G.st[G.n_st - 1].nbits; ++b) om += G.out_cstride[b];
+    if (om >= alloc(g.output)) return "group " + std::to_string(gi) + ": output overflows";
+    if (C.gsmem[gi] > 200 * 1024) return "group shared memory";
+  }
   const int T = (int)prog.tensors.size();
-  const int nb = (int)prog.buckets.size();
   for (int t = 0; t < T; ++t) {
+    if (LV.internal[t]) continue;
     if (L.off[t] < 0 || L.off[t] + alloc(t) > L.arena_elems) return "tensor outside arena";
     if (L.off[t] % 32) return "tensor offset not 256-byte aligned";
   }
   for (int a = 0; a < T; ++a)
     for (int c = a + 1; c < T; ++c) {
-      const PTensor &x = prog.tensors[a], &y = prog.tensors[c];
-      const int la = x.producer, ha = x.consumer >= 0 ? x.consumer : nb;
-      const int lc = y.producer, hc = y.consumer >= 0 ? y.consumer : nb;
-      if (la <= hc && lc <= ha && L.off[a] < L.off[c] + alloc(c) && L.off[c] < L.off[a] + alloc(a))
+      if (LV.internal[a] || LV.internal[c]) continue;
+      if (LV.lo[a] <= LV.hi[c] && LV.lo[c] <= LV.hi[a] && L.off[a] < L.off[c] + alloc(c) &&
+          L.off[c] < L.off[a] + alloc(a))
         return "live tensors " + std::to_string(a) + " and " + std::to_string(c) + " overlap";
     }
   return "";
 }
 
+static cudaError_t allow_group_smem() {
+  return cudaFuncSetAttribute(k_group, cudaFuncAttributeMaxDynamicSharedMemorySize, GROUP_SMEM_BYTES);
+}
+
+static tnq_status group_grid_size(int* out) {
+  int dev = 0, sms = 0, per_sm = 0;
+  CU(cudaGetDevice(&dev));
+  CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_group, TPB, GROUP_SMEM_BYTES));
+  *out = std::max(1, sms * std::max(1, per_sm));
+  return TNQ_OK;
+}
+
 static tnq_status build_config(const tnq_plan& P, int mode, int B, ExecConfig** out) {
+  CU(allow_group_smem());
+  int ggrid = 0;
+  tnq_status gst = group_grid_size(&ggrid);
+  if (gst != TNQ_OK) return gst;
   ExecConfig* C = new ExecConfig();
+  C->group_grid = ggrid;
   C->L = make_layout(P, mode, B);
   const Program& prog = P.prog;
   std::vector<LeafDev> leaves, scalars;
@@ -612,7 +1080,7 @@ static tnq_status build_config(const tnq_plan& P, int mode, int B, ExecConfig** 
     delete C;
     return TNQ_ECUDA;
   }
-  if (!build_kparams(P, C->L, C->kp, C->kshape)) {
+  if (!build_steps(P, C->L, *C)) {
     cudaFree(C->d_leaves);
     cudaFree(C->d_scalars);
     cudaFree(C->d_inout);
@@ -647,6 +1115,31 @@ static void launch_bucket(const KParams& k, int n_in, int LT, cudaStream_t s) {
   }
 }
 
+// Launches step i of the configuration (a single bucket or a fused group)
+// with its pointers rebased on the arena.
+static void launch_step(const ExecConfig& C, int i, float2* arena, int* me, unsigned* mm, cudaStream_t s) {
+  char* base = reinterpret_cast<char*>(arena);
+  const auto st = C.steps[i];
+  if (st.first == 0) {
+    KParams k = C.kp[st.second];
+    k.out = reinterpret_cast<float2*>(base + reinterpret_cast<size_t>(k.out));
+    for (int j = 0; j < C.kshape[st.second].first; ++j)
+      k.in[j] = reinterpret_cast<const float2*>(base + reinterpret_cast<size_t>(k.in[j]));
+    k.meta_e = me;
+    k.meta_m = mm;
+    launch_bucket(k, C.kshape[st.second].first, C.kshape[st.second].second, s);
+  } else {
+    GParams g = C.gp[st.second];
+    g.out = reinterpret_cast<float2*>(base + reinterpret_cast<size_t>(g.out));
+    for (int j = 0; j < g.n_gin; ++j) g.gin[j].ptr = reinterpret_cast<const float2*>(base + reinterpret_cast<size_t>(g.gin[j].ptr));
+    g.meta_e = me;
+    g.meta_m = mm;
+    const long long tiles = (g.out_dep ? (long long)g.B : 1ll) << g.n_h;
+    const long long grid = std::min<long long>(tiles, (long long)C.group_grid);
+    k_group<<<(unsigned)grid, TPB, C.gsmem[st.second], s>>>(g, tiles);
+  }
+}
+
 // Enqueues one batch (everything after the header upload) on stream s.
 static void enqueue_batch(const tnq_plan& P, ExecConfig& C, char* ws, cudaStream_t s) {
   const Layout& L = C.L;
@@ -666,15 +1159,7 @@ static void enqueue_batch(const tnq_plan& P, ExecConfig& C, char* ws, cudaStream
     k_leaf_init<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(C.d_leaves, C.n_leaves, hdr, bits, arena, B);
   }
   k_scalar_init<<<(B + 127) / 128, 128, 0, s>>>(C.d_scalars, C.n_scalars, C.d_inout, C.n_inout, hdr, bits, scal, B);
-  for (size_t i = 0; i < C.kp.size(); ++i) {
-    KParams k = C.kp[i];
-    k.out = reinterpret_cast<float2*>(reinterpret_cast<char*>(arena) + reinterpret_cast<size_t>(k.out));
-    for (int j = 0; j < C.kshape[i].first; ++j)
-      k.in[j] = reinterpret_cast<const float2*>(reinterpret_cast<const char*>(arena) + reinterpret_cast<size_t>(k.in[j]));
-    k.meta_e = me;
-    k.meta_m = mm;
-    launch_bucket(k, C.kshape[i].first, C.kshape[i].second, s);
-  }
+  for (size_t i = 0; i < C.steps.size(); ++i) launch_step(C, (int)i, arena, me, mm, s);
   const double sc = P.amp_scale_log2;  // = -n_sqrt2 / 2
   const int n_sqrt2 = (int)std::lround(-2.0 * sc);
   const int scale_exp = -(n_sqrt2 / 2), scale_half = n_sqrt2 & 1;
@@ -817,22 +1302,34 @@ int tnq_internal_validate(const tnq_plan* plan, int mode, uint32_t batch, char* 
 // CUDA event pair around every bucket launch on `stream`. Per bucket it
 // returns the launch time (ms), the algorithmic bytes of the launch (every
 // operand read once, the output written once; 8 B per complex64) and the bag
-// size r. *out_n = number of bucket launches, *out_B = batch used.
-int tnq_internal_profile(const tnq_plan* plan, const uint8_t* bits, uint64_t s0, uint64_t s1, void* workspace,
-                         size_t ws_bytes, uint32_t max_batch, void* stream, int cap, float* ms, double* bytes,
-                         int* bag, int* out_n, int* out_B) {
-  if (!plan || !bits || !workspace || s1 <= s0 || s1 > (1ull << plan->mu.size())) return TNQ_EINVAL;
+// size r (of the first bucket for a fused group) and the kind (0: one bucket,
+// m > 1: a fused group of m buckets). *out_n = launches, *out_B = batch used.
+}  // extern "C"
+
+namespace tnq {
+// Runs the first batch of tnq_contract_sliced(plan, bits, s0, s1, ...) with
+// direct launches and a CUDA event pair around every step; returns per-step
+// times (ms) and the configuration used.
+static tnq_status profile_steps(const tnq_plan* plan, const uint8_t* bits, uint64_t s0, uint64_t s1, void* workspace,
+                                size_t ws_bytes, uint32_t max_batch, void* stream, std::vector<float>& ms,
+                                ExecConfig** cfg) {
+  if (!plan || !bits || !workspace || s1 <= s0 || s1 > (1ull << plan->mu.size())) {
+    set_error("bad profile arguments");
+    return TNQ_EINVAL;
+  }
   tnq_status st = check_device();
   if (st != TNQ_OK) return st;
   uint64_t cap_b = 1;
   while (cap_b < s1 - s0 && cap_b < (1ull << MAX_ITEM_BITS)) cap_b <<= 1;
   if (max_batch > 0) cap_b = std::min<uint64_t>(cap_b, 1ull << ilog2_floor(max_batch));
   const int B = pick_batch(*plan, 0, ws_bytes, cap_b);
-  if (B == 0) return TNQ_ENOMEM;
+  if (B == 0) {
+    set_error("workspace too small for one slice");
+    return TNQ_ENOMEM;
+  }
   ExecConfig* C = nullptr;
   if ((st = get_config(*plan, 0, B, &C)) != TNQ_OK) return st;
-  const int nbk = (int)C->kp.size();
-  if (cap < nbk) return TNQ_EINVAL;
+  const int nbk = (int)C->steps.size();
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   char* ws = reinterpret_cast<char*>(workspace);
   std::vector<unsigned> words((size_t)C->L.n_words * C->L.n_rows, 0u);
@@ -860,38 +1357,128 @@ int tnq_internal_profile(const tnq_plan* plan, const uint8_t* bits, uint64_t s0,
   std::vector<cudaEvent_t> ev(2 * (size_t)nbk);
   for (auto& e : ev) CU(cudaEventCreate(&e));
   for (int i = 0; i < nbk; ++i) {
-    KParams k = C->kp[i];
-    k.out = reinterpret_cast<float2*>(reinterpret_cast<char*>(arena) + reinterpret_cast<size_t>(k.out));
-    for (int j = 0; j < C->kshape[i].first; ++j)
-      k.in[j] = reinterpret_cast<const float2*>(reinterpret_cast<const char*>(arena) + reinterpret_cast<size_t>(k.in[j]));
-    k.meta_e = me;
-    k.meta_m = mm;
     CU(cudaEventRecord(ev[2 * i], s));
-    launch_bucket(k, C->kshape[i].first, C->kshape[i].second, s);
+    launch_step(*C, i, arena, me, mm, s);
     CU(cudaEventRecord(ev[2 * i + 1], s));
   }
   CU(cudaGetLastError());
   CU(cudaStreamSynchronize(s));
-  const Program& prog = plan->prog;
-  for (int i = 0; i < nbk; ++i) {
-    float t = 0;
-    CU(cudaEventElapsedTime(&t, ev[2 * i], ev[2 * i + 1]));
-    const PBucket& b = prog.buckets[i];
-    double by = std::ldexp(8.0, prog.tensors[b.output].rank()) * (L.dep[b.output] ? B : 1);
-    for (int tid : b.inputs) by += std::ldexp(8.0, prog.tensors[tid].rank()) * (L.dep[tid] ? B : 1);
-    ms[i] = t;
-    bytes[i] = by;
-    bag[i] = b.r;
-  }
+  ms.assign(nbk, 0.f);
+  for (int i = 0; i < nbk; ++i) CU(cudaEventElapsedTime(&ms[i], ev[2 * i], ev[2 * i + 1]));
   for (auto& e : ev) cudaEventDestroy(e);
+  *cfg = C;
+  return TNQ_OK;
+}
+
+// Drops every device configuration of the plan (after its program changed).
+static void reset_device_state(const tnq_plan& P) {
+  {
+    std::lock_guard<std::mutex> lk(P.dev_mu);
+    if (P.dev) {
+      destroy_device_state(P.dev);
+      P.dev = nullptr;
+    }
+  }
+  std::lock_guard<std::mutex> lk(P.layout_mu);
+  P.layout_bytes.clear();
+}
+}  // namespace tnq
+
+extern "C" {
+
+int tnq_internal_profile(const tnq_plan* plan, const uint8_t* bits, uint64_t s0, uint64_t s1, void* workspace,
+                         size_t ws_bytes, uint32_t max_batch, void* stream, int cap, float* ms, double* bytes,
+                         int* bag, int* kind, int* out_n, int* out_B) {
+  std::vector<float> t;
+  ExecConfig* C = nullptr;
+  tnq_status st = profile_steps(plan, bits, s0, s1, workspace, ws_bytes, max_batch, stream, t, &C);
+  if (st != TNQ_OK) return st;
+  const int nbk = (int)C->steps.size();
+  if (cap < nbk) return TNQ_EINVAL;
+  const Program& prog = plan->prog;
+  int single = 0;
+  for (int i = 0; i < nbk; ++i) {
+    ms[i] = t[i];
+    bytes[i] = C->step_bytes[i];
+    const auto st2 = C->steps[i];
+    if (st2.first == 0) {
+      int bi = 0, seen = -1;  // the st2.second-th single bucket
+      for (; bi < (int)prog.buckets.size(); ++bi)
+        if ((prog.group_of.empty() || prog.group_of[bi] < 0) && ++seen == st2.second) break;
+      bag[i] = prog.buckets[bi].r;
+      kind[i] = 0;
+      ++single;
+    } else {
+      bag[i] = prog.buckets[prog.groups[st2.second].buckets.front()].r;
+      kind[i] = (int)prog.groups[st2.second].buckets.size();
+    }
+  }
   *out_n = nbk;
-  *out_B = B;
+  *out_B = C->L.B;
+  return TNQ_OK;
+}
+
+tnq_status tnq_plan_autotune(tnq_plan* plan, const uint8_t* bits, void* workspace, size_t ws_bytes,
+                             uint32_t max_batch, void* stream, int32_t* out_n_fused) {
+  if (!plan || !bits || !workspace) { set_error("NULL argument"); return TNQ_EINVAL; }
+  for (int q = 0; q < plan->net.n_qubits; ++q)
+    if (bits[q] > 1) { set_error("bitstring bytes must be 0 or 1"); return TNQ_EINVAL; }
+  Program& prog = plan->prog;
+  const std::vector<FusedGroup> all = prog.groups;
+  const uint64_t n_sl = 1ull << plan->mu.size();
+  if (!all.empty()) {
+    tnq_status st = check_device();
+    if (st != TNQ_OK) return st;
+    // one batch size for both forms: the largest that fits both layouts
+    uint64_t cap = 1;
+    while (cap < n_sl && cap < (1ull << MAX_ITEM_BITS)) cap <<= 1;
+    if (max_batch > 0) cap = std::min<uint64_t>(cap, 1ull << ilog2_floor(max_batch));
+    const int b_fused = pick_batch(*plan, 0, ws_bytes, cap);
+    set_groups(prog, {});
+    reset_device_state(*plan);
+    const int b_plain = pick_batch(*plan, 0, ws_bytes, cap);
+    set_groups(prog, all);
+    reset_device_state(*plan);
+    const int B = std::min(b_fused, b_plain);
+    if (B == 0) { set_error("workspace too small for one slice of the unfused plan"); return TNQ_ENOMEM; }
+    // every candidate chain fused
+    std::vector<float> tf, tu;
+    ExecConfig* C = nullptr;
+    st = profile_steps(plan, bits, 0, n_sl, workspace, ws_bytes, (uint32_t)B, stream, tf, &C);
+    if (st != TNQ_OK) return st;
+    std::vector<float> group_ms(all.size(), 0.f);
+    for (size_t i = 0; i < C->steps.size(); ++i)
+      if (C->steps[i].first == 1) group_ms[C->steps[i].second] = tf[i];
+    // no chain fused: one step per bucket, in bucket order
+    set_groups(prog, {});
+    reset_device_state(*plan);
+    st = profile_steps(plan, bits, 0, n_sl, workspace, ws_bytes, (uint32_t)B, stream, tu, &C);
+    if (st != TNQ_OK) {
+      set_groups(prog, all);
+      reset_device_state(*plan);
+      return st;
+    }
+    std::vector<FusedGroup> keep;
+    for (size_t g = 0; g < all.size(); ++g) {
+      float t_unfused = 0.f;
+      for (int b : all[g].buckets) t_unfused += tu[b];
+      if (group_ms[g] < t_unfused) keep.push_back(all[g]);
+    }
+    set_groups(prog, keep);
+    reset_device_state(*plan);
+  }
+  if (out_n_fused) *out_n_fused = (int32_t)prog.groups.size();
   return TNQ_OK;
 }
 
 // Internal: kernel launches of one batch of configuration (mode, batch).
 int tnq_internal_launches_per_batch(const tnq_plan* plan) {
-  return plan ? (int)plan->prog.buckets.size() + 4 : 0;
+  if (!plan) return 0;
+  int n = 0;
+  const auto& prog = plan->prog;
+  for (size_t b = 0; b < prog.buckets.size(); ++b)
+    n += (prog.group_of.empty() || prog.group_of[b] < 0 || prog.groups[prog.group_of[b]].buckets.back() == (int)b);
+  return n + 4;
 }
 
 size_t tnq_plan_workspace_bytes(const tnq_plan* plan, uint32_t batch) {
@@ -1080,6 +1667,9 @@ tnq_status tnq_contract_sliced_noalloc(const tnq_plan* plan, const uint8_t* bits
   if (st != TNQ_OK) return st;
   void* scratch = nullptr;
   if ((st = noalloc_scratch_address(&scratch)) != TNQ_OK) return st;
+  CU(allow_group_smem());
+  int ggrid = 0;
+  if ((st = group_grid_size(&ggrid)) != TNQ_OK) return st;
 
   // Host copies of the plan tables; they go to the front of the scratch.
   const Program& prog = plan->prog;
@@ -1103,13 +1693,14 @@ tnq_status tnq_contract_sliced_noalloc(const tnq_plan* plan, const uint8_t* bits
     return TNQ_ENOMEM;
   }
   ExecConfig C;  // pointers into the scratch; nothing here is freed
+  C.group_grid = ggrid;
   C.L = make_layout(*plan, 0, B);
   std::vector<LeafDev> leaves, scalars;
   for (int t : prog.leaves) leaves.push_back(make_leafdev(*plan, &prog.tensors[t], prog.tensors[t].leaf_gate, &C.L, t));
   for (int g : prog.scalar_leaves) scalars.push_back(make_leafdev(*plan, nullptr, g, nullptr, -1));
   std::vector<FinalDev> finals;
   for (int t : prog.finals) finals.push_back(FinalDev{C.L.off[t], t, (int)C.L.dep[t]});
-  if (!build_kparams(*plan, C.L, C.kp, C.kshape)) return TNQ_EUNSUPPORTED;
+  if (!build_steps(*plan, C.L, C)) return TNQ_EUNSUPPORTED;
   char* base = reinterpret_cast<char*>(scratch);
   size_t o = 0;
   C.d_leaves = reinterpret_cast<LeafDev*>(base + o);

@@ -37,7 +37,7 @@ class PlanOpts(ctypes.Structure):
     _fields_ = [("slicer", ctypes.c_int32), ("max_bag_log2", ctypes.c_int32), ("min_p", ctypes.c_int32),
                 ("max_p", ctypes.c_int32), ("seed", ctypes.c_uint64), ("precision", ctypes.c_int32),
                 ("gemm_min_k_log2", ctypes.c_int32), ("ordering", ctypes.c_int32),
-                ("td_rebuild", ctypes.c_int32)]
+                ("td_rebuild", ctypes.c_int32), ("fuse_min_rank", ctypes.c_int32), ("pad_", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -46,7 +46,8 @@ class PlanInfo(ctypes.Structure):
                 ("tau_full", ctypes.c_int32), ("tau", ctypes.c_int32), ("max_bag", ctypes.c_int32),
                 ("n_slices", ctypes.c_uint64), ("flops_per_slice", ctypes.c_double),
                 ("bytes_per_slice", ctypes.c_double), ("peak_bytes_per_slice", ctypes.c_double),
-                ("total_flops", ctypes.c_double), ("n_gemm_buckets", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+                ("total_flops", ctypes.c_double), ("n_gemm_buckets", ctypes.c_int32),
+                ("n_fused_groups", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
@@ -70,6 +71,7 @@ SIGNATURES = {
     "tnq_plan_workspace_bytes": (ctypes.c_size_t, [_vp, ctypes.c_uint32]),
     "tnq_contract_sliced": (ctypes.c_int, [_vp, _u8p, ctypes.c_uint64, ctypes.c_uint64, _vp, ctypes.c_size_t,
                                            ctypes.c_uint32, _vp, _f64p, _f64p]),
+    "tnq_plan_autotune": (ctypes.c_int, [_vp, _u8p, _vp, ctypes.c_size_t, ctypes.c_uint32, _vp, _i32p]),
     "tnq_contract_sliced_noalloc": (ctypes.c_int, [_vp, _u8p, ctypes.c_uint64, ctypes.c_uint64, _vp, _f64p, _f64p]),
     "tnq_amplitudes_batch": (ctypes.c_int, [_P(_vp), ctypes.c_size_t, _u8p, _szp, _vp, ctypes.c_size_t, _vp,
                                             _f64p]),
@@ -175,6 +177,18 @@ class Plan:
 
     def workspace_bytes(self, batch: int = 1) -> int:
         return int(lib().tnq_plan_workspace_bytes(self.handle, batch))
+
+    def autotune(self, bits, workspace=None, max_batch: int = 0, stream=None) -> int:
+        """tnq_plan_autotune: keep each fused chain only where it measures faster. Returns #chains fused."""
+        import torch
+
+        b = _bits_array(bits, self.n_qubits)
+        if workspace is None:
+            workspace = torch.empty(self.workspace_bytes(max(max_batch, 1)), dtype=torch.uint8, device="cuda")
+        n = ctypes.c_int32()
+        _check(lib().tnq_plan_autotune(self.handle, _ptr(b, ctypes.c_uint8), ctypes.c_void_p(workspace.data_ptr()),
+                                       workspace.numel(), max_batch, _stream_ptr(stream), ctypes.byref(n)))
+        return n.value
 
 
 def _bits_array(bits, n):

@@ -202,3 +202,54 @@ def test_7x7_full_size_sampled_slices(cuda, tnq_lib, oracle_lib):
     _, per1 = tnq_lib.contract_sliced(plan, bits, 0, 4, workspace=ws, max_batch=1, per_slice=True)
     assert np.array_equal(per1, per[:4])
     assert abs(per.sum() - amp) <= 1e-12 * np.abs(per).sum()
+
+
+@pytest.mark.parametrize("fuse", [1, 4, 8])
+def test_fused_chains_match_oracle(cuda, tnq_lib, oracle_lib, fuse):
+    """Chains fused into one kernel (down to tiny chains) give the oracle's slices."""
+    n_groups = 0
+    for seed, (rows, cols, cyc, p) in enumerate([(4, 4, 16, 2), (5, 5, 20, 3), (4, 5, 24, 4)]):
+        circ = I.random_grid_circuit(rows, cols, cyc, 20 + seed)
+        bits = I.random_bitstring(circ.n_qubits, seed)
+        plan = tnq_lib.Plan(circ, min_p=p, max_p=p, fuse_min_rank=fuse)
+        n_groups += plan.info()["n_fused_groups"]
+        amp, per = tnq_lib.contract_sliced(plan, bits, per_slice=True)
+        ref, ref_per = oracle_lib.contract(circ, bits, order=plan.order(), mu=plan.sliced(), per_slice=True)
+        n = circ.n_qubits
+        for s in range(len(per)):
+            assert rel_err(per[s], ref_per[s], n) < TOL, (seed, s)
+        assert rel_err(amp, ref, n) < TOL
+        # batched bitstrings through fused groups
+        bl = [I.random_bitstring(n, 100 + j) for j in range(3)]
+        out = tnq_lib.amplitudes_batch([plan], [bl])
+        for b, a in zip(bl, out):
+            assert rel_err(a, oracle_lib.contract(circ, b), n) < TOL
+    assert n_groups > 0
+
+
+def test_fused_equals_unfused(cuda, tnq_lib):
+    """Fusion only regroups the same products: slice values agree to FP32 rounding."""
+    circ = I.random_grid_circuit(6, 6, 24, 0)
+    bits = I.random_bitstring(36, 0)
+    fused = tnq_lib.Plan(circ, max_bag_log2=24, min_p=5, max_p=5)
+    plain = tnq_lib.Plan(circ, max_bag_log2=24, min_p=5, max_p=5, fuse_min_rank=0)
+    assert fused.info()["n_fused_groups"] > 0 and plain.info()["n_fused_groups"] == 0
+    assert fused.info()["bytes_per_slice"] < plain.info()["bytes_per_slice"]
+    _, a = tnq_lib.contract_sliced(fused, bits, per_slice=True)
+    _, b = tnq_lib.contract_sliced(plain, bits, per_slice=True)
+    assert np.max(np.abs(a - b)) <= 1e-6 * np.max(np.abs(b))
+
+
+def test_autotune_keeps_results(cuda, tnq_lib, oracle_lib):
+    """Autotuning only chooses between fused and unfused forms of the same products."""
+    circ = I.random_grid_circuit(6, 6, 24, 1)
+    bits = I.random_bitstring(36, 1)
+    plan = tnq_lib.Plan(circ, max_bag_log2=24, min_p=4, max_p=4, fuse_min_rank=8)
+    n0 = plan.info()["n_fused_groups"]
+    _, before = tnq_lib.contract_sliced(plan, bits, per_slice=True)
+    n1 = plan.autotune(bits, max_batch=16)
+    assert 0 <= n1 <= n0 and plan.info()["n_fused_groups"] == n1
+    amp, after = tnq_lib.contract_sliced(plan, bits, per_slice=True)
+    assert np.max(np.abs(after - before)) <= 1e-6 * np.max(np.abs(before))
+    ref = oracle_lib.contract(circ, bits, order=plan.order(), mu=plan.sliced())
+    assert rel_err(amp, ref, 36) < TOL
