@@ -94,6 +94,71 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# FP32 CUDA-core peak of GB300 from unit counts and clocks: 152 SMs x 128 FP32
+# lanes x 2 flops (FMA) x 2.07 GHz (the maximum SM clock in MEASURED_PEAKS.json).
+FP32_LANES_PER_SM = 128
+
+
+def fp32_peak_tflops(peaks):
+    return 152 * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+
+
+def launch_roofline(L, plan, bits, ws, B, n_sl, stream, peaks, info):
+    """Times every launch of one batch with CUDA events on the launching stream
+    and returns the roofline of the kernel with the largest share of time."""
+    import numpy as np
+
+    nb = info["n_buckets"] + 64
+    ms = (ctypes.c_float * nb)()
+    by = (ctypes.c_double * nb)()
+    fl = (ctypes.c_double * nb)()
+    bag = (ctypes.c_int * nb)()
+    kind = (ctypes.c_int * nb)()
+    n_out, b_out = ctypes.c_int(), ctypes.c_int()
+    P = ctypes.POINTER
+    L.tnq_internal_profile.argtypes = [ctypes.c_void_p, P(ctypes.c_uint8), ctypes.c_uint64, ctypes.c_uint64,
+                                       ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_int,
+                                       P(ctypes.c_float), P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_int),
+                                       P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int)]
+    bb = np.ascontiguousarray(np.array(bits, dtype=np.uint8))
+    rc = L.tnq_internal_profile(plan.handle, bb.ctypes.data_as(P(ctypes.c_uint8)), 0, n_sl,
+                                ctypes.c_void_p(ws.data_ptr()), ws.numel(), B, ctypes.c_void_p(stream.cuda_stream),
+                                nb, ms, by, fl, bag, kind, ctypes.byref(n_out), ctypes.byref(b_out))
+    if rc != 0:
+        return None
+    n = n_out.value
+    grp = [i for i in range(n) if kind[i] > 0]
+    one = [i for i in range(n) if kind[i] == 0]
+    t_grp = sum(ms[i] for i in grp)
+    t_one = sum(ms[i] for i in one)
+    tot = t_grp + t_one
+    hbm = peaks["hbm_gbs"]
+    fp32 = fp32_peak_tflops(peaks)
+    one_gbs = sum(by[i] for i in one) / (t_one / 1e3) / 1e9 if t_one > 0 else None
+    grp_tfs = sum(fl[i] for i in grp) / (t_grp / 1e3) / 1e12 if t_grp > 0 else None
+    k_bucket = {"kernel": "k_bucket", "bound": "hbm", "achieved": one_gbs, "peak": hbm, "unit": "GB/s",
+                "frac": one_gbs / hbm if one_gbs else None, "launches": len(one), "time_share": t_one / tot,
+                "bytes_per_launch": sum(by[i] for i in one) / max(len(one), 1),
+                "ms_per_launch": t_one / max(len(one), 1)}
+    k_group = {"kernel": "k_group", "bound": "alu", "achieved": grp_tfs, "peak": fp32, "unit": "TFLOP/s",
+               "frac": grp_tfs / fp32 if grp_tfs else None, "launches": len(grp), "time_share": t_grp / tot,
+               "flops_per_launch": sum(fl[i] for i in grp) / max(len(grp), 1),
+               "ms_per_launch": t_grp / max(len(grp), 1),
+               "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}
+    dom, other = (k_group, k_bucket) if t_grp >= t_one else (k_bucket, k_group)
+    out = dict(dom)
+    out["traffic"] = None
+    out["peak_source"] = dom.get("peak_source", "measured (MEASURED_PEAKS.json hbm_gbs)")
+    out["batch"] = b_out.value
+    out["other_kernel"] = other
+    out["top_launches"] = [{"kind": "group" if kind[i] else "bucket", "buckets": max(1, kind[i]), "bag": bag[i],
+                            "ms": round(ms[i], 4),
+                            "gbs": round(by[i] / (ms[i] / 1e3) / 1e9, 1) if ms[i] > 0 else None,
+                            "tflops": round(fl[i] / (ms[i] / 1e3) / 1e12, 2) if ms[i] > 0 else None}
+                           for i in sorted(range(n), key=lambda i: -ms[i])[:8]]
+    return out
+
+
 def oracle_slice(circ, bits, plan, s):
     """FP64 oracle value and time of slice s of the plan (test infrastructure, CPU)."""
     from oracle import oracle
@@ -223,47 +288,11 @@ def main():
     n_batches = (n_sl + B - 1) // B
     launches = args.steps * n_batches * L.tnq_internal_launches_per_batch(plan.handle)
 
-    # live per-bucket timing of one batch (CUDA events on the launching stream)
+    # live per-launch timing of one batch (CUDA events on the launching stream)
     roof = None
     peaks = load_peaks()
     if not args.no_profile and rank == 0:
-        nb = info["n_buckets"] + 64
-        ms = (ctypes.c_float * nb)()
-        by = (ctypes.c_double * nb)()
-        bag = (ctypes.c_int * nb)()
-        kind = (ctypes.c_int * nb)()
-        n_out, b_out = ctypes.c_int(), ctypes.c_int()
-        import numpy as np
-
-        bb = np.ascontiguousarray(np.array(bits, dtype=np.uint8))
-        L.tnq_internal_profile.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint8), ctypes.c_uint64,
-                                           ctypes.c_uint64, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint32,
-                                           ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
-                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
-                                           ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
-                                           ctypes.POINTER(ctypes.c_int)]
-        rc = L.tnq_internal_profile(plan.handle, bb.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), 0, n_sl,
-                                    ctypes.c_void_p(ws.data_ptr()), ws.numel(), B, ctypes.c_void_p(stream.cuda_stream),
-                                    nb, ms, by, bag, kind, ctypes.byref(n_out), ctypes.byref(b_out))
-        if rc == 0:
-            n = n_out.value
-            tot_ms = sum(ms[i] for i in range(n))
-            tot_by = sum(by[i] for i in range(n))
-            big = [i for i in range(n) if bag[i] >= info["max_bag"] - 6]
-            big_ms = sum(ms[i] for i in big)
-            big_by = sum(by[i] for i in big)
-            achieved = tot_by / (tot_ms / 1e3) / 1e9
-            roof = {"bound": "hbm", "kernel": "k_bucket (fused product + sum-out, all bucket launches of one batch)",
-                    "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                    "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if not peaks.get("fallback") else "fallback",
-                    "launches": n, "batch": b_out.value, "bytes_per_launch": tot_by / n, "ms_per_launch": tot_ms / n,
-                    "big_buckets_gbs": big_by / (big_ms / 1e3) / 1e9 if big_ms > 0 else None,
-                    "big_bucket_time_share": big_ms / tot_ms if tot_ms > 0 else None,
-                    "top_launches": [{"kind": "group" if kind[i] else "bucket", "buckets": max(1, kind[i]),
-                                      "bag": bag[i], "ms": round(ms[i], 4),
-                                      "gbs": round(by[i] / (ms[i] / 1e3) / 1e9, 1) if ms[i] > 0 else None}
-                                     for i in sorted(range(n), key=lambda i: -ms[i])[:8]]}
+        roof = launch_roofline(L, plan, bits, ws, B, n_sl, stream, peaks, info)
 
     cpu = None
     err = None

@@ -1,6 +1,8 @@
 // capi.cpp -- host-side C-ABI entry points: errors, planning, plan queries and
 // the graph-level algorithms (Algorithms 1, 2, 4 and the Section III scores).
 #include <algorithm>
+#include <cstdio>
+#include <iterator>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -314,4 +316,51 @@ extern "C" int tnq_internal_bucket_chain(const tnq_plan* P, int32_t* consumer, i
     union_size[i] = (int)u.size();
   }
   return 0;
+}
+
+// Internal analysis: for every summing bucket with exactly two inputs of rank
+// >= min_rank (the rest rank <= 2), follows the chain of consumers while each
+// next bucket eliminates a variable shared by both operands and adds only
+// small tensors; prints batch/M/N/K bit counts of the resulting product
+// Sum_K A[S,X,K] B[S,Y,K]. Returns the number of candidates printed.
+extern "C" int tnq_internal_gemm_candidates(const tnq_plan* P, int min_rank) {
+  if (!P) return -1;
+  const auto& prog = P->prog;
+  int n = 0;
+  for (size_t i = 0; i < prog.buckets.size(); ++i) {
+    const auto& b = prog.buckets[i];
+    if (!b.sum) continue;
+    std::vector<int> big;
+    bool small_rest = true;
+    for (int t : b.inputs) {
+      if (prog.tensors[t].rank() >= min_rank) big.push_back(t);
+      else if (prog.tensors[t].rank() > 2) small_rest = false;
+    }
+    if (big.size() != 2 || !small_rest) continue;
+    std::vector<int> A = prog.tensors[big[0]].vars, B = prog.tensors[big[1]].vars;
+    std::sort(A.begin(), A.end());
+    std::sort(B.begin(), B.end());
+    std::vector<int> S;
+    std::set_intersection(A.begin(), A.end(), B.begin(), B.end(), std::back_inserter(S));
+    int k = 1;
+    int cur = (int)i;
+    std::vector<int> K{b.u};
+    while (true) {
+      const int c = prog.tensors[prog.buckets[cur].output].consumer;
+      if (c < 0) break;
+      const auto& cb = prog.buckets[c];
+      bool ok = std::binary_search(S.begin(), S.end(), cb.u);
+      for (int t : cb.inputs)
+        if (t != prog.buckets[cur].output && prog.tensors[t].rank() > 2) ok = false;
+      if (!ok) break;
+      K.push_back(cb.u);
+      ++k;
+      cur = c;
+    }
+    const int s = (int)S.size() - k;
+    std::fprintf(stderr, "bucket %zu r=%d: A rank %d, B rank %d, shared %zu -> batch 2^%d M 2^%d N 2^%d K 2^%d\n", i, b.r,
+                 (int)A.size(), (int)B.size(), S.size(), s, (int)A.size() - (int)S.size(), (int)B.size() - (int)S.size(), k);
+    ++n;
+  }
+  return n;
 }

@@ -680,6 +680,7 @@ struct ExecConfig {
   int group_grid = 152 * 4;          // persistent blocks of k_group (SMs x resident blocks)
   std::vector<std::pair<int, int>> steps;  // (0, index into kp) or (1, index into gp), program order
   std::vector<double> step_bytes;    // algorithmic bytes of each step (all items)
+  std::vector<double> step_flops;    // algorithmic flops of each step (all items; cost model of Section IV)
   void* ws = nullptr;                // workspace the graph was captured for
   cudaGraphExec_t exec = nullptr;
 };
@@ -908,7 +909,13 @@ static bool build_steps(const tnq_plan& P, const Layout& L, ExecConfig& C) {
   C.gsmem.clear();
   C.steps.clear();
   C.step_bytes.clear();
+  C.step_flops.clear();
   auto tbytes = [&](int t) { return std::ldexp(8.0, prog.tensors[t].rank()) * (L.dep[t] ? L.B : 1); };
+  auto bflops = [&](int bi) {
+    const PBucket& b = prog.buckets[bi];
+    const double full = std::ldexp(1.0, b.r);
+    return (6.0 * (b.k - 1) * full + (b.sum ? full : 0.0)) * (L.dep[b.output] ? L.B : 1);
+  };
   for (size_t bi = 0; bi < prog.buckets.size(); ++bi) {
     const int gi = prog.group_of.empty() ? -1 : prog.group_of[bi];
     if (gi < 0) {
@@ -921,6 +928,7 @@ static bool build_steps(const tnq_plan& P, const Layout& L, ExecConfig& C) {
       double by = tbytes(prog.buckets[bi].output);
       for (int t : prog.buckets[bi].inputs) by += tbytes(t);
       C.step_bytes.push_back(by);
+      C.step_flops.push_back(bflops((int)bi));
     } else if ((int)bi == prog.groups[gi].buckets.back()) {
       bool ok;
       int smem = 0;
@@ -932,6 +940,9 @@ static bool build_steps(const tnq_plan& P, const Layout& L, ExecConfig& C) {
       double by = tbytes(prog.groups[gi].output);
       for (int t : prog.groups[gi].ext_inputs) by += tbytes(t);
       C.step_bytes.push_back(by);
+      double fl = 0;
+      for (int b : prog.groups[gi].buckets) fl += bflops(b);
+      C.step_flops.push_back(fl);
     }
   }
   return true;
@@ -1302,8 +1313,9 @@ int tnq_internal_validate(const tnq_plan* plan, int mode, uint32_t batch, char* 
 // CUDA event pair around every bucket launch on `stream`. Per bucket it
 // returns the launch time (ms), the algorithmic bytes of the launch (every
 // operand read once, the output written once; 8 B per complex64) and the bag
-// size r (of the first bucket for a fused group) and the kind (0: one bucket,
-// m > 1: a fused group of m buckets). *out_n = launches, *out_B = batch used.
+// size r (of the first bucket for a fused group), the algorithmic flops (cost
+// model, all items) and the kind (0: one bucket, m > 1: a fused group of m
+// buckets). *out_n = launches, *out_B = batch used.
 }  // extern "C"
 
 namespace tnq {
@@ -1388,7 +1400,7 @@ extern "C" {
 
 int tnq_internal_profile(const tnq_plan* plan, const uint8_t* bits, uint64_t s0, uint64_t s1, void* workspace,
                          size_t ws_bytes, uint32_t max_batch, void* stream, int cap, float* ms, double* bytes,
-                         int* bag, int* kind, int* out_n, int* out_B) {
+                         double* flops, int* bag, int* kind, int* out_n, int* out_B) {
   std::vector<float> t;
   ExecConfig* C = nullptr;
   tnq_status st = profile_steps(plan, bits, s0, s1, workspace, ws_bytes, max_batch, stream, t, &C);
@@ -1400,6 +1412,7 @@ int tnq_internal_profile(const tnq_plan* plan, const uint8_t* bits, uint64_t s0,
   for (int i = 0; i < nbk; ++i) {
     ms[i] = t[i];
     bytes[i] = C->step_bytes[i];
+    flops[i] = C->step_flops[i];
     const auto st2 = C->steps[i];
     if (st2.first == 0) {
       int bi = 0, seen = -1;  // the st2.second-th single bucket
