@@ -1,0 +1,334 @@
+// gemm_tc.cu -- tcgen05 split-precision batched GEMM (see gemm_tc.cuh).
+//
+// One block (4 warps) computes one 128 x 128 FP32 tile of C in tensor memory:
+// thread 0 streams the A/B hi/lo tiles of each K step into a double-buffered
+// shared-memory stage with bulk-async copies (mbarrier transaction counts),
+// issues the three split-precision MMA passes (hi*hi, hi*lo, lo*hi; lo*lo is
+// below FP32 rounding and dropped) and commits them to a per-stage mbarrier;
+// the four warps then read their 32 accumulator lanes with tcgen05.ld.
+// Every wait is bounded by %globaltimer: on a timeout the kernel records a
+// status, waits (bounded) for the copies and MMAs it issued, frees its tensor
+// memory and returns.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "gemm_tc.cuh"
+
+namespace tnq {
+
+void set_error(const std::string& msg);
+
+namespace {
+
+constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s per wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// Waits for the phase with the given parity to complete; false after WAIT_NS.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const unsigned long long t0 = gtimer();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (gtimer() - t0 > WAIT_NS) return false;
+  }
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: no swizzle, K-major core matrices of
+// 8 rows x 16 bytes, 128 bytes apart along K (leading) and 1024 bytes apart
+// along rows (stride); descriptor version 1.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((128u >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((1024u >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// Instruction descriptor: FP32 accumulator, A/B format fmt (1 = BF16 for
+// kind::f16, 2 = TF32 for kind::tf32), both K-major, N = 128, M = 128.
+__host__ __device__ constexpr uint32_t idesc(uint32_t fmt) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+}
+
+template <int KIND>
+__device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t acc) {
+  if (KIND == GEMM_BF16) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            tmem_d),
+        "l"(a), "l"(b), "r"(idesc(1)), "r"(acc)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            tmem_d),
+        "l"(a), "l"(b), "r"(idesc(2)), "r"(acc)
+        : "memory");
+  }
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+// 32 consecutive accumulator columns of this thread's lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%"
+      "19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+constexpr int STAGE_BYTES = 4 * GT_TILE_BYTES;  // A hi, A lo, B hi, B lo
+constexpr int SMEM_BYTES = 2 * STAGE_BYTES + 1024;
+
+template <int KIND>
+__global__ void __launch_bounds__(128) k_gemm_tc(const GemmArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ uint64_t full_bar[2], mma_bar[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int s_fail;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ct = blockIdx.x, rt = blockIdx.y, b = blockIdx.z;
+  const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  if (tid == 0) {
+    mbar_init(&full_bar[0], 1);
+    mbar_init(&full_bar[1], 1);
+    mbar_init(&mma_bar[0], 1);
+    mbar_init(&mma_bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    s_fail = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(128u)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_d = tmem_slot;
+
+  if (tid == 0) {
+    const size_t tile = GT_TILE_BYTES;
+    const char* A_hi = (const char*)a.a_hi + (size_t)(b * a.row_tiles_a + rt) * a.k_tiles * tile;
+    const char* A_lo = (const char*)a.a_lo + (size_t)(b * a.row_tiles_a + rt) * a.k_tiles * tile;
+    const char* B_hi = (const char*)a.b_hi + (size_t)(b * a.row_tiles_b + ct) * a.k_tiles * tile;
+    const char* B_lo = (const char*)a.b_lo + (size_t)(b * a.row_tiles_b + ct) * a.k_tiles * tile;
+    bool ok = true;
+    int copies_pending = -1, mma_pending = -1;  // last k step whose copies / MMAs were issued but not waited for
+    for (int kt = 0; kt < a.k_tiles && ok; ++kt) {
+      const int s = kt & 1;
+      if (kt >= 2) {
+        ok = mbar_wait(&mma_bar[s], ((kt >> 1) - 1) & 1);  // MMAs of step kt-2 released stage s
+        if (!ok) break;
+      }
+      const uint32_t st = base + (uint32_t)s * STAGE_BYTES;
+      mbar_expect_tx(&full_bar[s], STAGE_BYTES);
+      bulk_g2s(st + 0 * GT_TILE_BYTES, A_hi + kt * tile, GT_TILE_BYTES, &full_bar[s]);
+      bulk_g2s(st + 1 * GT_TILE_BYTES, A_lo + kt * tile, GT_TILE_BYTES, &full_bar[s]);
+      bulk_g2s(st + 2 * GT_TILE_BYTES, B_hi + kt * tile, GT_TILE_BYTES, &full_bar[s]);
+      bulk_g2s(st + 3 * GT_TILE_BYTES, B_lo + kt * tile, GT_TILE_BYTES, &full_bar[s]);
+      copies_pending = kt;
+      ok = mbar_wait(&full_bar[s], (kt >> 1) & 1);
+      if (!ok) break;
+      copies_pending = -1;
+      tc_fence_after();
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {  // 4 MMAs of 32 bytes of K per 128-byte tile row
+        const uint32_t off = (uint32_t)j * 256u;
+        mma<KIND>(tmem_d, sdesc(st + off), sdesc(st + 2 * GT_TILE_BYTES + off), (kt > 0 || j > 0) ? 1u : 0u);
+        mma<KIND>(tmem_d, sdesc(st + off), sdesc(st + 3 * GT_TILE_BYTES + off), 1u);
+        mma<KIND>(tmem_d, sdesc(st + GT_TILE_BYTES + off), sdesc(st + 2 * GT_TILE_BYTES + off), 1u);
+      }
+      mma_commit(&mma_bar[s]);
+      mma_pending = kt;
+    }
+    if (ok && mma_pending >= 0) {
+      ok = mbar_wait(&mma_bar[mma_pending & 1], (mma_pending >> 1) & 1);
+      if (ok) mma_pending = -1;
+    }
+    if (!ok) {
+      s_fail = 1;
+      atomicExch(a.status, 1);
+      // drain what this thread issued before the block frees its resources
+      if (copies_pending >= 0) mbar_wait(&full_bar[copies_pending & 1], (copies_pending >> 1) & 1);
+      if (mma_pending >= 0) mbar_wait(&mma_bar[mma_pending & 1], (mma_pending >> 1) & 1);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (!s_fail && a.out_c) {
+    const int row = rt * GT_ROWS + warp * 32 + lane;
+    float* crow = a.out_c + ((long long)b * a.row_tiles_a * GT_ROWS + row) * a.ldc + (long long)ct * 128;
+#pragma unroll 1
+    for (int chunk = 0; chunk < 4; ++chunk) {
+      float v[32];
+      tmem_ld32(tmem_d + ((uint32_t)(warp * 32) << 16) + (uint32_t)(chunk * 32), v);
+#pragma unroll
+      for (int i = 0; i < 32; i += 4)
+        *reinterpret_cast<float4*>(crow + chunk * 32 + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_d), "r"(128u) : "memory");
+}
+
+// Split of real matrices (rows x K per batch, row-major FP32) into hi/lo
+// operands in tile-major layout.
+template <int KIND>
+__global__ void k_pack_real(const float* __restrict__ X, int rows, int K, int batch, void* hi, void* lo) {
+  const long long n = (long long)batch * rows * K;
+  const int esize = KIND == GEMM_BF16 ? 2 : 4;
+  const int kt_count = K * esize / GT_KBYTES, rt_count = rows / GT_ROWS;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(i % K);
+    const int r = (int)((i / K) % rows);
+    const int b = (int)(i / ((long long)K * rows));
+    const float x = X[i];
+    const long long tile = ((long long)(b * rt_count + r / GT_ROWS) * kt_count + (k * esize) / GT_KBYTES);
+    const size_t off = (size_t)tile * GT_TILE_BYTES + gt_offset(r % GT_ROWS, k, esize);
+    if (KIND == GEMM_BF16) {
+      const __nv_bfloat16 h = __float2bfloat16_rn(x);
+      const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+      *reinterpret_cast<__nv_bfloat16*>((char*)hi + off) = h;
+      *reinterpret_cast<__nv_bfloat16*>((char*)lo + off) = l;
+    } else {
+      uint32_t h, l;
+      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+      const float rest = x - __uint_as_float(h);
+      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(rest));
+      *reinterpret_cast<uint32_t*>((char*)hi + off) = h;
+      *reinterpret_cast<uint32_t*>((char*)lo + off) = l;
+    }
+  }
+}
+
+}  // namespace
+
+void gemm_tc_launch(int kind, const GemmArgs& args, void* stream) {
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  dim3 grid(args.row_tiles_b, args.row_tiles_a, args.batch);
+  if (kind == GEMM_BF16) {
+    cudaFuncSetAttribute(k_gemm_tc<GEMM_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    k_gemm_tc<GEMM_BF16><<<grid, 128, SMEM_BYTES, s>>>(args);
+  } else {
+    cudaFuncSetAttribute(k_gemm_tc<GEMM_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    k_gemm_tc<GEMM_TF32><<<grid, 128, SMEM_BYTES, s>>>(args);
+  }
+}
+
+}  // namespace tnq
+
+// Internal self-test hook (not in include/tnq.h): C[b] = A[b] B[b]^T for real
+// FP32 matrices (host, row-major: A batch x M x K, B batch x N x K, C batch x M
+// x N) through the split-precision tensor-core path. M, N multiples of 128;
+// K a multiple of 64 (BF16) or 32 (TF32). Returns 0, or nonzero with a message.
+extern "C" int tnq_internal_gemm_selftest(int kind, int batch, int M, int N, int K, const float* A, const float* B,
+                                          float* C, char* msg, size_t msg_len) {
+  using namespace tnq;
+  auto fail = [&](const std::string& m) {
+    if (msg && msg_len) {
+      std::strncpy(msg, m.c_str(), msg_len - 1);
+      msg[msg_len - 1] = 0;
+    }
+    return 1;
+  };
+  const int esize = kind == GEMM_BF16 ? 2 : 4;
+  if (batch < 1 || M % 128 || N % 128 || (K * esize) % GT_KBYTES || K <= 0) return fail("bad shape");
+  const size_t na = (size_t)batch * M * K, nb = (size_t)batch * N * K, nc = (size_t)batch * M * N;
+  float *dA = nullptr, *dB = nullptr, *dC = nullptr;
+  void *ah = nullptr, *al = nullptr, *bh = nullptr, *bl = nullptr;
+  int* dst = nullptr;
+  auto cleanup = [&]() {
+    cudaFree(dA); cudaFree(dB); cudaFree(dC); cudaFree(ah); cudaFree(al); cudaFree(bh); cudaFree(bl); cudaFree(dst);
+  };
+  cudaError_t e = cudaSuccess;
+  if ((e = cudaMalloc(&dA, na * 4)) || (e = cudaMalloc(&dB, nb * 4)) || (e = cudaMalloc(&dC, nc * 4)) ||
+      (e = cudaMalloc(&ah, na * esize)) || (e = cudaMalloc(&al, na * esize)) || (e = cudaMalloc(&bh, nb * esize)) ||
+      (e = cudaMalloc(&bl, nb * esize)) || (e = cudaMalloc(&dst, 4))) {
+    cleanup();
+    return fail(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  cudaMemcpy(dA, A, na * 4, cudaMemcpyHostToDevice);
+  cudaMemcpy(dB, B, nb * 4, cudaMemcpyHostToDevice);
+  cudaMemset(dC, 0, nc * 4);
+  cudaMemset(dst, 0, 4);
+  if (kind == GEMM_BF16) {
+    k_pack_real<GEMM_BF16><<<1024, 256>>>(dA, M, K, batch, ah, al);
+    k_pack_real<GEMM_BF16><<<1024, 256>>>(dB, N, K, batch, bh, bl);
+  } else {
+    k_pack_real<GEMM_TF32><<<1024, 256>>>(dA, M, K, batch, ah, al);
+    k_pack_real<GEMM_TF32><<<1024, 256>>>(dB, N, K, batch, bh, bl);
+  }
+  GemmArgs g;
+  std::memset(&g, 0, sizeof(g));
+  g.a_hi = ah;
+  g.a_lo = al;
+  g.b_hi = bh;
+  g.b_lo = bl;
+  g.row_tiles_a = M / 128;
+  g.row_tiles_b = N / 128;
+  g.k_tiles = K * esize / GT_KBYTES;
+  g.batch = batch;
+  g.status = dst;
+  g.out_c = dC;
+  g.ldc = N;
+  gemm_tc_launch(kind, g, nullptr);
+  e = cudaDeviceSynchronize();
+  int status = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&status, dst, 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(C, dC, nc * 4, cudaMemcpyDeviceToHost);
+  cleanup();
+  if (e != cudaSuccess) return fail(std::string("CUDA: ") + cudaGetErrorString(e));
+  if (status) return fail("device wait timed out");
+  return 0;
+}

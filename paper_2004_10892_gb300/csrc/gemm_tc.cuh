@@ -1,0 +1,53 @@
+// gemm_tc.cuh -- split-precision batched GEMM on the 5th-generation tensor
+// cores (tcgen05, sm_103a) used for merged buckets whose product is a
+// contraction Sum_K A[S,X,K] B[S,Y,K] (several consecutive eliminations of
+// variables shared by two large tensors).
+//
+// C[b] (rows x cols, FP32) = sum over the passes hi*hi + hi*lo + lo*hi of
+// A_p[b] (rows x Kr) . B_p[b]^T (cols x Kr), where x = hi + lo splits an FP32
+// value into two BF16 (or TF32) parts; FP32 accumulation in tensor memory.
+//
+// Operands live in global memory already in the tensor core's shared-memory
+// layout ("tile-major"): a tile is 128 rows x 128 bytes of K, stored as 16
+// row groups of 8 core matrices (8 rows x 16 bytes each, 128 bytes apart
+// along K, 1024 bytes apart along rows), so one tile is one contiguous 16 KB
+// bulk-async copy. Tile (b, rt, kt) of an operand with RT row tiles and KT
+// K tiles starts at ((b * RT + rt) * KT + kt) * 16384 bytes.
+#pragma once
+#include <cstdint>
+
+namespace tnq {
+
+enum GemmKind { GEMM_BF16 = 0, GEMM_TF32 = 1 };
+
+constexpr int GT_ROWS = 128;           // rows of an operand tile (M of one MMA)
+constexpr int GT_KBYTES = 128;         // bytes of K per tile row
+constexpr int GT_TILE_BYTES = GT_ROWS * GT_KBYTES;  // 16 KB
+
+// Byte offset of element (r, k) inside its tile; esize = 2 (BF16) or 4 (TF32).
+__host__ __device__ inline uint32_t gt_offset(int r, int k, int esize) {
+  const int kb = (k * esize) & (GT_KBYTES - 1);
+  return (uint32_t)((r >> 3) * 1024 + (kb >> 4) * 128 + (r & 7) * 16 + (kb & 15));
+}
+
+// Device-side status word: 0 ok, 1 a bulk-copy wait gave up, 2 an MMA wait gave up.
+struct GemmArgs {
+  const void* a_hi;
+  const void* a_lo;
+  const void* b_hi;
+  const void* b_lo;
+  int row_tiles_a;   // rows of A / 128
+  int row_tiles_b;   // rows of B / 128 (columns of C / 128)
+  int k_tiles;       // Kr bytes / 128
+  int batch;
+  int* status;
+  // epilogue: C written as FP32 rows x cols per batch (ldc floats per row) when
+  // `out_c` is set; the bucket path supplies its own epilogue data instead
+  float* out_c;
+  long long ldc;
+};
+
+// Launches C = sum_passes A_p B_p^T for every batch (grid = col tiles x row tiles x batch).
+void gemm_tc_launch(int kind, const GemmArgs& args, void* stream);
+
+}  // namespace tnq
