@@ -127,11 +127,13 @@ def launch_roofline(L, plan, bits, ws, B, n_sl, stream, peaks, info):
     if rc != 0:
         return None
     n = n_out.value
-    grp = [i for i in range(n) if kind[i] > 0]
+    grp = [i for i in range(n) if 0 < kind[i] < 100]
     one = [i for i in range(n) if kind[i] == 0]
+    gem = [i for i in range(n) if kind[i] >= 100]
     t_grp = sum(ms[i] for i in grp)
     t_one = sum(ms[i] for i in one)
-    tot = t_grp + t_one
+    t_gem = sum(ms[i] for i in gem)
+    tot = t_grp + t_one + t_gem
     hbm = peaks["hbm_gbs"]
     fp32 = fp32_peak_tflops(peaks)
     one_gbs = sum(by[i] for i in one) / (t_one / 1e3) / 1e9 if t_one > 0 else None
@@ -151,7 +153,13 @@ def launch_roofline(L, plan, bits, ws, B, n_sl, stream, peaks, info):
     out["peak_source"] = dom.get("peak_source", "measured (MEASURED_PEAKS.json hbm_gbs)")
     out["batch"] = b_out.value
     out["other_kernel"] = other
-    out["top_launches"] = [{"kind": "group" if kind[i] else "bucket", "buckets": max(1, kind[i]), "bag": bag[i],
+    if gem:
+        # split precision: 3 BF16/TF32 MMA passes over the real embedding (4x the complex flops)
+        gem_tfs = sum(fl[i] for i in gem) / (t_gem / 1e3) / 1e12 if t_gem > 0 else None
+        out["gemm_buckets"] = {"kernel": "k_gemm_pack + k_gemm_tc", "launches": len(gem), "time_share": t_gem / tot,
+                               "algorithmic_tflops": gem_tfs}
+    out["top_launches"] = [{"kind": ("gemm" if kind[i] >= 100 else "group") if kind[i] else "bucket",
+                            "buckets": max(1, kind[i] % 100), "bag": bag[i],
                             "ms": round(ms[i], 4),
                             "gbs": round(by[i] / (ms[i] / 1e3) / 1e9, 1) if ms[i] > 0 else None,
                             "tflops": round(fl[i] / (ms[i] / 1e3) / 1e12, 2) if ms[i] > 0 else None}
@@ -215,6 +223,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-profile", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--precision", default="c64", choices=["c64", "bf16x3", "tf32x3"],
+                    help="merged GEMM-shaped buckets on tensor cores in split precision")
     ap.add_argument("--tune-batch", type=int, default=16, help="slices per batch while autotuning")
     ap.add_argument("--tune-gb", type=int, default=48, help="workspace GiB while autotuning")
     args = ap.parse_args()
@@ -240,7 +250,8 @@ def main():
     circ = inputs.random_grid_circuit(rows, cols, cyc, 0)
     bits = inputs.random_bitstring(circ.n_qubits, rank)
     t_plan = time.perf_counter()
-    plan = tnq.Plan(circ, max_bag_log2=mb, min_p=pmin, max_p=pmax)
+    prec = {"c64": 0, "bf16x3": 1, "tf32x3": 2}[args.precision]
+    plan = tnq.Plan(circ, max_bag_log2=mb, min_p=pmin, max_p=pmax, precision=prec, gemm_min_k_log2=4)
     t_plan = time.perf_counter() - t_plan
     n_sl = plan.info()["n_slices"]
     stream = torch.cuda.current_stream()
@@ -311,13 +322,16 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": "slices/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"c64": "c64", "bf16x3": "c64+3xbf16", "tf32x3": "c64+3xtf32"}[args.precision],
+            "data": "synthetic",
             "config": {"workload": f"grid {args.config} random circuit (seed 0), one amplitude per step per GPU",
                        "n_qubits": circ.n_qubits, "p": info["p"], "n_slices": n_sl, "tau_full": info["tau_full"],
                        "tau": info["tau"], "max_bag": info["max_bag"], "batch": B,
                        "flops_per_slice": info["flops_per_slice"], "bytes_per_slice": info["bytes_per_slice"],
                        "l2": "inputs larger than L2 (each batch streams GBs)", "plan_s": t_plan,
-                       "autotune_s": t_tune, "fused_chains": info["n_fused_groups"]},
+                       "autotune_s": t_tune, "fused_chains": info["n_fused_groups"],
+                       "gemm_buckets": info["n_gemm_buckets"], "precision": args.precision},
             "time_per_amplitude_s": t_dev / args.steps,
             "rel_err_vs_fp64": err,
             "amplitude": [amp.real, amp.imag],

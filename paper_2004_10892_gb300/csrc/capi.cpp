@@ -102,6 +102,8 @@ tnq_status tnq_plan_from_circuit(int32_t n_qubits, const tnq_gate* gates, size_t
     for (int v : P->mu) delete_vertex(reduced, v);
     P->tau = treewidth_of_order(reduced, P->order);
     P->prog = compile_program(P->net, P->order, P->mu);
+    if (o.precision != TNQ_PREC_C64)
+      find_gemm_chains(P->prog, P->order, o.gemm_min_k_log2 > 0 ? o.gemm_min_k_log2 : 4, 8);
     fuse_chains(P->prog, P->order, o.fuse_min_rank);
     P->amp_scale_log2 = -0.5 * P->net.n_sqrt2;
     *out_plan = P.release();
@@ -139,7 +141,11 @@ tnq_status tnq_plan_info_get(const tnq_plan* P, tnq_plan_info* out) {
   }
   out->total_flops = std::ldexp(P->prog.flops_per_slice, (int)P->mu.size());
   out->n_gemm_buckets = 0;
-  out->n_fused_groups = (int32_t)P->prog.groups.size();
+  out->n_fused_groups = 0;
+  for (const auto& g : P->prog.groups) {
+    if (g.gemm) out->n_gemm_buckets += (int32_t)g.buckets.size();
+    else out->n_fused_groups += 1;
+  }
   return TNQ_OK;
 }
 
@@ -168,11 +174,13 @@ tnq_status tnq_plan_buckets(const tnq_plan* P, int32_t* bag, int32_t* k, int32_t
   // one entry per summing bucket (product-only splits fold into their bucket)
   size_t i = 0;
   int extra_k = 0;
-  for (const auto& b : P->prog.buckets) {
+  for (size_t bi = 0; bi < P->prog.buckets.size(); ++bi) {
+    const auto& b = P->prog.buckets[bi];
     if (!b.sum) { extra_k += b.k - 1; continue; }
+    const int g = P->prog.group_of.empty() ? -1 : P->prog.group_of[bi];
+    if (gemm) gemm[i] = (g >= 0 && P->prog.groups[g].gemm) ? 1 : 0;
     if (bag) bag[i] = b.r;
     if (k) k[i] = b.k + extra_k;
-    if (gemm) gemm[i] = 0;
     extra_k = 0;
     ++i;
   }

@@ -12,6 +12,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
 #include <string>
@@ -216,6 +217,42 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const GemmArgs a) {
       for (int i = 0; i < 32; i += 4)
         *reinterpret_cast<float4*>(crow + chunk * 32 + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
     }
+  } else if (!s_fail) {
+    // bucket epilogue: row = X assignment, column pair (2n, 2n+1) = (Re, Im) of Y assignment n
+    const GemmEpilogue& ep = a.ep;
+    const int m = rt * GT_ROWS + warp * 32 + lane;
+    const long long item = b >> ep.ns, sidx = b & ((1ll << ep.ns) - 1);
+    float tmax = 0.f;
+    const bool row_ok = m < (1 << ep.nx);
+    long long base = ep.dep ? item * ep.istride : 0ll;
+    for (int i = 0; i < ep.ns; ++i)
+      if ((sidx >> i) & 1) base += ep.s[i];
+    for (int i = 0; i < ep.nx; ++i)
+      if ((m >> i) & 1) base += ep.x[i];
+#pragma unroll 1
+    for (int chunk = 0; chunk < 4; ++chunk) {
+      float v[32];
+      // warp-collective: every lane loads, whether or not its row is written
+      tmem_ld32(tmem_d + ((uint32_t)(warp * 32) << 16) + (uint32_t)(chunk * 32), v);
+      if (row_ok) {
+#pragma unroll 1
+        for (int i = 0; i < 32; i += 2) {
+          const int n = (ct * 128 + chunk * 32 + i) >> 1;
+          if (n >= (1 << ep.ny)) break;
+          long long off = base;
+          for (int q = 0; q < ep.ny; ++q)
+            if ((n >> q) & 1) off += ep.y[q];
+          ep.out[off] = make_float2(v[i], v[i + 1]);
+          tmax = fmaxf(tmax, fmaxf(fabsf(v[i]), fabsf(v[i + 1])));
+        }
+      }
+    }
+    for (int off = 16; off > 0; off >>= 1) tmax = fmaxf(tmax, __shfl_xor_sync(0xffffffffu, tmax, off));
+    if (lane == 0 && tmax > 0.f) {
+      unsigned* p = &ep.meta_m[(long long)ep.meta * ep.B + (ep.dep ? item : 0ll)];
+      const unsigned bits = __float_as_uint(tmax);
+      if (bits > *reinterpret_cast<volatile unsigned*>(p)) atomicMax(p, bits);
+    }
   }
   tc_fence_before();
   __syncthreads();
@@ -252,6 +289,123 @@ __global__ void k_pack_real(const float* __restrict__ X, int rows, int K, int ba
   }
 }
 
+
+// Power-of-two scale bringing a tensor with largest |re|,|im| bits `mbits`
+// into [0.5, 1) (same rule as the bucket kernels).
+__device__ __forceinline__ float pack_scale(unsigned mbits, int* mexp) {
+  if (mbits == 0u) {
+    *mexp = 0;
+    return 1.f;
+  }
+  int ex = (int)((mbits >> 23) & 0xffu);
+  if (ex == 0) ex = 1;
+  int m = ex - 126;
+  if (m > 126) m = 126;
+  *mexp = m;
+  return __int_as_float((127 - m) << 23);
+}
+
+__device__ __forceinline__ float2 operand_value(const GemmOperand& o, long long item, long long s, long long r,
+                                                long long k, int ns, int nr, int nk, float f) {
+  long long off = o.dep ? item * o.istride : 0ll;
+  for (int i = 0; i < ns; ++i)
+    if ((s >> i) & 1) off += o.sstride[i];
+  for (int i = 0; i < nr; ++i)
+    if ((r >> i) & 1) off += o.rstride[i];
+  for (int i = 0; i < nk; ++i)
+    if ((k >> i) & 1) off += o.kstride[i];
+  const float2 v = o.ptr[off];
+  return make_float2(v.x * f, v.y * f);
+}
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+template <int KIND>
+__device__ __forceinline__ void store_split(void* hi, void* lo, size_t off, float x) {
+  if (KIND == GEMM_BF16) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+    *reinterpret_cast<__nv_bfloat16*>((char*)hi + off) = h;
+    *reinterpret_cast<__nv_bfloat16*>((char*)lo + off) = l;
+  } else {
+    uint32_t h, l;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+    const float rest = x - __uint_as_float(h);
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(rest));
+    *reinterpret_cast<uint32_t*>((char*)hi + off) = h;
+    *reinterpret_cast<uint32_t*>((char*)lo + off) = l;
+  }
+}
+
+// side 0: A rows = X assignments, columns [Re | Im] over K.
+// side 1: B rows 2n, 2n+1 = [Re | -Im], [Im | Re] over K for Y assignment n.
+template <int KIND>
+__global__ void k_gemm_pack(const GemmBucketArgs g, int side) {
+  const int esize = KIND == GEMM_BF16 ? 2 : 4;
+  const GemmOperand* ops = side == 0 ? g.a : g.b;
+  const int nops = side == 0 ? g.na : g.nb;
+  const int nr = side == 0 ? g.nx : g.ny;
+  const long long rows = side == 0 ? g.m_pad : g.n_pad;  // complex rows
+  const long long batch = (long long)g.items << g.ns;
+  const long long n = batch * rows * g.k_pad;
+  const int kt_count = 2 * g.k_pad * esize / GT_KBYTES;
+  const int rt_count = (int)((side == 0 ? rows : 2 * rows) / GT_ROWS);
+  void* hi = side == 0 ? g.a_hi : g.b_hi;
+  void* lo = side == 0 ? g.a_lo : g.b_lo;
+  if (side == 0 && blockIdx.x == 0) {
+    // output exponent per item: sum over every operand of its exponent and scale shift
+    for (int it = threadIdx.x; it < g.items; it += blockDim.x) {
+      int e = 0;
+      for (int j = 0; j < g.na + g.nb; ++j) {
+        const GemmOperand& o = j < g.na ? g.a[j] : g.b[j - g.na];
+        if (o.meta < 0) continue;
+        const long long row = (long long)o.meta * g.B + (o.dep ? it : 0);
+        int m;
+        pack_scale(g.meta_m[row], &m);
+        e += g.meta_e[row] + m;
+      }
+      g.meta_e[(long long)g.out_meta * g.B + (g.out_dep ? it : 0)] = e;
+    }
+  }
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long k = i % g.k_pad;
+    const long long r = (i / g.k_pad) % rows;
+    const long long bi = i / ((long long)g.k_pad * rows);
+    const long long item = bi >> g.ns, s = bi & ((1ll << g.ns) - 1);
+    float2 v = make_float2(0.f, 0.f);
+    if (r < (1ll << nr) && k < (1ll << g.nk)) {
+      v = make_float2(1.f, 0.f);
+      for (int j = 0; j < nops; ++j) {
+        const GemmOperand& o = ops[j];
+        float f = 1.f;
+        if (o.meta >= 0) {
+          int m;
+          f = pack_scale(g.meta_m[(long long)o.meta * g.B + (o.dep ? item : 0ll)], &m);
+        }
+        v = cmulf(v, operand_value(o, item, s, r, k, g.ns, nr, g.nk, f));
+      }
+    }
+    const size_t tb = (size_t)GT_TILE_BYTES;
+    if (side == 0) {
+      const size_t t0 = ((size_t)(bi * rt_count + r / GT_ROWS) * kt_count);
+      const int kre = (int)k, kim = (int)(g.k_pad + k);
+      store_split<KIND>(hi, lo, (t0 + (size_t)(kre * esize / GT_KBYTES)) * tb + gt_offset((int)(r % GT_ROWS), kre, esize), v.x);
+      store_split<KIND>(hi, lo, (t0 + (size_t)(kim * esize / GT_KBYTES)) * tb + gt_offset((int)(r % GT_ROWS), kim, esize), v.y);
+    } else {
+      const long long r0 = 2 * r, r1 = 2 * r + 1;
+      const int kre = (int)k, kim = (int)(g.k_pad + k);
+      const size_t t0 = ((size_t)(bi * rt_count + r0 / GT_ROWS) * kt_count);
+      const size_t t1 = ((size_t)(bi * rt_count + r1 / GT_ROWS) * kt_count);
+      store_split<KIND>(hi, lo, (t0 + (size_t)(kre * esize / GT_KBYTES)) * tb + gt_offset((int)(r0 % GT_ROWS), kre, esize), v.x);
+      store_split<KIND>(hi, lo, (t0 + (size_t)(kim * esize / GT_KBYTES)) * tb + gt_offset((int)(r0 % GT_ROWS), kim, esize), -v.y);
+      store_split<KIND>(hi, lo, (t1 + (size_t)(kre * esize / GT_KBYTES)) * tb + gt_offset((int)(r1 % GT_ROWS), kre, esize), v.y);
+      store_split<KIND>(hi, lo, (t1 + (size_t)(kim * esize / GT_KBYTES)) * tb + gt_offset((int)(r1 % GT_ROWS), kim, esize), v.x);
+    }
+  }
+}
+
 }  // namespace
 
 void gemm_tc_launch(int kind, const GemmArgs& args, void* stream) {
@@ -264,6 +418,36 @@ void gemm_tc_launch(int kind, const GemmArgs& args, void* stream) {
     cudaFuncSetAttribute(k_gemm_tc<GEMM_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     k_gemm_tc<GEMM_TF32><<<grid, 128, SMEM_BYTES, s>>>(args);
   }
+}
+
+void gemm_bucket_launch(const GemmBucketArgs& g, const GemmEpilogue& ep, int* status, void* stream) {
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int esize = g.kind == GEMM_BF16 ? 2 : 4;
+  const long long batch = (long long)g.items << g.ns;
+  const long long na = batch * g.m_pad * g.k_pad, nb = batch * g.n_pad * g.k_pad;
+  const int blocks_a = (int)std::min<long long>((na + 255) / 256, 152 * 16);
+  const int blocks_b = (int)std::min<long long>((nb + 255) / 256, 152 * 16);
+  if (g.kind == GEMM_BF16) {
+    k_gemm_pack<GEMM_BF16><<<blocks_a, 256, 0, s>>>(g, 0);
+    k_gemm_pack<GEMM_BF16><<<blocks_b, 256, 0, s>>>(g, 1);
+  } else {
+    k_gemm_pack<GEMM_TF32><<<blocks_a, 256, 0, s>>>(g, 0);
+    k_gemm_pack<GEMM_TF32><<<blocks_b, 256, 0, s>>>(g, 1);
+  }
+  GemmArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.a_hi = g.a_hi;
+  a.a_lo = g.a_lo;
+  a.b_hi = g.b_hi;
+  a.b_lo = g.b_lo;
+  a.row_tiles_a = g.m_pad / GT_ROWS;
+  a.row_tiles_b = 2 * g.n_pad / GT_ROWS;
+  a.k_tiles = 2 * g.k_pad * esize / GT_KBYTES;
+  a.batch = (int)batch;
+  a.status = status;
+  a.out_c = nullptr;
+  a.ep = ep;
+  gemm_tc_launch(g.kind, a, stream);
 }
 
 }  // namespace tnq

@@ -30,6 +30,48 @@ __host__ __device__ inline uint32_t gt_offset(int r, int k, int esize) {
   return (uint32_t)((r >> 3) * 1024 + (kb >> 4) * 128 + (r & 7) * 16 + (kb & 15));
 }
 
+// ---- merged bucket as a complex GEMM --------------------------------------
+// out[item, S, X, Y] = Sum_K A'[item, S, X, K] B'[item, S, Y, K], where A' (B')
+// is the product of the large operand and the small tensors folded into its
+// side, each scaled by its power-of-two factor. Complex through the real
+// embedding: A_real = [Re A' | Im A'] (rows X), B rows interleaved
+// [Re B' | -Im B'], [Im B' | Re B'], so C columns (2n, 2n+1) = (Re, Im) of out.
+constexpr int GB_BITS = 16;   // most variables in one of S (with item bits), X, Y, K
+constexpr int GB_SIDE = 17;   // large operand + up to 16 small tensors per side
+
+struct GemmOperand {
+  const float2* ptr;
+  long long istride;           // per item (0 when item-invariant)
+  long long sstride[GB_BITS];  // per batch variable
+  long long rstride[GB_BITS];  // per row (X) or column (Y) variable
+  long long kstride[GB_BITS];  // per summed variable
+  int meta;                    // meta row (-1: leaf, unit scale)
+  int dep;
+};
+
+struct GemmBucketArgs {
+  GemmOperand a[GB_SIDE], b[GB_SIDE];
+  int na, nb;
+  int ns, nx, ny, nk;          // variable counts
+  int items;                   // items of the output (1 when item-invariant)
+  int m_pad, n_pad, k_pad;     // padded complex sizes (rows, columns, K)
+  int kind;
+  void *a_hi, *a_lo, *b_hi, *b_lo;
+  int out_meta, out_dep, B;
+  int* meta_e;
+  unsigned* meta_m;
+};
+
+// Epilogue data of a bucket GEMM (in GemmArgs when out_c is null).
+struct GemmEpilogue {
+  float2* out;
+  long long istride;
+  long long s[GB_BITS], x[GB_BITS], y[GB_BITS];
+  int ns, nx, ny;
+  int meta, dep, B;
+  unsigned* meta_m;
+};
+
 // Device-side status word: 0 ok, 1 a bulk-copy wait gave up, 2 an MMA wait gave up.
 struct GemmArgs {
   const void* a_hi;
@@ -45,9 +87,14 @@ struct GemmArgs {
   // `out_c` is set; the bucket path supplies its own epilogue data instead
   float* out_c;
   long long ldc;
+  GemmEpilogue ep;  // used when out_c is null
 };
 
 // Launches C = sum_passes A_p B_p^T for every batch (grid = col tiles x row tiles x batch).
 void gemm_tc_launch(int kind, const GemmArgs& args, void* stream);
+
+// Packs both operands, writes the output exponents and runs the GEMM with the
+// bucket epilogue on `stream`.
+void gemm_bucket_launch(const GemmBucketArgs& g, const GemmEpilogue& ep, int* status, void* stream);
 
 }  // namespace tnq

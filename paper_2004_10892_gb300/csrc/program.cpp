@@ -238,10 +238,15 @@ static std::vector<int> bag_of(const Program& P, const PBucket& b) {
 void fuse_chains(Program& P, const std::vector<int>& order, int min_rank) {
   const int nb = (int)P.buckets.size();
   if (P.bytes_unfused == 0) P.bytes_unfused = P.bytes_per_slice;
-  P.groups.clear();
+  std::vector<FusedGroup> gemms;
+  for (const auto& g : P.groups)
+    if (g.gemm) gemms.push_back(g);
+  P.groups = gemms;
   P.group_of.assign(nb, -1);
+  for (size_t gi = 0; gi < P.groups.size(); ++gi)
+    for (int b : P.groups[gi].buckets) P.group_of[b] = (int)gi;
   if (min_rank <= 0) {
-    set_groups(P, {});
+    set_groups(P, gemms);
     return;
   }
   std::vector<int> pos(order.size() + 1, 0);
@@ -299,6 +304,95 @@ void fuse_chains(Program& P, const std::vector<int>& order, int min_rank) {
     P.groups.push_back(g);
   }
   set_groups(P, std::vector<FusedGroup>(P.groups));
+}
+
+void find_gemm_chains(Program& P, const std::vector<int>& order, int min_k_log2, int min_rank) {
+  const int nb = (int)P.buckets.size();
+  if (P.bytes_unfused == 0) P.bytes_unfused = P.bytes_per_slice;
+  if (P.group_of.size() != (size_t)nb) P.group_of.assign(nb, -1);
+  int maxv = 0;
+  for (int v : order) maxv = std::max(maxv, v);
+  std::vector<int> pos(maxv + 1, -1);
+  for (size_t i = 0; i < order.size(); ++i) pos[order[i]] = (int)i;
+  auto by_pos = [&](int a, int b) { return pos[a] < pos[b]; };
+  auto sorted = [&](std::vector<int> v) {
+    std::sort(v.begin(), v.end());
+    return v;
+  };
+  auto subset = [](const std::vector<int>& a, const std::vector<int>& b) {  // both sorted
+    return std::includes(b.begin(), b.end(), a.begin(), a.end());
+  };
+  std::vector<FusedGroup> found(P.groups);
+  for (int i = 0; i < nb; ++i) {
+    if (P.group_of[i] >= 0 || !P.buckets[i].sum) continue;
+    const PBucket& b0 = P.buckets[i];
+    std::vector<int> big, small;
+    for (int t : b0.inputs) (P.tensors[t].rank() >= min_rank ? big : small).push_back(t);
+    if (big.size() != 2) continue;
+    const std::vector<int> Av = sorted(P.tensors[big[0]].vars), Bv = sorted(P.tensors[big[1]].vars);
+    std::vector<int> S;
+    std::set_intersection(Av.begin(), Av.end(), Bv.begin(), Bv.end(), std::back_inserter(S));
+    FusedGroup g;
+    g.gemm = true;
+    g.ga = big[0];
+    g.gb = big[1];
+    auto fold = [&](int t) {
+      if (P.tensors[t].rank() > 2) return false;
+      const std::vector<int> v = sorted(P.tensors[t].vars);
+      if (subset(v, Av)) g.a_side.push_back(t);
+      else if (subset(v, Bv)) g.b_side.push_back(t);
+      else return false;
+      return true;
+    };
+    bool ok = true;
+    for (int t : small) ok = ok && fold(t);
+    if (!ok || g.a_side.size() > (size_t)GEMM_SIDE_MAX || g.b_side.size() > (size_t)GEMM_SIDE_MAX) continue;
+    g.buckets = {i};
+    g.kvars = {b0.u};
+    int cur = i;
+    while (true) {
+      const int c = P.tensors[P.buckets[cur].output].consumer;
+      if (c < 0 || P.group_of[c] >= 0 || !P.buckets[c].sum) break;
+      const PBucket& bc = P.buckets[c];
+      if (!std::binary_search(S.begin(), S.end(), bc.u)) break;
+      const size_t na = g.a_side.size(), nbs = g.b_side.size();
+      bool fits = true;
+      for (int t : bc.inputs)
+        if (t != P.buckets[cur].output) fits = fits && fold(t);
+      if (g.a_side.size() > (size_t)GEMM_SIDE_MAX || g.b_side.size() > (size_t)GEMM_SIDE_MAX) fits = false;
+      if (!fits) {
+        g.a_side.resize(na);
+        g.b_side.resize(nbs);
+        break;
+      }
+      g.buckets.push_back(c);
+      g.kvars.push_back(bc.u);
+      cur = c;
+    }
+    if ((int)g.kvars.size() < min_k_log2) continue;
+    g.output = P.buckets[g.buckets.back()].output;
+    const std::vector<int> K = sorted(g.kvars);
+    for (int v : S)
+      if (!std::binary_search(K.begin(), K.end(), v)) g.svars.push_back(v);
+    for (int v : Av)
+      if (!std::binary_search(S.begin(), S.end(), v)) g.xvars.push_back(v);
+    for (int v : Bv)
+      if (!std::binary_search(S.begin(), S.end(), v)) g.yvars.push_back(v);
+    for (auto* v : {&g.kvars, &g.svars, &g.xvars, &g.yvars}) std::sort(v->begin(), v->end(), by_pos);
+    // the chain's result holds exactly S' + X + Y
+    if (P.tensors[g.output].rank() != (int)(g.svars.size() + g.xvars.size() + g.yvars.size())) continue;
+    if (g.xvars.size() > 12 || g.yvars.size() > 12 || g.kvars.size() > 12 ||
+        g.svars.size() > (size_t)GEMM_BITS_MAX)
+      continue;
+    g.ext_inputs = {g.ga, g.gb};
+    g.ext_inputs.insert(g.ext_inputs.end(), g.a_side.begin(), g.a_side.end());
+    g.ext_inputs.insert(g.ext_inputs.end(), g.b_side.begin(), g.b_side.end());
+    g.local_vars = g.kvars;
+    const int gi = (int)found.size();
+    for (int b : g.buckets) P.group_of[b] = gi;
+    found.push_back(g);
+  }
+  set_groups(P, found);
 }
 
 void set_groups(Program& P, const std::vector<FusedGroup>& groups) {

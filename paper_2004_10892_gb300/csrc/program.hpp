@@ -92,9 +92,17 @@ constexpr int GL_MAX = 13;   // local variables of a group (stage outputs have <
 constexpr int GM_MAX = 8;    // buckets per group
 constexpr int GL_OUT_MIN = 8;  // output variables a group keeps local (>= one entry per thread in the last stage)
 constexpr int GIN_MAX = 16;  // tensors a group reads from memory
+constexpr int GEMM_SIDE_MAX = 16;  // small tensors folded into one GEMM operand
+constexpr int GEMM_BITS_MAX = 16;  // variables in one of a GEMM group's batch / row / column / summed sets
 
 struct FusedGroup {
   std::vector<int> buckets;     // chain order; the group runs at the last bucket's position
+  // GEMM form (tensor cores): the chain's product is Sum_K A[S,X,K] B[S,Y,K]
+  // with small tensors folded into A or B
+  bool gemm = false;
+  int ga = -1, gb = -1;                   // the two large operands
+  std::vector<int> a_side, b_side;        // small tensors multiplied into A / B
+  std::vector<int> kvars, svars, xvars, yvars;  // summed, batch, row and column variables (by position)
   std::vector<int> local_vars;  // L: the eliminated variables + the earliest output variables, by position
   std::vector<int> tile_vars;   // H: the other output variables, by position
   std::vector<int> ext_inputs;  // tensors read from memory, in stage order
@@ -113,6 +121,12 @@ struct Program {
   double bytes_unfused = 0;  // bytes_per_slice with no fused group
   int max_bag = 0;
 };
+
+// GEMM pass: chains whose product is a batched contraction of two tensors of
+// rank >= min_rank over >= min_k_log2 summed variables (every further bucket
+// eliminates a variable both hold and adds only rank <= 2 tensors whose
+// variables lie in one of them) become GEMM groups. Run before fuse_chains.
+void find_gemm_chains(Program& prog, const std::vector<int>& order, int min_k_log2, int min_rank);
 
 // Replaces the program's fused groups (recomputes group_of and bytes_per_slice).
 void set_groups(Program& prog, const std::vector<FusedGroup>& groups);

@@ -26,11 +26,15 @@
 #include <vector>
 
 #include "../../include/tnq.h"
+#include "gemm_tc.cuh"
 #include "plan.hpp"
+
+extern "C" const char* tnq_last_error(void);
 
 namespace tnq {
 
 constexpr int GMAX = 52;  // index bits of one bucket launch (output bits + item bits)
+static_assert(GB_SIDE >= GEMM_SIDE_MAX + 1 && GB_BITS >= GEMM_BITS_MAX, "GEMM limits of planner and kernels differ");
 constexpr int TPB = 256;  // threads per block of the bucket kernel
 constexpr int MAX_ITEM_BITS = 16;
 
@@ -596,14 +600,36 @@ struct Layout {
   std::vector<long long> off;   // element offset per tensor
   std::vector<char> dep;        // item-dependent per tensor
   long long arena_elems = 0;
+  long long gemm_off = 0;        // element offset of the GEMM operand scratch inside the arena
   size_t hdr_off = 0, bits_off = 0, scalar_off = 0, res_off = 0, part_off = 0, meta_e_off = 0, meta_m_off = 0,
-         arena_off = 0, total = 0;
+         arena_off = 0, status_off = 0, total = 0;
   int n_words = 1, n_rows = 1;
 };
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 bool tensor_dep(const PTensor& t, int mode) { return t.dep_slice || (mode == 1 && t.dep_bits); }
+
+// Padded sizes of a GEMM group (complex rows, columns and K; operand bytes).
+struct GemmShape {
+  int kind = 0, m_pad = 0, n_pad = 0, k_pad = 0;
+  long long batch = 0;
+  size_t a_bytes = 0, b_bytes = 0;  // one of hi / lo
+};
+
+GemmShape gemm_shape(const tnq_plan& P, const FusedGroup& g, int items) {
+  GemmShape s;
+  s.kind = P.opts.precision == TNQ_PREC_SPLIT_TF32 ? GEMM_TF32 : GEMM_BF16;
+  const int esize = s.kind == GEMM_BF16 ? 2 : 4;
+  auto up = [](long long x, long long a) { return (x + a - 1) / a * a; };
+  s.m_pad = (int)up(1ll << g.xvars.size(), GT_ROWS);
+  s.n_pad = (int)up(1ll << g.yvars.size(), GT_ROWS / 2);
+  s.k_pad = (int)up(1ll << g.kvars.size(), GT_KBYTES / (2 * esize));
+  s.batch = (long long)items << g.svars.size();
+  s.a_bytes = (size_t)s.batch * s.m_pad * 2 * s.k_pad * esize;
+  s.b_bytes = (size_t)s.batch * 2 * s.n_pad * 2 * s.k_pad * esize;
+  return s;
+}
 
 Layout make_layout(const tnq_plan& P, int mode, int B) {
   const Program& prog = P.prog;
@@ -645,10 +671,20 @@ Layout make_layout(const tnq_plan& P, int mode, int B) {
     L.arena_elems = std::max(L.arena_elems, cand + size[t]);
     placed.push_back(t);
   }
+  // GEMM operand scratch (shared by every GEMM step): hi/lo of both operands
+  long long gemm_elems = 0;
+  for (const FusedGroup& g : prog.groups) {
+    if (!g.gemm) continue;
+    const GemmShape sh = gemm_shape(P, g, L.dep[g.output] ? B : 1);
+    gemm_elems = std::max<long long>(gemm_elems, (long long)(2 * (sh.a_bytes + sh.b_bytes) / 8));
+  }
+  L.gemm_off = (long long)align_up((size_t)L.arena_elems, 128);
+  if (gemm_elems) L.arena_elems = L.gemm_off + gemm_elems;
   L.n_words = (P.net.n_qubits + 31) / 32;
   L.n_rows = B + 1;
   size_t o = 0;
-  L.hdr_off = o; o = align_up(o + sizeof(BatchHdr), 256);
+  L.hdr_off = o; o = align_up(o + sizeof(BatchHdr), 128);
+  L.status_off = o; o = align_up(o + 4, 256);
   L.bits_off = o; o = align_up(o + (size_t)L.n_rows * L.n_words * 4, 256);
   L.scalar_off = o; o = align_up(o + (size_t)B * 16, 256);
   L.res_off = o; o = align_up(o + (size_t)B * 16, 256);
@@ -678,7 +714,10 @@ struct ExecConfig {
   std::vector<GParams> gp;           // per fused-group step
   std::vector<int> gsmem;            // dynamic shared memory bytes per fused-group step
   int group_grid = 152 * 4;          // persistent blocks of k_group (SMs x resident blocks)
-  std::vector<std::pair<int, int>> steps;  // (0, index into kp) or (1, index into gp), program order
+  std::vector<GemmBucketArgs> gb;    // per GEMM step (pointers are arena offsets)
+  std::vector<GemmEpilogue> ge;
+  std::vector<std::pair<int, int>> steps;  // (0, kp index), (1, gp index) or (2, gb index), program order
+  std::vector<int> step_group;       // group index of each step (-1 for a single bucket)
   std::vector<double> step_bytes;    // algorithmic bytes of each step (all items)
   std::vector<double> step_flops;    // algorithmic flops of each step (all items; cost model of Section IV)
   void* ws = nullptr;                // workspace the graph was captured for
@@ -901,6 +940,91 @@ static GParams group_gparams(const tnq_plan& P, const Layout& L, const FusedGrou
   return G;
 }
 
+// GEMM-step parameters of a GEMM group, with pointers holding byte offsets
+// from the arena base (rebased per call). Host only.
+static bool gemm_params(const tnq_plan& P, const Layout& L, const FusedGroup& g, GemmBucketArgs& G,
+                        GemmEpilogue& E) {
+  const Program& prog = P.prog;
+  std::memset(&G, 0, sizeof(G));
+  std::memset(&E, 0, sizeof(E));
+  const int items = L.dep[g.output] ? L.B : 1;
+  const GemmShape sh = gemm_shape(P, g, items);
+  if (g.svars.size() > (size_t)GB_BITS || g.xvars.size() > (size_t)GB_BITS || g.yvars.size() > (size_t)GB_BITS ||
+      g.kvars.size() > (size_t)GB_BITS || 1 + g.a_side.size() > (size_t)GB_SIDE || 1 + g.b_side.size() > (size_t)GB_SIDE) {
+    set_error("GEMM group: too many variables or folded tensors");
+    return false;
+  }
+  auto operand = [&](int tid, const std::vector<int>& rows, GemmOperand& o) {
+    const PTensor& x = prog.tensors[tid];
+    o.ptr = reinterpret_cast<const float2*>((size_t)L.off[tid] * 8);
+    o.dep = L.dep[tid];
+    o.istride = 1ll << x.rank();
+    o.meta = x.leaf_gate >= 0 ? -1 : tid;
+    auto fill = [&](const std::vector<int>& vars, long long* st) {
+      for (size_t i = 0; i < vars.size(); ++i) {
+        const int p = index_in(x.vars, vars[i]);
+        st[i] = p < 0 ? 0 : (1ll << p);
+      }
+    };
+    fill(g.svars, o.sstride);
+    fill(rows, o.rstride);
+    fill(g.kvars, o.kstride);
+    // every variable of the operand is a batch, row or summed variable
+    for (int v : x.vars)
+      if (index_in(g.svars, v) < 0 && index_in(rows, v) < 0 && index_in(g.kvars, v) < 0) {
+        set_error("GEMM group: operand variable outside its batch/row/summed sets");
+        return false;
+      }
+    return true;
+  };
+  G.na = 1 + (int)g.a_side.size();
+  G.nb = 1 + (int)g.b_side.size();
+  if (!operand(g.ga, g.xvars, G.a[0]) || !operand(g.gb, g.yvars, G.b[0])) return false;
+  for (size_t j = 0; j < g.a_side.size(); ++j)
+    if (!operand(g.a_side[j], g.xvars, G.a[1 + j])) return false;
+  for (size_t j = 0; j < g.b_side.size(); ++j)
+    if (!operand(g.b_side[j], g.yvars, G.b[1 + j])) return false;
+  G.ns = (int)g.svars.size();
+  G.nx = (int)g.xvars.size();
+  G.ny = (int)g.yvars.size();
+  G.nk = (int)g.kvars.size();
+  G.items = items;
+  G.m_pad = sh.m_pad;
+  G.n_pad = sh.n_pad;
+  G.k_pad = sh.k_pad;
+  G.kind = sh.kind;
+  const size_t base = (size_t)L.gemm_off * 8;
+  G.a_hi = reinterpret_cast<void*>(base);
+  G.a_lo = reinterpret_cast<void*>(base + sh.a_bytes);
+  G.b_hi = reinterpret_cast<void*>(base + 2 * sh.a_bytes);
+  G.b_lo = reinterpret_cast<void*>(base + 2 * sh.a_bytes + sh.b_bytes);
+  G.out_meta = g.output;
+  G.out_dep = L.dep[g.output];
+  G.B = L.B;
+  const PTensor& o = prog.tensors[g.output];
+  E.out = reinterpret_cast<float2*>((size_t)L.off[g.output] * 8);
+  E.istride = 1ll << o.rank();
+  auto ofill = [&](const std::vector<int>& vars, long long* st) {
+    for (size_t i = 0; i < vars.size(); ++i) {
+      const int p = index_in(o.vars, vars[i]);
+      if (p < 0) return false;
+      st[i] = 1ll << p;
+    }
+    return true;
+  };
+  if (!ofill(g.svars, E.s) || !ofill(g.xvars, E.x) || !ofill(g.yvars, E.y)) {
+    set_error("GEMM group: output misses a batch/row/column variable");
+    return false;
+  }
+  E.ns = G.ns;
+  E.nx = G.nx;
+  E.ny = G.ny;
+  E.meta = g.output;
+  E.dep = G.out_dep;
+  E.B = L.B;
+  return true;
+}
+
 static bool build_steps(const tnq_plan& P, const Layout& L, ExecConfig& C) {
   const Program& prog = P.prog;
   C.kp.clear();
@@ -908,6 +1032,9 @@ static bool build_steps(const tnq_plan& P, const Layout& L, ExecConfig& C) {
   C.gp.clear();
   C.gsmem.clear();
   C.steps.clear();
+  C.step_group.clear();
+  C.gb.clear();
+  C.ge.clear();
   C.step_bytes.clear();
   C.step_flops.clear();
   auto tbytes = [&](int t) { return std::ldexp(8.0, prog.tensors[t].rank()) * (L.dep[t] ? L.B : 1); };
@@ -923,18 +1050,34 @@ static bool build_steps(const tnq_plan& P, const Layout& L, ExecConfig& C) {
       KParams k = single_kparams(P, L, prog.buckets[bi], &ok);
       if (!ok) { set_error("bucket too large for one launch"); return false; }
       C.steps.push_back({0, (int)C.kp.size()});
+      C.step_group.push_back(-1);
       C.kp.push_back(k);
       C.kshape.push_back({prog.buckets[bi].k, k.G > 8 ? 12 : 8});
       double by = tbytes(prog.buckets[bi].output);
       for (int t : prog.buckets[bi].inputs) by += tbytes(t);
       C.step_bytes.push_back(by);
       C.step_flops.push_back(bflops((int)bi));
+    } else if ((int)bi == prog.groups[gi].buckets.back() && prog.groups[gi].gemm) {
+      GemmBucketArgs G;
+      GemmEpilogue E;
+      if (!gemm_params(P, L, prog.groups[gi], G, E)) return false;
+      C.steps.push_back({2, (int)C.gb.size()});
+      C.step_group.push_back(gi);
+      C.gb.push_back(G);
+      C.ge.push_back(E);
+      double by = tbytes(prog.groups[gi].output);
+      for (int t : prog.groups[gi].ext_inputs) by += tbytes(t);
+      C.step_bytes.push_back(by);
+      double fl = 0;
+      for (int b : prog.groups[gi].buckets) fl += bflops(b);
+      C.step_flops.push_back(fl);
     } else if ((int)bi == prog.groups[gi].buckets.back()) {
       bool ok;
       int smem = 0;
       GParams g = group_gparams(P, L, prog.groups[gi], &ok, &smem);
       if (!ok) { set_error("fused group does not fit one launch"); return false; }
       C.steps.push_back({1, (int)C.gp.size()});
+      C.step_group.push_back(gi);
       C.gp.push_back(g);
       C.gsmem.push_back(smem);
       double by = tbytes(prog.groups[gi].output);
@@ -956,7 +1099,7 @@ static std::string validate_config(const tnq_plan& P, int mode, int B) {
   const Layout L = make_layout(P, mode, B);
   ExecConfig C;
   C.L = L;
-  if (!build_steps(P, L, C)) return "build_steps failed";
+  if (!build_steps(P, L, C)) return std::string("build_steps failed: ") + tnq_last_error();
   const Program& prog = P.prog;
   const Liveness LV = tensor_liveness(prog);
   auto alloc = [&](int t) { return ((long long)1 << prog.tensors[t].rank()) * (L.dep[t] ? B : 1); };
@@ -978,9 +1121,11 @@ static std::string validate_config(const tnq_plan& P, int mode, int B) {
         if (k.sum && (k.stride[j][i] & 1)) return "odd stride in a summing bucket";
     }
   }
-  for (size_t gi = 0; gi < C.gp.size(); ++gi) {
+  for (size_t si = 0; si < C.steps.size(); ++si) {
+    if (C.steps[si].first != 1) continue;
+    const size_t gi = (size_t)C.steps[si].second;
     const GParams& G = C.gp[gi];
-    const FusedGroup& g = prog.groups[gi];
+    const FusedGroup& g = prog.groups[C.step_group[si]];
     const long long items = G.out_dep ? B : 1;
     // largest index of every memory operand over all tiles, items and stages
     std::vector<long long> in_max(G.n_gin, 0);
@@ -1024,6 +1169,39 @@ static std::string validate_config(const tnq_plan& P, int mode, int B) {
     for (int b = 0; b < G.st[G.n_st - 1].nbits; ++b) om += G.out_cstride[b];
     if (om >= alloc(g.output)) return "group " + std::to_string(gi) + ": output overflows";
     if (C.gsmem[gi] > 200 * 1024) return "group shared memory";
+  }
+  for (size_t gi = 0; gi < C.gb.size(); ++gi) {
+    const GemmBucketArgs& G = C.gb[gi];
+    const GemmEpilogue& E = C.ge[gi];
+    int grp = -1;
+    for (size_t i = 0, n2 = 0; i < C.steps.size(); ++i)
+      if (C.steps[i].first == 2 && n2++ == gi) grp = C.step_group[i];
+    const FusedGroup& g = prog.groups[grp];
+    auto omax = [&](const GemmOperand& o, int nr) {
+      long long m = o.dep ? (long long)(G.items - 1) * o.istride : 0;
+      for (int i = 0; i < G.ns; ++i) m += o.sstride[i];
+      for (int i = 0; i < nr; ++i) m += o.rstride[i];
+      for (int i = 0; i < G.nk; ++i) m += o.kstride[i];
+      return m;
+    };
+    std::vector<int> a_ids{g.ga}, b_ids{g.gb};
+    a_ids.insert(a_ids.end(), g.a_side.begin(), g.a_side.end());
+    b_ids.insert(b_ids.end(), g.b_side.begin(), g.b_side.end());
+    for (int j = 0; j < G.na; ++j)
+      if (omax(G.a[j], G.nx) >= alloc(a_ids[j])) return "GEMM group: A operand overflows";
+    for (int j = 0; j < G.nb; ++j)
+      if (omax(G.b[j], G.ny) >= alloc(b_ids[j])) return "GEMM group: B operand overflows";
+    long long om = E.dep ? (long long)(G.items - 1) * E.istride : 0;
+    for (int i = 0; i < E.ns; ++i) om += E.s[i];
+    for (int i = 0; i < E.nx; ++i) om += E.x[i];
+    for (int i = 0; i < E.ny; ++i) om += E.y[i];
+    if (om >= alloc(g.output)) return "GEMM group: output overflows";
+    const GemmShape sh = gemm_shape(P, g, G.items);
+    if ((long long)((size_t)L.gemm_off * 8 + 2 * (sh.a_bytes + sh.b_bytes)) > L.arena_elems * 8)
+      return "GEMM scratch outside the arena";
+    if (G.m_pad % GT_ROWS || (2 * G.n_pad) % GT_ROWS || (2 * G.k_pad * (G.kind == GEMM_BF16 ? 2 : 4)) % GT_KBYTES)
+      return "GEMM padding";
+    if ((L.gemm_off * 8) % 1024) return "GEMM scratch alignment";
   }
   const int T = (int)prog.tensors.size();
   for (int t = 0; t < T; ++t) {
@@ -1128,7 +1306,8 @@ static void launch_bucket(const KParams& k, int n_in, int LT, cudaStream_t s) {
 
 // Launches step i of the configuration (a single bucket or a fused group)
 // with its pointers rebased on the arena.
-static void launch_step(const ExecConfig& C, int i, float2* arena, int* me, unsigned* mm, cudaStream_t s) {
+static void launch_step(const ExecConfig& C, int i, float2* arena, int* me, unsigned* mm, int* status,
+                        cudaStream_t s) {
   char* base = reinterpret_cast<char*>(arena);
   const auto st = C.steps[i];
   if (st.first == 0) {
@@ -1139,6 +1318,21 @@ static void launch_step(const ExecConfig& C, int i, float2* arena, int* me, unsi
     k.meta_e = me;
     k.meta_m = mm;
     launch_bucket(k, C.kshape[st.second].first, C.kshape[st.second].second, s);
+  } else if (st.first == 2) {
+    GemmBucketArgs g = C.gb[st.second];
+    GemmEpilogue e = C.ge[st.second];
+    auto rb = [&](const void* p) { return reinterpret_cast<const float2*>(base + reinterpret_cast<size_t>(p)); };
+    for (int j = 0; j < g.na; ++j) g.a[j].ptr = rb(g.a[j].ptr);
+    for (int j = 0; j < g.nb; ++j) g.b[j].ptr = rb(g.b[j].ptr);
+    g.a_hi = base + reinterpret_cast<size_t>(g.a_hi);
+    g.a_lo = base + reinterpret_cast<size_t>(g.a_lo);
+    g.b_hi = base + reinterpret_cast<size_t>(g.b_hi);
+    g.b_lo = base + reinterpret_cast<size_t>(g.b_lo);
+    g.meta_e = me;
+    g.meta_m = mm;
+    e.out = reinterpret_cast<float2*>(base + reinterpret_cast<size_t>(e.out));
+    e.meta_m = mm;
+    gemm_bucket_launch(g, e, status, s);
   } else {
     GParams g = C.gp[st.second];
     g.out = reinterpret_cast<float2*>(base + reinterpret_cast<size_t>(g.out));
@@ -1170,7 +1364,8 @@ static void enqueue_batch(const tnq_plan& P, ExecConfig& C, char* ws, cudaStream
     k_leaf_init<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(C.d_leaves, C.n_leaves, hdr, bits, arena, B);
   }
   k_scalar_init<<<(B + 127) / 128, 128, 0, s>>>(C.d_scalars, C.n_scalars, C.d_inout, C.n_inout, hdr, bits, scal, B);
-  for (size_t i = 0; i < C.steps.size(); ++i) launch_step(C, (int)i, arena, me, mm, s);
+  int* status = reinterpret_cast<int*>(ws + L.status_off);
+  for (size_t i = 0; i < C.steps.size(); ++i) launch_step(C, (int)i, arena, me, mm, status, s);
   const double sc = P.amp_scale_log2;  // = -n_sqrt2 / 2
   const int n_sqrt2 = (int)std::lround(-2.0 * sc);
   const int scale_exp = -(n_sqrt2 / 2), scale_half = n_sqrt2 & 1;
@@ -1313,9 +1508,9 @@ int tnq_internal_validate(const tnq_plan* plan, int mode, uint32_t batch, char* 
 // CUDA event pair around every bucket launch on `stream`. Per bucket it
 // returns the launch time (ms), the algorithmic bytes of the launch (every
 // operand read once, the output written once; 8 B per complex64) and the bag
-// size r (of the first bucket for a fused group), the algorithmic flops (cost
+// size r (of the first bucket for a group), the algorithmic flops (cost
 // model, all items) and the kind (0: one bucket, m > 1: a fused group of m
-// buckets). *out_n = launches, *out_B = batch used.
+// buckets, 100 + m: a GEMM group of m buckets). *out_n = launches, *out_B = batch.
 }  // extern "C"
 
 namespace tnq {
@@ -1362,6 +1557,7 @@ static tnq_status profile_steps(const tnq_plan* plan, const uint8_t* bits, uint6
   auto* me = reinterpret_cast<int*>(ws + L.meta_e_off);
   auto* mm = reinterpret_cast<unsigned*>(ws + L.meta_m_off);
   CU(cudaMemsetAsync(mm, 0, (size_t)T * B * 4, s));
+  CU(cudaMemsetAsync(ws + L.status_off, 0, 4, s));
   if (C->n_leaves) {
     long long n = (long long)C->n_leaves * B;
     k_leaf_init<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(C->d_leaves, C->n_leaves, hdr, bw, arena, B);
@@ -1370,7 +1566,7 @@ static tnq_status profile_steps(const tnq_plan* plan, const uint8_t* bits, uint6
   for (auto& e : ev) CU(cudaEventCreate(&e));
   for (int i = 0; i < nbk; ++i) {
     CU(cudaEventRecord(ev[2 * i], s));
-    launch_step(*C, i, arena, me, mm, s);
+    launch_step(*C, i, arena, me, mm, reinterpret_cast<int*>(ws + L.status_off), s);
     CU(cudaEventRecord(ev[2 * i + 1], s));
   }
   CU(cudaGetLastError());
@@ -1422,8 +1618,9 @@ int tnq_internal_profile(const tnq_plan* plan, const uint8_t* bits, uint64_t s0,
       kind[i] = 0;
       ++single;
     } else {
-      bag[i] = prog.buckets[prog.groups[st2.second].buckets.front()].r;
-      kind[i] = (int)prog.groups[st2.second].buckets.size();
+      const FusedGroup& g = prog.groups[C->step_group[i]];
+      bag[i] = prog.buckets[g.buckets.front()].r;
+      kind[i] = (int)g.buckets.size() + (g.gemm ? 100 : 0);
     }
   }
   *out_n = nbk;
@@ -1461,7 +1658,7 @@ tnq_status tnq_plan_autotune(tnq_plan* plan, const uint8_t* bits, void* workspac
     if (st != TNQ_OK) return st;
     std::vector<float> group_ms(all.size(), 0.f);
     for (size_t i = 0; i < C->steps.size(); ++i)
-      if (C->steps[i].first == 1) group_ms[C->steps[i].second] = tf[i];
+      if (C->step_group[i] >= 0) group_ms[C->step_group[i]] = tf[i];
     // no chain fused: one step per bucket, in bucket order
     set_groups(prog, {});
     reset_device_state(*plan);
@@ -1527,7 +1724,9 @@ tnq_status tnq_contract_sliced(const tnq_plan* plan, const uint8_t* bits, uint64
   std::vector<unsigned> words((size_t)C->L.n_words * C->L.n_rows, 0u);
   pack_bits(bits, plan->net.n_qubits, words);
   CU(cudaMemcpyAsync(ws + C->L.bits_off, words.data(), words.size() * 4, cudaMemcpyHostToDevice, s));
+  CU(cudaMemsetAsync(ws + C->L.status_off, 0, 4, s));
   std::vector<double> res(2 * (size_t)B), part(2);
+  int dev_status = 0;
   double sre = 0, sim = 0;
   std::lock_guard<std::mutex> lk(plan->dev_mu);  // one capture/launch sequence per plan at a time
   for (uint64_t base = slice_begin; base < slice_end; base += B) {
@@ -1540,9 +1739,11 @@ tnq_status tnq_contract_sliced(const tnq_plan* plan, const uint8_t* bits, uint64
     h.n_words = C->L.n_words;
     if ((st = run_batch(*plan, *C, ws, s, h)) != TNQ_OK) return st;
     CU(cudaMemcpyAsync(part.data(), ws + C->L.part_off, 16, cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(&dev_status, ws + C->L.status_off, 4, cudaMemcpyDeviceToHost, s));
     if (out_slice_amps)
       CU(cudaMemcpyAsync(res.data(), ws + C->L.res_off, 16 * (size_t)B, cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
+    if (dev_status) { set_error("a tensor-core wait timed out on the device"); return TNQ_ETIMEOUT; }
     sre += part[0];
     sim += part[1];
     if (out_slice_amps) {
@@ -1597,6 +1798,7 @@ tnq_status tnq_amplitudes_batch(const tnq_plan* const* plans, size_t n_plans, co
         for (int q = 0; q < n; ++q)
           if (pb[b * n + q]) words[(size_t)(b - b0) * C->L.n_words + (q >> 5)] |= 1u << (q & 31);
       CU(cudaMemcpyAsync(ws + C->L.bits_off, words.data(), words.size() * 4, cudaMemcpyHostToDevice, s));
+      CU(cudaMemsetAsync(ws + C->L.status_off, 0, 4, s));
       BatchHdr h;
       std::memset(&h, 0, sizeof(h));
       h.item_base = base;
@@ -1607,7 +1809,10 @@ tnq_status tnq_amplitudes_batch(const tnq_plan* const* plans, size_t n_plans, co
       h.n_words = C->L.n_words;
       if ((st = run_batch(P, *C, ws, s, h)) != TNQ_OK) return st;
       CU(cudaMemcpyAsync(part.data(), ws + C->L.part_off, 16 * (size_t)C->L.n_rows, cudaMemcpyDeviceToHost, s));
+      int dev_status = 0;
+      CU(cudaMemcpyAsync(&dev_status, ws + C->L.status_off, 4, cudaMemcpyDeviceToHost, s));
       CU(cudaStreamSynchronize(s));
+      if (dev_status) { set_error("a tensor-core wait timed out on the device"); return TNQ_ETIMEOUT; }
       for (uint64_t b = b0; b <= b1; ++b) {
         acc[2 * b] += part[2 * (b - b0)];
         acc[2 * b + 1] += part[2 * (b - b0) + 1];
@@ -1737,7 +1942,9 @@ tnq_status tnq_contract_sliced_noalloc(const tnq_plan* plan, const uint8_t* bits
   std::vector<unsigned> words((size_t)C.L.n_words * C.L.n_rows, 0u);
   pack_bits(bits, plan->net.n_qubits, words);
   CU(cudaMemcpyAsync(ws + C.L.bits_off, words.data(), words.size() * 4, cudaMemcpyHostToDevice, s));
+  CU(cudaMemsetAsync(ws + C.L.status_off, 0, 4, s));
   std::vector<double> res(2 * (size_t)B), part(2);
+  int dev_status = 0;
   double sre = 0, sim = 0;
   for (uint64_t b0 = slice_begin; b0 < slice_end; b0 += B) {
     BatchHdr h;
@@ -1750,8 +1957,10 @@ tnq_status tnq_contract_sliced_noalloc(const tnq_plan* plan, const uint8_t* bits
     enqueue_batch(*plan, C, ws, s);  // clears the atomicMax targets first
     CU(cudaGetLastError());
     CU(cudaMemcpyAsync(part.data(), ws + C.L.part_off, 16, cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(&dev_status, ws + C.L.status_off, 4, cudaMemcpyDeviceToHost, s));
     if (out_slice_amps) CU(cudaMemcpyAsync(res.data(), ws + C.L.res_off, 16 * (size_t)B, cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
+    if (dev_status) { set_error("a tensor-core wait timed out on the device"); return TNQ_ETIMEOUT; }
     sre += part[0];
     sim += part[1];
     if (out_slice_amps) {

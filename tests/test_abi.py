@@ -110,7 +110,10 @@ def test_launch_bounds_hold_on_host(tnq_lib):
     f.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32, ctypes.c_char_p, ctypes.c_size_t]
     buf = ctypes.create_string_buffer(256)
     for c, kw in [(I.random_grid_circuit(4, 4, 16, 0), {}), (I.random_grid_circuit(5, 5, 20, 1), dict(min_p=3, max_p=3)),
-                  (I.ghz(5), {}), (I.all_h(3), {}), (I.random_small_circuit(9, 90, 2), dict(min_p=2, max_p=2))]:
+                  (I.ghz(5), {}), (I.all_h(3), {}), (I.random_small_circuit(9, 90, 2), dict(min_p=2, max_p=2)),
+                  (I.random_grid_circuit(6, 6, 24, 3), dict(max_bag_log2=24, min_p=4, max_p=4, precision=1,
+                                                            gemm_min_k_log2=3)),
+                  (I.random_grid_circuit(5, 5, 20, 2), dict(precision=2, gemm_min_k_log2=3, fuse_min_rank=4))]:
         plan = tnq_lib.Plan(c, **kw)
         for mode in (0, 1):
             for B in (1, 2, 8, 64, 1024):

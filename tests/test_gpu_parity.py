@@ -253,3 +253,38 @@ def test_autotune_keeps_results(cuda, tnq_lib, oracle_lib):
     assert np.max(np.abs(after - before)) <= 1e-6 * np.max(np.abs(before))
     ref = oracle_lib.contract(circ, bits, order=plan.order(), mu=plan.sliced())
     assert rel_err(amp, ref, 36) < TOL
+
+
+SPLIT_TOL = 1e-4
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_split_precision_gemm_buckets_match_oracle(cuda, tnq_lib, oracle_lib, precision):
+    """Merged GEMM-shaped buckets on the tensor cores (3xBF16 / 3xTF32) agree
+    with the FP64 oracle within the split-precision tolerance."""
+    n_gemm = 0
+    for seed, (rows, cols, cyc, p) in enumerate([(5, 5, 20, 0), (5, 5, 20, 2), (6, 6, 24, 4)]):
+        circ = I.random_grid_circuit(rows, cols, cyc, seed)
+        bits = I.random_bitstring(circ.n_qubits, 40 + seed)
+        plan = tnq_lib.Plan(circ, min_p=p, max_p=p, precision=precision, gemm_min_k_log2=3)
+        n_gemm += plan.info()["n_gemm_buckets"]
+        amp, per = tnq_lib.contract_sliced(plan, bits, per_slice=True)
+        ref, ref_per = oracle_lib.contract(circ, bits, order=plan.order(), mu=plan.sliced(), per_slice=True)
+        n = circ.n_qubits
+        for s in range(len(per)):
+            assert rel_err(per[s], ref_per[s], n) < SPLIT_TOL, (seed, s, per[s], ref_per[s])
+        assert rel_err(amp, ref, n) < SPLIT_TOL
+        out = tnq_lib.amplitudes_batch([plan], [[bits, I.random_bitstring(n, 99)]])
+        assert rel_err(out[0], ref, n) < SPLIT_TOL
+    assert n_gemm > 0
+
+
+def test_split_precision_agrees_with_c64(cuda, tnq_lib):
+    circ = I.random_grid_circuit(6, 6, 24, 3)
+    bits = I.random_bitstring(36, 3)
+    c64 = tnq_lib.Plan(circ, max_bag_log2=24, min_p=4, max_p=4)
+    tf = tnq_lib.Plan(circ, max_bag_log2=24, min_p=4, max_p=4, precision=2, gemm_min_k_log2=3)
+    assert tf.info()["n_gemm_buckets"] > 0
+    _, a = tnq_lib.contract_sliced(c64, bits, per_slice=True)
+    _, b = tnq_lib.contract_sliced(tf, bits, per_slice=True)
+    assert np.max(np.abs(a - b)) <= SPLIT_TOL * np.max(np.abs(a))
