@@ -230,6 +230,46 @@ tnq_status tnq_contract_sliced_noalloc(const tnq_plan* plan, const uint8_t* bits
                                        uint64_t slice_begin, uint64_t slice_end, void* stream,
                                        double* out_amp, double* out_slice_amps);
 
+/* ---- learned slicing proposer -------------------------------------------
+ * Not in the paper: a small network ranks the candidates of Algorithm 2's
+ * tree-trimming step (the vertices of the largest bags, Section III.B).
+ * Features per candidate (tnq_learned_features() floats): tree-trimming length
+ * and weight, degree, position in the order, counts of maximum / near-maximum
+ * bags holding it, its elimination bag size, global sizes. Model: 3-layer MLP
+ * F -> H -> H -> 1 with ReLU, FP32; parameters one flat array W1 (H x F), b1,
+ * W2 (H x H), b2, W3 (H), b3, weights row-major (output x input). It predicts
+ * the change of log2 total contraction cost caused by deleting the candidate;
+ * TNQ_SLICER_LEARNED deletes the lowest prediction and falls back to
+ * tree-trimming when no weights are set. */
+int32_t tnq_learned_features(void);
+size_t tnq_learned_param_count(int32_t hidden);
+/* Copies the weights used by TNQ_SLICER_LEARNED (host pointer, process-wide);
+ * hidden = 0 clears them. */
+tnq_status tnq_learned_set_weights(const float* params, int32_t hidden);
+/* Training data of one circuit: follows tree-trimming for max_steps deletions
+ * and at each step writes, for every candidate, its features (F floats), its
+ * label (exact change of log2 cost: log2(2^(p+1) sum_i 2^|bag_i|) after the
+ * deletion minus log2(2^p sum_i 2^|bag_i|) before, bags from Algorithm 1) and
+ * the step index and the candidate (free-variable index, in creation order).
+ * Host buffers of cap rows; *out_n = rows produced (TNQ_EINVAL if more than cap). */
+tnq_status tnq_learned_dataset(int32_t n_qubits, const tnq_gate* gates, size_t n_gates, int32_t ordering,
+                               int32_t max_steps, float* feats, float* labels, int32_t* step, int32_t* cand,
+                               size_t cap, size_t* out_n);
+/* Host forward pass (the planner's inference) for n rows of features. */
+tnq_status tnq_learned_predict_host(const float* params, int32_t hidden, const float* x, size_t n, float* out);
+/* GPU kernels (device pointers, ordered on `stream`). work: device floats,
+ * tnq_mlp_workspace_floats(hidden, n) of them. */
+size_t tnq_mlp_workspace_floats(int32_t hidden, size_t n);
+tnq_status tnq_mlp_forward(const float* params, int32_t hidden, const float* x, size_t n, float* out, float* work,
+                           void* stream);
+/* Gradient of (1/2n) sum_i (f(x_i) - y_i)^2 for every parameter into grads
+ * (same layout as params); the loss into *loss (device float, may be NULL). */
+tnq_status tnq_mlp_backward(const float* params, int32_t hidden, const float* x, const float* y, size_t n,
+                            float* grads, float* loss, float* work, void* stream);
+/* SGD with momentum: v = mu v + g; w -= lr v (count parameters). */
+tnq_status tnq_mlp_sgd(float* params, const float* grads, float* momentum, size_t count, float lr, float mu,
+                       void* stream);
+
 /* ---- graph-level planning (host only) ---------------------------------
  * The paper's graph algorithms on an arbitrary simple graph with vertices
  * 0..n-1 and edges (edges[2e], edges[2e+1]); self-loops and repeated edges

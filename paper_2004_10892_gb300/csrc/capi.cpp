@@ -14,7 +14,7 @@
 namespace tnq {
 static thread_local std::string g_last_error;
 void set_error(const std::string& msg) { g_last_error = msg; }
-int learned_propose(void* ctx, const Graph& g, const std::vector<int>& order, const TreeDecomposition& td);
+int learned_propose(void* ctx, const Graph& g, const std::vector<int>& order, const TreeDecomposition& td, int p);
 }  // namespace tnq
 
 using namespace tnq;

@@ -349,7 +349,7 @@ DeletionResult greedy_deletion(const Graph& g0, const std::vector<int>& order0, 
       case SLICER_DEGREE: u = score_degree(g, order, pos, rng); break;
       case SLICER_DIRECT: u = score_direct(g, order, pos, rng); break;
       case SLICER_LEARNED:
-        if (proposer) u = proposer(proposer_ctx, g, order, td);
+        if (proposer) u = proposer(proposer_ctx, g, order, td, p);
         if (u < 0 || u >= g.n || pos[u] < 0) u = score_tree_trimming(td, pos, rng);  // fallback
         break;
       default: u = score_tree_trimming(td, pos, rng); break;

@@ -80,9 +80,10 @@ struct DeletionResult {
   std::vector<int> reduced_order;    // pi~ = pi minus mu
 };
 
-// Callback used by the learned slicer: returns a vertex or -1 to fall back.
+// Callback used by the learned slicer (p = vertices deleted so far): returns a
+// vertex or -1 to fall back.
 typedef int (*ProposerFn)(void* ctx, const Graph& g, const std::vector<int>& order,
-                          const TreeDecomposition& td);
+                          const TreeDecomposition& td, int p);
 
 // Algorithm 2. Deletes vertices until p >= min_p and (largest bag <= max_bag, or
 // p == max_p). max_bag <= 0 means no bag limit.

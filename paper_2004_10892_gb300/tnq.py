@@ -75,6 +75,18 @@ SIGNATURES = {
     "tnq_contract_sliced_noalloc": (ctypes.c_int, [_vp, _u8p, ctypes.c_uint64, ctypes.c_uint64, _vp, _f64p, _f64p]),
     "tnq_amplitudes_batch": (ctypes.c_int, [_P(_vp), ctypes.c_size_t, _u8p, _szp, _vp, ctypes.c_size_t, _vp,
                                             _f64p]),
+    "tnq_learned_features": (ctypes.c_int32, []),
+    "tnq_learned_param_count": (ctypes.c_size_t, [ctypes.c_int32]),
+    "tnq_learned_set_weights": (ctypes.c_int, [_P(ctypes.c_float), ctypes.c_int32]),
+    "tnq_learned_dataset": (ctypes.c_int, [ctypes.c_int32, _P(Gate), ctypes.c_size_t, ctypes.c_int32, ctypes.c_int32,
+                                           _P(ctypes.c_float), _P(ctypes.c_float), _i32p, _i32p,
+                                           ctypes.c_size_t, _szp]),
+    "tnq_learned_predict_host": (ctypes.c_int, [_P(ctypes.c_float), ctypes.c_int32, _P(ctypes.c_float),
+                                                ctypes.c_size_t, _P(ctypes.c_float)]),
+    "tnq_mlp_workspace_floats": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_size_t]),
+    "tnq_mlp_forward": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, ctypes.c_size_t, _vp, _vp, _vp]),
+    "tnq_mlp_backward": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, ctypes.c_size_t, _vp, _vp, _vp, _vp]),
+    "tnq_mlp_sgd": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_size_t, ctypes.c_float, ctypes.c_float, _vp]),
     "tnq_graph_treewidth": (ctypes.c_int, [ctypes.c_int32, ctypes.c_size_t, _i32p, _i32p, _i32p, _i32p]),
     "tnq_graph_order": (ctypes.c_int, [ctypes.c_int32, ctypes.c_size_t, _i32p, ctypes.c_int32, _i32p]),
     "tnq_graph_tree_decomposition": (ctypes.c_int, [ctypes.c_int32, ctypes.c_size_t, _i32p, _i32p, ctypes.c_int32,
