@@ -9,12 +9,14 @@ tnq_learned_set_weights, falling back to tree-trimming without weights.
 from __future__ import annotations
 
 import ctypes
+import os
 
 import numpy as np
 
 from . import tnq
 
 HIDDEN = 128
+TRAINED = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data", "proposer_h128.npy")
 
 
 def features() -> int:
@@ -123,6 +125,11 @@ def train(X, y, epochs: int = 200, batch: int = 1024, lr: float = 0.05, mu: floa
             tot += float(loss)
         hist.append(tot / max(1, n // b))
     return params.cpu().numpy(), hist
+
+
+def load_trained():
+    """Weights trained by train_proposer.py on the 500-circuit set (numpy, FP32)."""
+    return np.load(TRAINED)
 
 
 def set_weights(params, hidden: int = HIDDEN):

@@ -219,6 +219,20 @@ def _stream_ptr(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
+def default_workspace(plans, want_items: int, fraction: float = 0.5):
+    """A device workspace (torch uint8) for the largest power-of-two batch of at
+    most want_items that fits every plan in `fraction` of the free device memory."""
+    import torch
+
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(free * fraction)
+    batch = 1
+    while batch * 2 <= max(want_items, 1) and max(p.workspace_bytes(batch * 2) for p in plans) <= budget:
+        batch *= 2
+    need = max(p.workspace_bytes(batch) for p in plans) if plans else 256
+    return torch.empty(need, dtype=torch.uint8, device="cuda")
+
+
 def contract_sliced(plan: Plan, bits, slice_begin: int = 0, slice_end: int | None = None, workspace=None,
                     max_batch: int = 0, stream=None, per_slice: bool = False):
     """tnq_contract_sliced: FP64 partial sum over slices [begin, end) (Eq. 5).
@@ -233,8 +247,8 @@ def contract_sliced(plan: Plan, bits, slice_begin: int = 0, slice_end: int | Non
         slice_end = n_slices
     b = _bits_array(bits, plan.n_qubits)
     if workspace is None:
-        batch = max_batch if max_batch > 0 else min(slice_end - slice_begin, 1 << 16) or 1
-        workspace = torch.empty(plan.workspace_bytes(batch), dtype=torch.uint8, device="cuda")
+        want = max_batch if max_batch > 0 else min(slice_end - slice_begin, 1 << 16) or 1
+        workspace = default_workspace([plan], want)
     out = np.zeros(2, np.float64)
     per = np.zeros(2 * max(slice_end - slice_begin, 1), np.float64) if per_slice else None
     _check(lib().tnq_contract_sliced(plan.handle, _ptr(b, ctypes.c_uint8), slice_begin, slice_end,
@@ -280,8 +294,8 @@ def amplitudes_batch(plans, bitstrings, workspace=None, stream=None):
     offsets = np.array(offs, dtype=np.uint64).astype(np.uintp)
     handles = (ctypes.c_void_p * max(len(plans), 1))(*[p.handle for p in plans])
     if workspace is None:
-        need = max(p.workspace_bytes(1) for p in plans) if plans else 1
-        workspace = torch.empty(max(need, 1 << 30), dtype=torch.uint8, device="cuda")
+        want = max([(1 << p.info()["p"]) * len(b) for p, b in zip(plans, bitstrings)] or [1])
+        workspace = default_workspace(plans, want)
     out = np.zeros(2 * max(offs[-1], 1), np.float64)
     _check(lib().tnq_amplitudes_batch(handles, len(plans), _ptr(allbits, ctypes.c_uint8),
                                       offsets.ctypes.data_as(_P(ctypes.c_size_t)),

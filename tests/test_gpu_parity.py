@@ -288,3 +288,30 @@ def test_split_precision_agrees_with_c64(cuda, tnq_lib):
     _, a = tnq_lib.contract_sliced(c64, bits, per_slice=True)
     _, b = tnq_lib.contract_sliced(tf, bits, per_slice=True)
     assert np.max(np.abs(a - b)) <= SPLIT_TOL * np.max(np.abs(a))
+
+
+@pytest.mark.slow
+def test_batched_serving_workload_full_size(cuda, tnq_lib, oracle_lib):
+    """The 64 circuits of the batched serving shape (5x5..7x7 grids, depths
+    1+16+1..1+32+1, uneven sizes), 4 of their seeded bitstrings each, in one
+    tnq_amplitudes_batch call; plans sliced to bags <= 2^26. The 5x5 circuits
+    are checked against the oracle; sampled amplitudes must equal their own
+    single-bitstring contraction."""
+    nb = 4
+    work = I.batched_serving_workload(n_circuits=64, bitstrings_per_circuit=16, seed=0)
+    plans = [tnq_lib.Plan(c, max_bag_log2=26, max_p=30) for c, _ in work]
+    bl = [bits[:nb] for _, bits in work]
+    out = tnq_lib.amplitudes_batch(plans, bl)
+    assert out.shape == (64 * nb,)
+    rng = np.random.default_rng(0)
+    checked = 0
+    for i, ((circ, bits), plan) in enumerate(zip(work, plans)):
+        j = int(rng.integers(nb))
+        if i % 4 == 0 or circ.n_qubits == 25:
+            single = tnq_lib.contract_sliced(plan, bits[j])
+            assert abs(out[nb * i + j] - single) <= 1e-9 * max(abs(single), 1e-30)
+        if circ.n_qubits == 25 and checked < 6:
+            ref = oracle_lib.contract(circ, bits[j], order=plan.order(), mu=plan.sliced())
+            assert rel_err(out[nb * i + j], ref, 25) < TOL
+            checked += 1
+    assert checked > 0
