@@ -266,6 +266,9 @@ def main():
     t_tune = time.perf_counter() - t_tune
     info = plan.info()
     B = min(args.max_batch, n_sl)
+    free, _ = torch.cuda.mem_get_info()
+    while B > 1 and plan.workspace_bytes(B) > 0.8 * free:
+        B //= 2
     ws = torch.empty(plan.workspace_bytes(B), dtype=torch.uint8, device="cuda")
 
     # warm-up (also captures the CUDA graph)

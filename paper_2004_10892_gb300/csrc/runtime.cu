@@ -350,7 +350,7 @@ struct GParams {
 template <int NV>
 __device__ __forceinline__ void group_stage(const GParams& P, const GSt& S, int t, const float2* prev, float2* cur,
                                             bool last, const long long* s_base, const float* s_scale,
-                                            int (*s_hi)[32], const int* s_out_hi, long long out_base, int out_lo,
+                                            int (*s_hi)[16], const int* s_out_hi, long long out_base, int out_lo,
                                             float* tmax) {
   const int nb = S.nbits;
   const int n_hi = nb > 8 ? (1 << (nb - 8)) : 1;
@@ -401,14 +401,14 @@ __device__ __forceinline__ void group_stage(const GParams& P, const GSt& S, int 
 
 // Persistent fused-group kernel: every block builds the stage tables once,
 // then loops over tiles (item, H assignment) tile = blockIdx.x + k*gridDim.x.
-__global__ void __launch_bounds__(TPB) k_group(const __grid_constant__ GParams P, long long n_tiles) {
+__global__ void __launch_bounds__(TPB, 4) k_group(const __grid_constant__ GParams P, long long n_tiles) {
   extern __shared__ float2 g_stage[];  // stage regions A (2^(GL_MAX-1) entries) and B (half of A)
-  __shared__ long long s_hstr[GIN_MAX + 1][GH_MAX];  // row GIN_MAX: the output
+  __shared__ int s_hstr[GIN_MAX + 1][GH_MAX];  // row GIN_MAX: the output (within-item offsets < 2^31)
   __shared__ long long s_base[GIN_MAX];
   __shared__ float s_scale[GIN_MAX];
   __shared__ int s_e[GIN_MAX];
-  __shared__ int s_hi[GM_MAX][KMAX][32];
-  __shared__ int s_out_hi[32];
+  __shared__ int s_hi[GM_MAX][KMAX][16];
+  __shared__ int s_out_hi[16];
   __shared__ long long s_out_base;
   __shared__ float s_red[TPB / 32];
   const int t = threadIdx.x;
@@ -417,7 +417,7 @@ __global__ void __launch_bounds__(TPB) k_group(const __grid_constant__ GParams P
     const int j = e / GH_MAX, i = e - j * GH_MAX;
     long long v = 0;
     if (i < P.n_h) v = (j < P.n_gin) ? P.gin[j].hstride[i] : (j == GIN_MAX ? P.out_hstride[i] : 0ll);
-    s_hstr[j][i] = v;
+    s_hstr[j][i] = (int)v;
   }
   for (int s = 0; s < P.n_st; ++s) {
     const GSt& S = P.st[s];
@@ -1148,6 +1148,8 @@ static std::string validate_config(const tnq_plan& P, int mode, int B) {
           if (S.cstride[j][b] & 1) return "group " + std::to_string(gi) + ": odd local stride";
         if (S.src[j] >= 0) {
           const GIn& in = G.gin[S.src[j]];
+          for (int i = 0; i < G.n_h; ++i)
+            if (in.hstride[i] >= (1ll << 31)) return "group tile stride does not fit 32 bits";
           if ((in.istride & 1) || ((size_t)in.ptr / 8) % 2) return "group input base not even";
           for (int i = 0; i < G.n_h; ++i)
             if (in.hstride[i] & 1) return "group " + std::to_string(gi) + ": odd tile stride";
