@@ -94,6 +94,20 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# DRAM bytes (read + write) of the largest fused-chain launch per slice, from
+# the ncu capture in profiles/k_group_7x7_d1+32+1.md, valid only for the
+# kernel source it was taken from (reported as null once runtime.cu changes).
+MEASURED_TRAFFIC = {"k_group": {"source_sha1": "3fd6ece8901074bd9f6dfb360ae02ebd21a65871", "bytes_per_slice": 76.627712e6 + 30.664448e6,
+                                "launch": "largest k_group launch (5-bucket chain, bags 28 -> 24)"}}
+
+
+def runtime_source_sha1():
+    import hashlib
+
+    with open(os.path.join(ROOT, "paper_2004_10892_gb300", "csrc", "runtime.cu"), "rb") as f:
+        return hashlib.sha1(f.read()).hexdigest()
+
+
 # FP32 CUDA-core peak of GB300 from unit counts and clocks: 152 SMs x 128 FP32
 # lanes x 2 flops (FMA) x 2.07 GHz (the maximum SM clock in MEASURED_PEAKS.json).
 FP32_LANES_PER_SM = 128
@@ -150,6 +164,14 @@ def launch_roofline(L, plan, bits, ws, B, n_sl, stream, peaks, info):
     dom, other = (k_group, k_bucket) if t_grp >= t_one else (k_bucket, k_group)
     out = dict(dom)
     out["traffic"] = None
+    if dom["kernel"] == "k_group" and grp:
+        big = max(grp, key=lambda i: ms[i])
+        out["largest_launch"] = {"ms": ms[big], "flops": fl[big], "algorithmic_bytes": by[big],
+                                 "achieved_tflops": fl[big] / (ms[big] / 1e3) / 1e12 if ms[big] > 0 else None}
+        mt = MEASURED_TRAFFIC["k_group"]
+        if mt["source_sha1"] == runtime_source_sha1():
+            out["traffic"] = mt["bytes_per_slice"] * b_out.value
+            out["traffic_launch"] = mt["launch"] + ", ncu dram bytes scaled by the batch"
     out["peak_source"] = dom.get("peak_source", "measured (MEASURED_PEAKS.json hbm_gbs)")
     out["batch"] = b_out.value
     out["other_kernel"] = other
