@@ -44,8 +44,8 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
 
-// Waits for the phase with the given parity to complete; false after WAIT_NS.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Waits for the phase with the given parity to complete; false after limit_ns.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned long long limit_ns = WAIT_NS) {
   const unsigned long long t0 = gtimer();
   while (true) {
     uint32_t done;
@@ -55,8 +55,20 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
         : "r"(smem_u32(bar)), "r"(parity)
         : "memory");
     if (done) return true;
-    if (gtimer() - t0 > WAIT_NS) return false;
+    if (gtimer() - t0 > limit_ns) return false;
   }
+}
+
+// Waits on an mbarrier that nothing ever arrives on, with the same bounded
+// wait the GEMM uses; records 1 in *status when the wait gives up.
+__global__ void k_wait_never(int* status, unsigned long long limit_ns) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait(&bar, 0, limit_ns)) atomicExch(status, 1);
 }
 
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint64_t* bar) {
@@ -451,6 +463,24 @@ void gemm_bucket_launch(const GemmBucketArgs& g, const GemmEpilogue& ep, int* st
 }
 
 }  // namespace tnq
+
+// Internal test hook (not in include/tnq.h): runs a kernel whose mbarrier wait
+// can never complete, bounded by limit_ns; returns TNQ_ETIMEOUT when the device
+// reported the timeout (the expected outcome), TNQ_OK if it did not, TNQ_ECUDA
+// on a CUDA error. The context stays usable.
+extern "C" int tnq_internal_wait_timeout_selftest(unsigned long long limit_ns) {
+  using namespace tnq;
+  int* d = nullptr;
+  if (cudaMalloc(&d, 4) != cudaSuccess) return 3;
+  cudaMemset(d, 0, 4);
+  k_wait_never<<<1, 32>>>(d, limit_ns);
+  cudaError_t e = cudaDeviceSynchronize();
+  int status = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&status, d, 4, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return 3;
+  return status ? 4 : 0;
+}
 
 // Internal self-test hook (not in include/tnq.h): C[b] = A[b] B[b]^T for real
 // FP32 matrices (host, row-major: A batch x M x K, B batch x N x K, C batch x M

@@ -47,3 +47,19 @@ def test_split_precision_accuracy(cuda, tnq_lib, kind, tol):
     ref = np.einsum("bmk,bnk->bmn", A.astype(np.float64), B.astype(np.float64))
     err = np.max(np.abs(C - ref)) / np.max(np.abs(ref))
     assert err < tol, err
+
+
+def test_bounded_wait_reports_timeout(cuda, tnq_lib):
+    """A device wait that can never complete gives up after its limit and the
+    host reads TNQ_ETIMEOUT; the context stays usable afterwards."""
+    import time
+
+    L = tnq_lib.lib()
+    f = L.tnq_internal_wait_timeout_selftest
+    f.argtypes = [ctypes.c_ulonglong]
+    t = time.perf_counter()
+    assert f(200_000_000) == tnq_lib.ETIMEOUT
+    assert time.perf_counter() - t < 10
+    A = np.ones((1, 128, 64), np.float32)
+    C = tc_gemm(tnq_lib, BF16, A, A)
+    assert np.all(C == 64)
