@@ -105,7 +105,9 @@ typedef struct {
   int32_t td_rebuild;     /* 0: after a deletion drop the vertex from every bag; 1: rebuild the TD from the reduced order */
   int32_t fuse_min_rank;  /* run chains of buckets whose intermediate results have >= 2^this entries as one
                              fused kernel (no intermediate reaches HBM); 0 = no fusion; default 12 */
-  int32_t pad_;
+  int32_t leaf_absorb;    /* 1 (default): multiply a rank <= 2 gate tensor into the earlier bucket that produces
+                             a tensor holding its variables, when that bucket's bag is smaller (exact, by
+                             distributivity in Eq. 2); 0: every gate tensor stays in its own bucket */
 } tnq_plan_opts;
 
 typedef struct {
@@ -135,7 +137,7 @@ const char* tnq_last_error(void);
 /* Library version string. */
 const char* tnq_version(void);
 /* Fills opts with defaults: tree-trimming, no bag limit, p in [0, 0], c64, min-fill, fusion of chains
- * whose results have >= 2^12 entries. */
+ * whose results have >= 2^12 entries, leaf absorption on. */
 void tnq_plan_opts_default(tnq_plan_opts* opts);
 
 /* ---- planning (host only; works without a GPU) ------------------------

@@ -61,6 +61,7 @@ void tnq_plan_opts_default(tnq_plan_opts* o) {
   o->ordering = TNQ_ORDER_MIN_FILL;
   o->td_rebuild = 0;
   o->fuse_min_rank = 12;
+  o->leaf_absorb = 1;
 }
 
 tnq_status tnq_plan_from_circuit(int32_t n_qubits, const tnq_gate* gates, size_t n_gates,
@@ -74,7 +75,7 @@ tnq_status tnq_plan_from_circuit(int32_t n_qubits, const tnq_gate* gates, size_t
   if (o.slicer < 0 || o.slicer > TNQ_SLICER_LEARNED || o.min_p < 0 || o.max_p < o.min_p ||
       o.max_p > 62 || o.max_bag_log2 < 0 || o.max_bag_log2 > 40 || o.precision < 0 ||
       o.precision > TNQ_PREC_SPLIT_TF32 || o.ordering < 0 || o.ordering > TNQ_ORDER_MIN_DEGREE ||
-      o.fuse_min_rank < 0 || o.fuse_min_rank > 40) {
+      o.fuse_min_rank < 0 || o.fuse_min_rank > 40 || o.leaf_absorb < 0 || o.leaf_absorb > 1) {
     set_error("invalid plan options");
     return TNQ_EINVAL;
   }
@@ -104,6 +105,7 @@ tnq_status tnq_plan_from_circuit(int32_t n_qubits, const tnq_gate* gates, size_t
     P->prog = compile_program(P->net, P->order, P->mu);
     if (o.precision != TNQ_PREC_C64)
       find_gemm_chains(P->prog, P->order, o.gemm_min_k_log2 > 0 ? o.gemm_min_k_log2 : 4, 8);
+    if (o.leaf_absorb) absorb_leaves(P->prog);
     fuse_chains(P->prog, P->order, o.fuse_min_rank);
     P->amp_scale_log2 = -0.5 * P->net.n_sqrt2;
     *out_plan = P.release();

@@ -188,15 +188,7 @@ Program compile_program(const Network& net, const std::vector<int>& order, const
     out.producer = bidx;
     P.tensors.push_back(out);
     b.output = (int)P.tensors.size() - 1;
-    double in_elems = 0;
-    for (int tid : inputs) {
-      P.tensors[tid].consumer = bidx;
-      in_elems += std::ldexp(1.0, P.tensors[tid].rank());
-    }
-    const double full = std::ldexp(1.0, b.r);
-    P.flops_per_slice += 6.0 * (b.k - 1) * full + (sum ? 2.0 * (full / 2) : 0.0);
-    P.bytes_per_slice += 8.0 * (in_elems + std::ldexp(1.0, P.tensors[b.output].rank()));
-    P.max_bag = std::max(P.max_bag, b.r);
+    for (int tid : inputs) P.tensors[tid].consumer = bidx;
     P.buckets.push_back(b);
     return b.output;
   };
@@ -220,7 +212,74 @@ Program compile_program(const Network& net, const std::vector<int>& order, const
     if (P.tensors[out].vars.empty()) P.finals.push_back(out);
     else place(out);
   }
+  count_costs(P);
   return P;
+}
+
+void count_costs(Program& P) {
+  P.flops_per_slice = 0;
+  P.bytes_per_slice = 0;
+  P.max_bag = 0;
+  for (const PBucket& b : P.buckets) {
+    double in_elems = 0;
+    for (int tid : b.inputs) in_elems += std::ldexp(1.0, P.tensors[tid].rank());
+    const double full = std::ldexp(1.0, b.r);
+    P.flops_per_slice += 6.0 * (b.k - 1) * full + (b.sum ? 2.0 * (full / 2) : 0.0);
+    P.bytes_per_slice += 8.0 * (in_elems + std::ldexp(1.0, P.tensors[b.output].rank()));
+    P.max_bag = std::max(P.max_bag, b.r);
+  }
+}
+
+int absorb_leaves(Program& P) {
+  const int nb = (int)P.buckets.size();
+  if (P.group_of.size() != (size_t)nb) P.group_of.assign(nb, -1);
+  auto in_group = [&](int b) { return P.group_of[b] >= 0; };
+  int moved = 0;
+  for (int b = nb - 1; b >= 0; --b) {
+    if (in_group(b)) continue;
+    PBucket& B = P.buckets[b];
+    for (size_t li = 0; li < B.inputs.size();) {
+      const int L = B.inputs[li];
+      const PTensor& tl = P.tensors[L];
+      int best = -1;
+      if (tl.leaf_gate >= 0 && tl.rank() <= 2 && !tl.wide_range && B.inputs.size() > 1) {
+        std::vector<int> lv = tl.vars;
+        std::sort(lv.begin(), lv.end());
+        for (int T : B.inputs) {
+          const PTensor& tt = P.tensors[T];
+          const int p = tt.producer;
+          if (T == L || p < 0 || in_group(p) || P.buckets[p].k >= KMAX || P.buckets[p].u < 0) continue;
+          if (P.buckets[p].r >= B.r) continue;
+          if ((tl.dep_slice && !tt.dep_slice) || (tl.dep_bits && !tt.dep_bits)) continue;
+          std::vector<int> tv = tt.vars;
+          std::sort(tv.begin(), tv.end());
+          if (!std::includes(tv.begin(), tv.end(), lv.begin(), lv.end())) continue;
+          if (best < 0 || P.buckets[p].r < P.buckets[P.tensors[best].producer].r) best = T;
+        }
+      }
+      if (best < 0) {
+        ++li;
+        continue;
+      }
+      const int p = P.tensors[best].producer;
+      // every input of a bucket holds its eliminated variable as bit 0: give L
+      // u_p as a variable it does not depend on (u_p precedes all of p's variables)
+      std::vector<int>& v = P.tensors[L].vars;
+      if (std::find(v.begin(), v.end(), P.buckets[p].u) == v.end()) v.insert(v.begin(), P.buckets[p].u);
+      P.buckets[p].inputs.push_back(L);
+      P.buckets[p].k = (int)P.buckets[p].inputs.size();
+      P.tensors[L].consumer = p;
+      B.inputs.erase(B.inputs.begin() + li);
+      B.k = (int)B.inputs.size();
+      ++moved;
+    }
+  }
+  if (moved) {
+    count_costs(P);
+    P.bytes_unfused = P.bytes_per_slice;
+    set_groups(P, std::vector<FusedGroup>(P.groups));
+  }
+  return moved;
 }
 
 }  // namespace tnq

@@ -134,6 +134,23 @@ void set_groups(Program& prog, const std::vector<FusedGroup>& groups);
 // Compiles the bucket program for the reduced order (free ids) and sliced set.
 Program compile_program(const Network& net, const std::vector<int>& order, const std::vector<int>& mu);
 
+// Recomputes flops_per_slice, bytes_per_slice (every bucket unfused) and max_bag.
+void count_costs(Program& prog);
+
+// Leaf absorption: a gate tensor L (rank <= 2, not wide-range) of bucket b
+// whose variables all lie in another input T of b, where T is the result of an
+// earlier bucket p with a smaller bag (r_p < r_b), is multiplied into bucket p
+// instead of b. Exact: L does not hold p's eliminated variable, so
+// Sum_{u_p} L * (product of p) = L * Sum_{u_p} (product of p) (Eq. 2, by
+// distributivity), and b's product is unchanged. Each move saves
+// 2^r_b - 2^r_p complex multiplies per slice. Buckets in GEMM groups are left
+// alone; L must not depend on the slice or the bitstring unless T does. L
+// gains u_p as a variable it is constant in, so that every input of a bucket
+// keeps the bucket's eliminated variable as its first (bit 0) variable. Runs
+// after find_gemm_chains and before fuse_chains; returns the number of moves
+// and refreshes the costs.
+int absorb_leaves(Program& prog);
+
 // Fusion pass (stages inside a group are not renormalised, so chains that
 // read a wide-range leaf stay unfused): chains of summing buckets whose results are at least
 // 2^min_rank entries become fused groups when no new variable enters along

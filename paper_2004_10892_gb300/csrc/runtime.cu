@@ -344,26 +344,34 @@ struct GParams {
 
 // One stage of a fused group. Inputs n_var.. do not vary over the block's
 // local bits: their (u=0, u=1) pairs, times the stage's power-of-two scales,
-// are multiplied once into a constant pair. Each thread handles local entries
-// c = t + 256 it; per entry only the NV varying operands are loaded (one
-// 16-byte load each: the eliminated variable is bit 0 of every operand).
-template <int NV>
+// are multiplied once into a constant pair (K = true). Without such inputs
+// (K = false) the product starts from the first varying operand and the
+// scales multiply the sum. Each thread handles local entries c = t + 256 it;
+// per entry only the NV varying operands are loaded (one 16-byte load each:
+// the eliminated variable is bit 0 of every operand), and the last operand's
+// multiply is fused with the sum over u.
+template <int NV, bool K, int NHI = 0>
 __device__ __forceinline__ void group_stage(const GParams& P, const GSt& S, int t, const float2* prev, float2* cur,
                                             bool last, const long long* s_base, const float* s_scale,
                                             int (*s_hi)[16], const int* s_out_hi, long long out_base, int out_lo,
                                             float* tmax) {
+  static_assert(K || NV > 0, "a stage without constant inputs has a varying operand");
+  // NHI > 0: the stage has exactly 2^(8 + log2 NHI) local entries (the caller
+  // checked nbits), so the entry loop is unrolled completely and unguarded
   const int nb = S.nbits;
-  const int n_hi = nb > 8 ? (1 << (nb - 8)) : 1;
-  const int nent = 1 << nb;
+  const int n_hi = NHI > 0 ? NHI : (nb > 8 ? (1 << (nb - 8)) : 1);
+  const int nent = NHI > 0 ? (NHI << 8) : (1 << nb);
   float F = 1.f;
   for (int j = 0; j < S.n_in; ++j)
     if (S.src[j] >= 0) F *= s_scale[S.src[j]];
   float2 k0 = make_float2(F, 0.f), k1 = make_float2(F, 0.f);
-  for (int j = NV; j < S.n_in; ++j) {
-    const float2* p = S.src[j] < 0 ? prev : P.gin[S.src[j]].ptr + s_base[S.src[j]];
-    const float4 v = *reinterpret_cast<const float4*>(p);
-    k0 = cmul(k0, make_float2(v.x, v.y));
-    k1 = cmul(k1, make_float2(v.z, v.w));
+  if (K) {
+    for (int j = NV; j < S.n_in; ++j) {
+      const float2* p = S.src[j] < 0 ? prev : P.gin[S.src[j]].ptr + s_base[S.src[j]];
+      const float4 v = *reinterpret_cast<const float4*>(p);
+      k0 = cmul(k0, make_float2(v.x, v.y));
+      k1 = cmul(k1, make_float2(v.z, v.w));
+    }
   }
   const float2* ptr[NV > 0 ? NV : 1];
   int lo[NV > 0 ? NV : 1];
@@ -377,18 +385,39 @@ __device__ __forceinline__ void group_stage(const GParams& P, const GSt& S, int 
       if (i < nb && ((t >> i) & 1)) a += S.cstride[j][i];
     lo[j] = a;
   }
-#pragma unroll 2
+#pragma unroll (NHI > 0 ? NHI : 2)
   for (int it = 0; it < n_hi; ++it) {
     const int c = t + (it << 8);
-    if (c < nent) {
+    if (NHI > 0 || c < nent) {
       float2 p0 = k0, p1 = k1;
+      constexpr int J0 = K ? 0 : 1;
+      if (!K) {
+        const float4 v = *reinterpret_cast<const float4*>(ptr[0] + lo[0] + s_hi[0][it]);
+        p0 = make_float2(v.x, v.y);
+        p1 = make_float2(v.z, v.w);
+      }
 #pragma unroll
-      for (int j = 0; j < NV; ++j) {
+      for (int j = J0; j < NV - 1; ++j) {
         const float4 v = *reinterpret_cast<const float4*>(ptr[j] + lo[j] + s_hi[j][it]);
         p0 = cmul(p0, make_float2(v.x, v.y));
         p1 = cmul(p1, make_float2(v.z, v.w));
       }
-      const float2 r = make_float2(p0.x + p1.x, p0.y + p1.y);
+      float2 r;
+      if (NV >= 1 && (K || NV >= 2)) {
+        const float4 v = *reinterpret_cast<const float4*>(ptr[NV - 1] + lo[NV - 1] + s_hi[NV - 1][it]);
+        float rx = p0.x * v.x;
+        rx = fmaf(-p0.y, v.y, rx);
+        rx = fmaf(p1.x, v.z, rx);
+        rx = fmaf(-p1.y, v.w, rx);
+        float ry = p0.x * v.y;
+        ry = fmaf(p0.y, v.x, ry);
+        ry = fmaf(p1.x, v.w, ry);
+        ry = fmaf(p1.y, v.z, ry);
+        r = make_float2(rx, ry);
+      } else {
+        r = make_float2(p0.x + p1.x, p0.y + p1.y);
+      }
+      if (!K) r = make_float2(r.x * F, r.y * F);
       if (last) {
         P.out[out_base + out_lo + s_out_hi[it]] = r;
         *tmax = fmaxf(*tmax, fmaxf(fabsf(r.x), fabsf(r.y)));
@@ -397,6 +426,18 @@ __device__ __forceinline__ void group_stage(const GParams& P, const GSt& S, int 
       }
     }
   }
+}
+
+template <int NV>
+__device__ __forceinline__ void run_stage(bool with_k, const GParams& P, const GSt& S, int t, const float2* prev,
+                                          float2* cur, bool last, const long long* s_base, const float* s_scale,
+                                          int (*s_hi)[16], const int* s_out_hi, long long out_base, int out_lo,
+                                          float* tmax) {
+  if (NV == 0 || with_k)
+    group_stage<NV, true>(P, S, t, prev, cur, last, s_base, s_scale, s_hi, s_out_hi, out_base, out_lo, tmax);
+  else
+    group_stage<(NV > 0 ? NV : 1), false>(P, S, t, prev, cur, last, s_base, s_scale, s_hi, s_out_hi, out_base,
+                                          out_lo, tmax);
 }
 
 // Persistent fused-group kernel: every block builds the stage tables once,
@@ -496,16 +537,19 @@ __global__ void __launch_bounds__(TPB, 4) k_group(const __grid_constant__ GParam
     for (int s = 0; s < P.n_st; ++s) {
       const GSt& S = P.st[s];
       const bool last = (s == P.n_st - 1);
+      const bool with_k = S.n_in > S.n_var;
       switch (S.n_var) {
-        case 0: group_stage<0>(P, S, t, prev, cur, last, s_base, s_scale, s_hi[s], s_out_hi, s_out_base, out_lo, &tmax); break;
-        case 1: group_stage<1>(P, S, t, prev, cur, last, s_base, s_scale, s_hi[s], s_out_hi, s_out_base, out_lo, &tmax); break;
-        case 2: group_stage<2>(P, S, t, prev, cur, last, s_base, s_scale, s_hi[s], s_out_hi, s_out_base, out_lo, &tmax); break;
-        case 3: group_stage<3>(P, S, t, prev, cur, last, s_base, s_scale, s_hi[s], s_out_hi, s_out_base, out_lo, &tmax); break;
-        case 4: group_stage<4>(P, S, t, prev, cur, last, s_base, s_scale, s_hi[s], s_out_hi, s_out_base, out_lo, &tmax); break;
-        case 5: group_stage<5>(P, S, t, prev, cur, last, s_base, s_scale, s_hi[s], s_out_hi, s_out_base, out_lo, &tmax); break;
-        case 6: group_stage<6>(P, S, t, prev, cur, last, s_base, s_scale, s_hi[s], s_out_hi, s_out_base, out_lo, &tmax); break;
-        case 7: group_stage<7>(P, S, t, prev, cur, last, s_base, s_scale, s_hi[s], s_out_hi, s_out_base, out_lo, &tmax); break;
-        default: group_stage<8>(P, S, t, prev, cur, last, s_base, s_scale, s_hi[s], s_out_hi, s_out_base, out_lo, &tmax); break;
+#define TNQ_STAGE(n) run_stage<n>(with_k, P, S, t, prev, cur, last, s_base, s_scale, s_hi[s], s_out_hi, s_out_base, out_lo, &tmax)
+        case 0: TNQ_STAGE(0); break;
+        case 1: TNQ_STAGE(1); break;
+        case 2: TNQ_STAGE(2); break;
+        case 3: TNQ_STAGE(3); break;
+        case 4: TNQ_STAGE(4); break;
+        case 5: TNQ_STAGE(5); break;
+        case 6: TNQ_STAGE(6); break;
+        case 7: TNQ_STAGE(7); break;
+        default: TNQ_STAGE(8); break;
+#undef TNQ_STAGE
       }
       if (!last) __syncthreads();
       float2* tmp = prev;

@@ -219,10 +219,11 @@ def test_plan_deterministic(tnq_lib):
 
 def test_cost_model_equals_oracle_counts(tnq_lib, oracle_lib):
     """Exact cost model: flops per slice = 6 (complex mults) + 2 (complex adds)
-    as counted by the oracle running the plan's buckets."""
+    as counted by the oracle running the plan's buckets (plain Eq. 2, every
+    gate tensor in the bucket of its earliest variable: leaf absorption off)."""
     for circ, kw in [(I.random_grid_circuit(4, 4, 12, 2), {}), (I.random_grid_circuit(4, 5, 16, 5), dict(min_p=2, max_p=2)),
                      (I.random_small_circuit(7, 70, 4), dict(min_p=1, max_p=1))]:
-        plan = tnq_lib.Plan(circ, **kw)
+        plan = tnq_lib.Plan(circ, leaf_absorb=0, **kw)
         inf = plan.info()
         bits = I.random_bitstring(circ.n_qubits, 3)
         _, (cmul, cadd) = oracle_lib.contract(circ, bits, order=plan.order(), mu=plan.sliced(), slices=(0, 1),
@@ -248,3 +249,31 @@ def test_plan_without_free_variables(tnq_lib):
     plan = tnq_lib.Plan(I.all_h(4))
     inf = plan.info()
     assert inf["n_free_vars"] == 0 and inf["n_buckets"] == 0 and inf["n_slices"] == 1
+
+
+def _bucket_rows(tnq_lib, plan):
+    """Per bucket (bag r, inputs k, output rank, sums) from the internal hook."""
+    import ctypes
+
+    L = tnq_lib.lib()
+    n = ctypes.c_int32()
+    cap = 12 * 4096
+    out = (ctypes.c_int32 * cap)()
+    assert L.tnq_internal_bucket_detail(plan.handle, out, cap, ctypes.byref(n)) == 0
+    return np.frombuffer(out, dtype=np.int32)[:12 * n.value].reshape(-1, 12)[:, :4]
+
+
+def test_leaf_absorption_moves_multiplies_to_smaller_buckets(tnq_lib):
+    """Leaf absorption keeps every bag and the number of tensor reads, and
+    lowers the exact flop count, which still equals the sum over the program's
+    buckets of 6 (k-1) 2^r + 2^r (the last term for summing buckets)."""
+    for circ, kw in [(I.random_grid_circuit(5, 5, 20, 1), dict(min_p=2, max_p=2)),
+                     (I.random_grid_circuit(6, 6, 24, 0), dict(max_bag_log2=20, max_p=12))]:
+        off = tnq_lib.Plan(circ, leaf_absorb=0, **kw)
+        on = tnq_lib.Plan(circ, **kw)
+        r0, r1 = _bucket_rows(tnq_lib, off), _bucket_rows(tnq_lib, on)
+        assert (r0[:, [0, 2, 3]] == r1[:, [0, 2, 3]]).all() and r0[:, 1].sum() == r1[:, 1].sum()
+        assert on.info()["flops_per_slice"] < off.info()["flops_per_slice"]
+        for plan, rows in ((off, r0), (on, r1)):
+            flops = sum(6.0 * (k - 1) * 2.0 ** r + (2.0 ** r if sm else 0.0) for r, k, _, sm in rows)
+            assert plan.info()["flops_per_slice"] == flops
