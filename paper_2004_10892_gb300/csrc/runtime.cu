@@ -308,9 +308,11 @@ __global__ void __launch_bounds__(TPB) k_bucket(const __grid_constant__ KParams 
 // the item); stage s eliminates u_s over the local variables in shared memory:
 //   stage_s[c] = sum_{u_s} prod_j in_j[c, u_s],
 // where in_j is a tensor read from memory at the block's H, or the previous
-// stage's buffer. Offsets are linear in the bits of the stage's local index c:
-// bits < 8 via a per-thread table, bits >= 8 via a per-iteration table.
-constexpr int GH_MAX = 48;  // tile bits (output variables outside the block + item bits)
+// stage's buffer. Offsets are linear in the bits of the stage's local index c;
+// per varying operand a 48-entry table holds the offset of each value of bits
+// 0-3, 4-7 and 8-11 of c (built once per block).
+constexpr int GH_MAX = 32;  // tile bits (output variables outside the block; a bag of 2^40 entries has < 32)
+constexpr int PAIR_MAX = GIN_MAX + GM_MAX - 1;  // varying (stage, operand) pairs: at most every input of every stage
 constexpr int GROUP_SMEM_BYTES = (1 << (GL_MAX - 1)) * 3 / 2 * (int)sizeof(float2);  // regions A + B
 
 struct GIn {
@@ -328,6 +330,7 @@ struct GSt {
   int src[KMAX];               // -1: previous stage buffer, else index into gin
   int cstride[KMAX][GL_MAX];   // element stride of local output bit b, per input
   int ustride[KMAX];           // stride of the eliminated variable, per input
+  int q0;                      // offset table of varying input j is pair q0 + j
 };
 
 struct GParams {
@@ -338,6 +341,7 @@ struct GParams {
   long long out_hstride[GH_MAX];
   int out_cstride[GL_MAX];
   int n_st, n_gin, n_h, out_meta, out_dep, B;
+  int n_pairs;
   int* meta_e;
   unsigned* meta_m;
 };
@@ -351,9 +355,9 @@ struct GParams {
 // the eliminated variable is bit 0 of every operand), and the last operand's
 // multiply is fused with the sum over u.
 template <int NV, bool K, int NHI = 0>
-__device__ __forceinline__ void group_stage(const GParams& P, const GSt& S, int t, const float2* prev, float2* cur,
-                                            bool last, const long long* s_base, const float* s_scale,
-                                            int (*s_hi)[16], const int* s_out_hi, long long out_base, int out_lo,
+__device__ __forceinline__ void group_stage(const GSt& S, int t, const float2* prev, float2* cur, float2* out,
+                                            bool last, const float2* const* s_ptr, const float* s_scale,
+                                            const int (*tab)[48], const int* s_out_hi, long long out_base, int out_lo,
                                             float* tmax) {
   static_assert(K || NV > 0, "a stage without constant inputs has a varying operand");
   // NHI > 0: the stage has exactly 2^(8 + log2 NHI) local entries (the caller
@@ -367,7 +371,7 @@ __device__ __forceinline__ void group_stage(const GParams& P, const GSt& S, int 
   float2 k0 = make_float2(F, 0.f), k1 = make_float2(F, 0.f);
   if (K) {
     for (int j = NV; j < S.n_in; ++j) {
-      const float2* p = S.src[j] < 0 ? prev : P.gin[S.src[j]].ptr + s_base[S.src[j]];
+      const float2* p = S.src[j] < 0 ? prev : s_ptr[S.src[j]];
       const float4 v = *reinterpret_cast<const float4*>(p);
       k0 = cmul(k0, make_float2(v.x, v.y));
       k1 = cmul(k1, make_float2(v.z, v.w));
@@ -378,12 +382,8 @@ __device__ __forceinline__ void group_stage(const GParams& P, const GSt& S, int 
 #pragma unroll
   for (int j = 0; j < NV; ++j) {
     const int src = S.src[j];
-    ptr[j] = src < 0 ? prev : P.gin[src].ptr + s_base[src];
-    int a = 0;
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-      if (i < nb && ((t >> i) & 1)) a += S.cstride[j][i];
-    lo[j] = a;
+    ptr[j] = src < 0 ? prev : s_ptr[src];
+    lo[j] = tab[j][t & 15] + tab[j][16 + ((t >> 4) & 15)];
   }
 #pragma unroll (NHI > 0 ? NHI : 2)
   for (int it = 0; it < n_hi; ++it) {
@@ -392,19 +392,19 @@ __device__ __forceinline__ void group_stage(const GParams& P, const GSt& S, int 
       float2 p0 = k0, p1 = k1;
       constexpr int J0 = K ? 0 : 1;
       if (!K) {
-        const float4 v = *reinterpret_cast<const float4*>(ptr[0] + lo[0] + s_hi[0][it]);
+        const float4 v = *reinterpret_cast<const float4*>(ptr[0] + lo[0] + tab[0][32 + it]);
         p0 = make_float2(v.x, v.y);
         p1 = make_float2(v.z, v.w);
       }
 #pragma unroll
       for (int j = J0; j < NV - 1; ++j) {
-        const float4 v = *reinterpret_cast<const float4*>(ptr[j] + lo[j] + s_hi[j][it]);
+        const float4 v = *reinterpret_cast<const float4*>(ptr[j] + lo[j] + tab[j][32 + it]);
         p0 = cmul(p0, make_float2(v.x, v.y));
         p1 = cmul(p1, make_float2(v.z, v.w));
       }
       float2 r;
       if (NV >= 1 && (K || NV >= 2)) {
-        const float4 v = *reinterpret_cast<const float4*>(ptr[NV - 1] + lo[NV - 1] + s_hi[NV - 1][it]);
+        const float4 v = *reinterpret_cast<const float4*>(ptr[NV - 1] + lo[NV - 1] + tab[NV - 1][32 + it]);
         float rx = p0.x * v.x;
         rx = fmaf(-p0.y, v.y, rx);
         rx = fmaf(p1.x, v.z, rx);
@@ -419,7 +419,7 @@ __device__ __forceinline__ void group_stage(const GParams& P, const GSt& S, int 
       }
       if (!K) r = make_float2(r.x * F, r.y * F);
       if (last) {
-        P.out[out_base + out_lo + s_out_hi[it]] = r;
+        out[out_base + out_lo + s_out_hi[it]] = r;
         *tmax = fmaxf(*tmax, fmaxf(fabsf(r.x), fabsf(r.y)));
       } else {
         cur[c] = r;
@@ -429,14 +429,14 @@ __device__ __forceinline__ void group_stage(const GParams& P, const GSt& S, int 
 }
 
 template <int NV>
-__device__ __forceinline__ void run_stage(bool with_k, const GParams& P, const GSt& S, int t, const float2* prev,
-                                          float2* cur, bool last, const long long* s_base, const float* s_scale,
-                                          int (*s_hi)[16], const int* s_out_hi, long long out_base, int out_lo,
+__device__ __forceinline__ void run_stage(bool with_k, const GSt& S, int t, const float2* prev, float2* cur,
+                                          float2* out, bool last, const float2* const* s_ptr, const float* s_scale,
+                                          const int (*tab)[48], const int* s_out_hi, long long out_base, int out_lo,
                                           float* tmax) {
   if (NV == 0 || with_k)
-    group_stage<NV, true>(P, S, t, prev, cur, last, s_base, s_scale, s_hi, s_out_hi, out_base, out_lo, tmax);
+    group_stage<NV, true>(S, t, prev, cur, out, last, s_ptr, s_scale, tab, s_out_hi, out_base, out_lo, tmax);
   else
-    group_stage<(NV > 0 ? NV : 1), false>(P, S, t, prev, cur, last, s_base, s_scale, s_hi, s_out_hi, out_base,
+    group_stage<(NV > 0 ? NV : 1), false>(S, t, prev, cur, out, last, s_ptr, s_scale, tab, s_out_hi, out_base,
                                           out_lo, tmax);
 }
 
@@ -445,10 +445,10 @@ __device__ __forceinline__ void run_stage(bool with_k, const GParams& P, const G
 __global__ void __launch_bounds__(TPB, 4) k_group(const __grid_constant__ GParams P, long long n_tiles) {
   extern __shared__ float2 g_stage[];  // stage regions A (2^(GL_MAX-1) entries) and B (half of A)
   __shared__ int s_hstr[GIN_MAX + 1][GH_MAX];  // row GIN_MAX: the output (within-item offsets < 2^31)
-  __shared__ long long s_base[GIN_MAX];
+  __shared__ const float2* s_ptr[GIN_MAX];
   __shared__ float s_scale[GIN_MAX];
   __shared__ int s_e[GIN_MAX];
-  __shared__ int s_hi[GM_MAX][KMAX][16];
+  __shared__ int s_tab[PAIR_MAX][48];
   __shared__ int s_out_hi[16];
   __shared__ long long s_out_base;
   __shared__ float s_red[TPB / 32];
@@ -463,13 +463,14 @@ __global__ void __launch_bounds__(TPB, 4) k_group(const __grid_constant__ GParam
   for (int s = 0; s < P.n_st; ++s) {
     const GSt& S = P.st[s];
     const int nb = S.nbits;
-    const int n_hi = nb > 8 ? (1 << (nb - 8)) : 1;
-    for (int e = t; e < S.n_var * n_hi; e += TPB) {
-      const int j = e / n_hi, it = e - j * n_hi;
+    for (int e = t; e < S.n_var * 48; e += TPB) {
+      const int j = e / 48, r = e - j * 48, part = r >> 4, v = r & 15;
       int a = 0;
-      for (int i = 8; i < nb; ++i)
-        if ((it >> (i - 8)) & 1) a += S.cstride[j][i];
-      s_hi[s][j][it] = a;
+      for (int i = 0; i < 4; ++i) {
+        const int bit = part * 4 + i;
+        if (bit < nb && ((v >> i) & 1)) a += S.cstride[j][bit];
+      }
+      s_tab[S.q0 + j][r] = a;
     }
   }
   const GSt& SL = P.st[P.n_st - 1];
@@ -506,13 +507,13 @@ __global__ void __launch_bounds__(TPB, 4) k_group(const __grid_constant__ GParam
       tmax = 0.f;
       cur_item = item;
     }
-    __syncthreads();  // previous tile done with s_base / stage buffers
+    __syncthreads();  // previous tile done with s_ptr / stage buffers
     if (t < P.n_gin) {
       const GIn& g = P.gin[t];
       long long b = g.dep ? item * g.istride : 0ll;
       for (int i = 0; i < P.n_h; ++i)
         if ((h >> i) & 1ll) b += s_hstr[t][i];
-      s_base[t] = b;
+      s_ptr[t] = g.ptr + b;
       if (g.meta < 0) {
         s_scale[t] = 1.f;
         s_e[t] = 0;
@@ -538,8 +539,14 @@ __global__ void __launch_bounds__(TPB, 4) k_group(const __grid_constant__ GParam
       const GSt& S = P.st[s];
       const bool last = (s == P.n_st - 1);
       const bool with_k = S.n_in > S.n_var;
-      switch (S.n_var) {
-#define TNQ_STAGE(n) run_stage<n>(with_k, P, S, t, prev, cur, last, s_base, s_scale, s_hi[s], s_out_hi, s_out_base, out_lo, &tmax)
+      // the dominant stage shapes (two varying operands, no constant pair,
+      // 2^11 or 2^12 local entries) get a fully unrolled entry loop
+      if (S.n_var == 2 && !with_k && S.nbits == 12)
+        group_stage<2, false, 16>(S, t, prev, cur, P.out, last, s_ptr, s_scale, s_tab + S.q0, s_out_hi, s_out_base, out_lo, &tmax);
+      else if (S.n_var == 2 && !with_k && S.nbits == 11)
+        group_stage<2, false, 8>(S, t, prev, cur, P.out, last, s_ptr, s_scale, s_tab + S.q0, s_out_hi, s_out_base, out_lo, &tmax);
+      else switch (S.n_var) {
+#define TNQ_STAGE(n) run_stage<n>(with_k, S, t, prev, cur, P.out, last, s_ptr, s_scale, s_tab + S.q0, s_out_hi, s_out_base, out_lo, &tmax)
         case 0: TNQ_STAGE(0); break;
         case 1: TNQ_STAGE(1); break;
         case 2: TNQ_STAGE(2); break;
@@ -928,6 +935,9 @@ static GParams group_gparams(const tnq_plan& P, const Layout& L, const FusedGrou
     std::stable_partition(ins.begin(), ins.end(), varies);
     S.n_var = 0;
     for (int tid : ins) S.n_var += varies(tid) ? 1 : 0;
+    S.q0 = G.n_pairs;
+    G.n_pairs += S.n_var;
+    if (G.n_pairs > PAIR_MAX) return G;
     for (int j = 0; j < B.k; ++j) {
       const int tid = ins[j];
       if (s > 0 && tid == prog.buckets[g.buckets[s - 1]].output) {
