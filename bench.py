@@ -156,6 +156,12 @@ def launch_roofline(L, plan, bits, ws, B, n_sl, stream, peaks, info):
                 "frac": one_gbs / hbm if one_gbs else None, "launches": len(one), "time_share": t_one / tot,
                 "bytes_per_launch": sum(by[i] for i in one) / max(len(one), 1),
                 "ms_per_launch": t_one / max(len(one), 1)}
+    big1 = [i for i in one if by[i] >= 64e6]  # launches large enough to stream at HBM speed
+    t_big1 = sum(ms[i] for i in big1)
+    if big1 and t_big1 > 0:
+        gbs = sum(by[i] for i in big1) / (t_big1 / 1e3) / 1e9
+        k_bucket["launches_ge_64MB"] = {"launches": len(big1), "achieved": gbs, "frac": gbs / hbm,
+                                        "share_of_k_bucket_time": t_big1 / t_one}
     k_group = {"kernel": "k_group", "bound": "alu", "achieved": grp_tfs, "peak": fp32, "unit": "TFLOP/s",
                "frac": grp_tfs / fp32 if grp_tfs else None, "launches": len(grp), "time_share": t_grp / tot,
                "flops_per_launch": sum(fl[i] for i in grp) / max(len(grp), 1),

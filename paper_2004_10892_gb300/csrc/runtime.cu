@@ -428,6 +428,108 @@ __device__ __forceinline__ void group_stage(const GSt& S, int t, const float2* p
   }
 }
 
+// Stage with NV = 1..3 varying operands and exactly 2^nbits = 256 NHI local
+// entries (NHI = 1 also covers nbits < 8: threads past the end compute a
+// duplicate entry from in-range offsets, since the tables hold 0 for bits >=
+// nbits, and do not store it). The entry loop is unrolled and each operand's
+// 16-byte loads run PF entries ahead of the arithmetic, so that several loads
+// per operand are in flight per thread (the loads are the latency that bounds
+// this kernel). K as in group_stage.
+template <int NV, bool K, int NHI>
+__device__ __forceinline__ void stage_pf(const GSt& S, int t, const float2* prev, float2* cur, float2* out,
+                                         bool last, const float2* const* s_ptr, const float* s_scale,
+                                         const int (*tab)[48], const int* s_out_hi, long long out_base, int out_lo,
+                                         float* tmax) {
+  static_assert(NV >= 1 && NV <= 3, "one to three varying operands");
+  constexpr int PF = NHI < 2 ? NHI : 2;
+  float F = 1.f;
+  for (int j = 0; j < S.n_in; ++j)
+    if (S.src[j] >= 0) F *= s_scale[S.src[j]];
+  float2 k0 = make_float2(F, 0.f), k1 = make_float2(F, 0.f);
+  if (K) {
+    for (int j = NV; j < S.n_in; ++j) {
+      const float2* q = S.src[j] < 0 ? prev : s_ptr[S.src[j]];
+      const float4 v = *reinterpret_cast<const float4*>(q);
+      k0 = cmul(k0, make_float2(v.x, v.y));
+      k1 = cmul(k1, make_float2(v.z, v.w));
+    }
+  }
+  const float2* pj[NV];
+#pragma unroll
+  for (int j = 0; j < NV; ++j)
+    pj[j] = (S.src[j] < 0 ? prev : s_ptr[S.src[j]]) + tab[j][t & 15] + tab[j][16 + ((t >> 4) & 15)];
+  float4 v[PF][NV];
+#pragma unroll
+  for (int i = 0; i < PF; ++i)
+#pragma unroll
+    for (int j = 0; j < NV; ++j) v[i][j] = *reinterpret_cast<const float4*>(pj[j] + tab[j][32 + i]);
+#pragma unroll
+  for (int it = 0; it < NHI; ++it) {
+    float4 cv[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) cv[j] = v[it % PF][j];
+    if (it + PF < NHI) {
+#pragma unroll
+      for (int j = 0; j < NV; ++j) v[it % PF][j] = *reinterpret_cast<const float4*>(pj[j] + tab[j][32 + it + PF]);
+    }
+    float2 p0 = k0, p1 = k1;
+    if (!K) {
+      p0 = make_float2(cv[0].x, cv[0].y);
+      p1 = make_float2(cv[0].z, cv[0].w);
+    }
+#pragma unroll
+    for (int j = K ? 0 : 1; j < NV - 1; ++j) {
+      p0 = cmul(p0, make_float2(cv[j].x, cv[j].y));
+      p1 = cmul(p1, make_float2(cv[j].z, cv[j].w));
+    }
+    float2 r;
+    if (K || NV >= 2) {
+      const float4 b = cv[NV - 1];
+      float rx = p0.x * b.x;
+      rx = fmaf(-p0.y, b.y, rx);
+      rx = fmaf(p1.x, b.z, rx);
+      rx = fmaf(-p1.y, b.w, rx);
+      float ry = p0.x * b.y;
+      ry = fmaf(p0.y, b.x, ry);
+      ry = fmaf(p1.x, b.w, ry);
+      ry = fmaf(p1.y, b.z, ry);
+      r = make_float2(rx, ry);
+    } else {
+      r = make_float2(p0.x + p1.x, p0.y + p1.y);
+    }
+    if (!K) r = make_float2(r.x * F, r.y * F);
+    const int c = t + (it << 8);
+    if (NHI > 1 || c < (1 << S.nbits)) {
+      if (last) {
+        out[out_base + out_lo + s_out_hi[it]] = r;
+        *tmax = fmaxf(*tmax, fmaxf(fabsf(r.x), fabsf(r.y)));
+      } else {
+        cur[c] = r;
+      }
+    }
+  }
+}
+
+// Dispatch of stage_pf over (NV, K, NHI); false if the stage has another shape.
+template <int NV, bool K>
+__device__ __forceinline__ bool stage_pf_nhi(const GSt& S, int t, const float2* prev, float2* cur, float2* out,
+                                             bool last, const float2* const* s_ptr, const float* s_scale,
+                                             const int (*tab)[48], const int* s_out_hi, long long out_base,
+                                             int out_lo, float* tmax) {
+#define TNQ_PF(n) stage_pf<NV, K, n>(S, t, prev, cur, out, last, s_ptr, s_scale, tab, s_out_hi, out_base, out_lo, tmax)
+  switch (S.nbits) {
+    case 12: TNQ_PF(16); return true;
+    case 11: TNQ_PF(8); return true;
+    case 10: TNQ_PF(4); return true;
+    case 9: TNQ_PF(2); return true;
+    default:
+      if (S.nbits > 8) return false;
+      TNQ_PF(1);
+      return true;
+  }
+#undef TNQ_PF
+}
+
 template <int NV>
 __device__ __forceinline__ void run_stage(bool with_k, const GSt& S, int t, const float2* prev, float2* cur,
                                           float2* out, bool last, const float2* const* s_ptr, const float* s_scale,
@@ -539,13 +641,13 @@ __global__ void __launch_bounds__(TPB, 4) k_group(const __grid_constant__ GParam
       const GSt& S = P.st[s];
       const bool last = (s == P.n_st - 1);
       const bool with_k = S.n_in > S.n_var;
-      // the dominant stage shapes (two varying operands, no constant pair,
-      // 2^11 or 2^12 local entries) get a fully unrolled entry loop
-      if (S.n_var == 2 && !with_k && S.nbits == 12)
-        group_stage<2, false, 16>(S, t, prev, cur, P.out, last, s_ptr, s_scale, s_tab + S.q0, s_out_hi, s_out_base, out_lo, &tmax);
-      else if (S.n_var == 2 && !with_k && S.nbits == 11)
-        group_stage<2, false, 8>(S, t, prev, cur, P.out, last, s_ptr, s_scale, s_tab + S.q0, s_out_hi, s_out_base, out_lo, &tmax);
-      else switch (S.n_var) {
+      bool done = false;
+#define TNQ_PFK(n) done = with_k ? stage_pf_nhi<n, true>(S, t, prev, cur, P.out, last, s_ptr, s_scale, s_tab + S.q0, s_out_hi, s_out_base, out_lo, &tmax) \
+                                 : stage_pf_nhi<n, false>(S, t, prev, cur, P.out, last, s_ptr, s_scale, s_tab + S.q0, s_out_hi, s_out_base, out_lo, &tmax)
+      if (S.n_var == 1) TNQ_PFK(1);
+      else if (S.n_var == 2) TNQ_PFK(2);
+#undef TNQ_PFK
+      if (!done) switch (S.n_var) {
 #define TNQ_STAGE(n) run_stage<n>(with_k, S, t, prev, cur, P.out, last, s_ptr, s_scale, s_tab + S.q0, s_out_hi, s_out_base, out_lo, &tmax)
         case 0: TNQ_STAGE(0); break;
         case 1: TNQ_STAGE(1); break;
