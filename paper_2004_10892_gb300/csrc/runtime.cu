@@ -1661,6 +1661,24 @@ int tnq_internal_validate(const tnq_plan* plan, int mode, uint32_t batch, char* 
   return m.empty() ? 0 : 1;
 }
 
+// Internal hook (not in include/tnq.h; host only): the kernel kind of every
+// step of the (mode, batch) configuration in program order (0 k_bucket,
+// 1 k_group, 2 GEMM) and, for steps of a group, its bucket count.
+int tnq_internal_step_kinds(const tnq_plan* plan, int mode, uint32_t batch, int32_t* kind, int32_t* nbk, int cap,
+                            int32_t* out_n) {
+  if (!plan || !kind || !out_n) return 1;
+  ExecConfig C;
+  C.L = make_layout(*plan, mode, (int)batch);
+  if (!build_steps(*plan, C.L, C)) return 1;
+  *out_n = (int32_t)C.steps.size();
+  if ((int)C.steps.size() > cap) return 1;
+  for (size_t i = 0; i < C.steps.size(); ++i) {
+    kind[i] = C.steps[i].first;
+    if (nbk) nbk[i] = C.step_group[i] < 0 ? 1 : (int32_t)plan->prog.groups[C.step_group[i]].buckets.size();
+  }
+  return 0;
+}
+
 // Internal measurement hook (not in include/tnq.h): runs the first batch of
 // tnq_contract_sliced(plan, bits, s0, s1, ...) with direct launches and a
 // CUDA event pair around every bucket launch on `stream`. Per bucket it

@@ -118,3 +118,22 @@ def test_launch_bounds_hold_on_host(tnq_lib):
         for mode in (0, 1):
             for B in (1, 2, 8, 64, 1024):
                 assert f(plan.handle, mode, B, buf, 256) == 0, (c.name, mode, B, buf.value)
+
+
+def test_step_kinds_of_the_7x7_plan(tnq_lib):
+    """Host-only configuration: the 7x7 depth 1+32+1 plan runs its chains as
+    fused k_group steps and every other bucket as a k_bucket step."""
+    L = tnq_lib.lib()
+    f = L.tnq_internal_step_kinds
+    P = ctypes.POINTER
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32, P(ctypes.c_int32), P(ctypes.c_int32), ctypes.c_int,
+                  P(ctypes.c_int32)]
+    plan = tnq_lib.Plan(I.random_grid_circuit(7, 7, 32, 0), max_bag_log2=28, max_p=40)
+    info = plan.info()
+    kind = (ctypes.c_int32 * 4096)()
+    nbk = (ctypes.c_int32 * 4096)()
+    n = ctypes.c_int32()
+    assert f(plan.handle, 0, 256, kind, nbk, 4096, ctypes.byref(n)) == 0
+    kinds = [kind[i] for i in range(n.value)]
+    assert kinds.count(1) == info["n_fused_groups"] and set(kinds) <= {0, 1}
+    assert sum(nbk[i] for i in range(n.value)) == info["n_buckets"]

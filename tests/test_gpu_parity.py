@@ -240,6 +240,24 @@ def test_fused_equals_unfused(cuda, tnq_lib):
     assert np.max(np.abs(a - b)) <= 1e-6 * np.max(np.abs(b))
 
 
+@pytest.mark.parametrize("fuse", [0, 12])
+def test_leaf_absorption_matches_oracle(cuda, tnq_lib, oracle_lib, fuse):
+    """Gate tensors moved into smaller producing buckets (leaf absorption) give the
+    oracle's slices, which keep every gate tensor in the bucket of its earliest
+    variable; with absorption off the same plan agrees too."""
+    circ = I.random_grid_circuit(6, 6, 24, 2)
+    bits = I.random_bitstring(36, 2)
+    ref, ref_per = None, None
+    for la in (1, 0):
+        plan = tnq_lib.Plan(circ, max_bag_log2=22, min_p=5, max_p=5, fuse_min_rank=fuse, leaf_absorb=la)
+        amp, per = tnq_lib.contract_sliced(plan, bits, per_slice=True)
+        if ref is None:
+            ref, ref_per = oracle_lib.contract(circ, bits, order=plan.order(), mu=plan.sliced(), per_slice=True)
+        for s in range(len(per)):
+            assert rel_err(per[s], ref_per[s], 36) < TOL, (la, s)
+        assert rel_err(amp, ref, 36) < TOL
+
+
 def test_autotune_keeps_results(cuda, tnq_lib, oracle_lib):
     """Autotuning only chooses between fused and unfused forms of the same products."""
     circ = I.random_grid_circuit(6, 6, 24, 1)
