@@ -253,6 +253,9 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--precision", default="c64", choices=["c64", "bf16x3", "tf32x3"],
                     help="merged GEMM-shaped buckets on tensor cores in split precision")
+    ap.add_argument("--plain", action="store_true",
+                    help="plain complex64 per-slice form: one kernel per bucket, no fusion or leaf absorption, "
+                         "one slice per launch (a comparison line, not the headline)")
     ap.add_argument("--tune-batch", type=int, default=16, help="slices per batch while autotuning")
     ap.add_argument("--tune-gb", type=int, default=48, help="workspace GiB while autotuning")
     args = ap.parse_args()
@@ -279,7 +282,11 @@ def main():
     bits = inputs.random_bitstring(circ.n_qubits, rank)
     t_plan = time.perf_counter()
     prec = {"c64": 0, "bf16x3": 1, "tf32x3": 2}[args.precision]
-    plan = tnq.Plan(circ, max_bag_log2=mb, min_p=pmin, max_p=pmax, precision=prec, gemm_min_k_log2=4)
+    if args.plain:
+        args.precision, prec, args.max_batch, args.no_autotune = "c64", 0, 1, True
+        plan = tnq.Plan(circ, max_bag_log2=mb, min_p=pmin, max_p=pmax, fuse_min_rank=0, leaf_absorb=0)
+    else:
+        plan = tnq.Plan(circ, max_bag_log2=mb, min_p=pmin, max_p=pmax, precision=prec, gemm_min_k_log2=4)
     t_plan = time.perf_counter() - t_plan
     n_sl = plan.info()["n_slices"]
     stream = torch.cuda.current_stream()
@@ -362,7 +369,8 @@ def main():
                        "flops_per_slice": info["flops_per_slice"], "bytes_per_slice": info["bytes_per_slice"],
                        "l2": "inputs larger than L2 (each batch streams GBs)", "plan_s": t_plan,
                        "autotune_s": t_tune, "fused_chains": info["n_fused_groups"],
-                       "gemm_buckets": info["n_gemm_buckets"], "precision": args.precision},
+                       "gemm_buckets": info["n_gemm_buckets"], "precision": args.precision,
+                       "form": "plain per-slice" if args.plain else "batched, fused, autotuned"},
             "time_per_amplitude_s": t_dev / args.steps,
             "rel_err_vs_fp64": err,
             "amplitude": [amp.real, amp.imag],

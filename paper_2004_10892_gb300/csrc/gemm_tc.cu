@@ -1,14 +1,14 @@
 // gemm_tc.cu -- tcgen05 split-precision batched GEMM (see gemm_tc.cuh).
 //
-// One block (4 warps) computes one 128 x 128 FP32 tile of C in tensor memory:
-// thread 0 streams the A/B hi/lo tiles of each K step into a double-buffered
-// shared-memory stage with bulk-async copies (mbarrier transaction counts),
-// issues the three split-precision MMA passes (hi*hi, hi*lo, lo*hi; lo*lo is
-// below FP32 rounding and dropped) and commits them to a per-stage mbarrier;
-// the four warps then read their 32 accumulator lanes with tcgen05.ld.
-// Every wait is bounded by %globaltimer: on a timeout the kernel records a
-// status, waits (bounded) for the copies and MMAs it issued, frees its tensor
-// memory and returns.
+// A persistent, warp-specialised kernel: per block one thread streams the
+// A/B hi/lo tiles of every K step into a 3-stage shared-memory ring with
+// bulk-async copies (mbarrier transaction counts), one thread issues the
+// three split-precision MMA passes (hi*hi, hi*lo, lo*hi; lo*lo is below FP32
+// rounding and dropped) into one of two tensor-memory accumulators, and four
+// warps read the other accumulator with tcgen05.ld and write the previous
+// tile. Every wait is bounded by %globaltimer: on a timeout the kernel
+// records a status, waits (bounded) for the copies and MMAs it issued, frees
+// its tensor memory and returns.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -137,138 +137,240 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 }
 
 constexpr int STAGE_BYTES = 4 * GT_TILE_BYTES;  // A hi, A lo, B hi, B lo
-constexpr int SMEM_BYTES = 2 * STAGE_BYTES + 1024;
+constexpr int N_STAGES = 3;                      // shared-memory ring of K steps
+constexpr int SMEM_BYTES = N_STAGES * STAGE_BYTES + 1024;
+constexpr int GEMM_THREADS = 192;  // warp 0: copies, warp 1: MMAs, warps 2-5: epilogue
+constexpr uint32_t TMEM_COLS = 256;  // two 128-column FP32 accumulators
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void epi_sync() {  // the four epilogue warps
+  asm volatile("bar.sync 1, 128;" ::: "memory");
+}
+
+// Persistent, warp-specialised GEMM. Each block loops over output tiles
+// tile = blockIdx.x + i * gridDim.x (tile -> batch b, row tile rt, column
+// tile ct, ct fastest). Warp 0 (one thread) streams the four 16 KB operand
+// tiles of every K step into a ring of N_STAGES shared-memory stages (bulk
+// async copies completing on full[s]); warp 1 (one thread) waits for a stage,
+// issues the 12 MMAs of the three split-precision passes into accumulator
+// buffer i & 1 and commits them to empty[s] (stage free) and, after the last
+// K step, to tfull[buf]; warps 2-5 read the accumulator lanes of their TMEM
+// quarter, write the tile and arrive on tempty[buf]. The accumulators are
+// double-buffered, so tile i's epilogue overlaps tile i+1's copies and MMAs.
+// Every wait is bounded; on a timeout the block records a status, stops
+// issuing, waits (bounded) for what it issued and frees its tensor memory.
 template <int KIND>
-__global__ void __launch_bounds__(128) k_gemm_tc(const GemmArgs a) {
+__global__ void __launch_bounds__(GEMM_THREADS, 1) k_gemm_tc(const GemmArgs a) {
   extern __shared__ uint8_t smem_raw[];
-  __shared__ uint64_t full_bar[2], mma_bar[2];
+  __shared__ uint64_t full_bar[N_STAGES], empty_bar[N_STAGES], tfull_bar[2], tempty_bar[2], drain_bar;
   __shared__ uint32_t tmem_slot;
-  __shared__ int s_fail;
+  __shared__ volatile int s_fail;
+  __shared__ long long s_yoff[2][64];
+  __shared__ int s_epi_stop[2];  // per tile parity: an epilogue thread's wait failed (set once, never cleared)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int ct = blockIdx.x, rt = blockIdx.y, b = blockIdx.z;
   const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  const long long n_tiles = (long long)a.batch * a.row_tiles_a * a.row_tiles_b;
   if (tid == 0) {
-    mbar_init(&full_bar[0], 1);
-    mbar_init(&full_bar[1], 1);
-    mbar_init(&mma_bar[0], 1);
-    mbar_init(&mma_bar[1], 1);
+    for (int s = 0; s < N_STAGES; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull_bar[b], 1);
+      mbar_init(&tempty_bar[b], 4);
+    }
+    mbar_init(&drain_bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     s_fail = 0;
+    s_epi_stop[0] = s_epi_stop[1] = 0;
   }
-  if (warp == 0) {
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                 "r"(128u)
+                 "r"(TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tmem_d = tmem_slot;
+  const uint32_t tmem_base = tmem_slot;
+  const size_t tb = GT_TILE_BYTES;
 
-  if (tid == 0) {
-    const size_t tile = GT_TILE_BYTES;
-    const char* A_hi = (const char*)a.a_hi + (size_t)(b * a.row_tiles_a + rt) * a.k_tiles * tile;
-    const char* A_lo = (const char*)a.a_lo + (size_t)(b * a.row_tiles_a + rt) * a.k_tiles * tile;
-    const char* B_hi = (const char*)a.b_hi + (size_t)(b * a.row_tiles_b + ct) * a.k_tiles * tile;
-    const char* B_lo = (const char*)a.b_lo + (size_t)(b * a.row_tiles_b + ct) * a.k_tiles * tile;
+  if (warp == 0 && lane == 0) {
+    // ---- producer: bulk copies of every K step of every tile of this block
+    int fills[N_STAGES] = {};
+    long long g = 0;
     bool ok = true;
-    int copies_pending = -1, mma_pending = -1;  // last k step whose copies / MMAs were issued but not waited for
-    for (int kt = 0; kt < a.k_tiles && ok; ++kt) {
-      const int s = kt & 1;
-      if (kt >= 2) {
-        ok = mbar_wait(&mma_bar[s], ((kt >> 1) - 1) & 1);  // MMAs of step kt-2 released stage s
-        if (!ok) break;
+    for (long long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+      const int ct = (int)(tile % a.row_tiles_b);
+      const int rt = (int)((tile / a.row_tiles_b) % a.row_tiles_a);
+      const long long b = tile / ((long long)a.row_tiles_b * a.row_tiles_a);
+      const char* A_hi = (const char*)a.a_hi + (size_t)(b * a.row_tiles_a + rt) * a.k_tiles * tb;
+      const char* A_lo = (const char*)a.a_lo + (size_t)(b * a.row_tiles_a + rt) * a.k_tiles * tb;
+      const char* B_hi = (const char*)a.b_hi + (size_t)(b * a.row_tiles_b + ct) * a.k_tiles * tb;
+      const char* B_lo = (const char*)a.b_lo + (size_t)(b * a.row_tiles_b + ct) * a.k_tiles * tb;
+      for (int kt = 0; kt < a.k_tiles; ++kt, ++g) {
+        const int s = (int)(g % N_STAGES);
+        if (fills[s] > 0 && !mbar_wait(&empty_bar[s], (fills[s] - 1) & 1)) {  // the MMAs released stage s
+          ok = false;
+          break;
+        }
+        if (s_fail) {
+          ok = false;
+          break;
+        }
+        const uint32_t st = base + (uint32_t)s * STAGE_BYTES;
+        mbar_expect_tx(&full_bar[s], STAGE_BYTES);
+        bulk_g2s(st + 0 * GT_TILE_BYTES, A_hi + kt * tb, GT_TILE_BYTES, &full_bar[s]);
+        bulk_g2s(st + 1 * GT_TILE_BYTES, A_lo + kt * tb, GT_TILE_BYTES, &full_bar[s]);
+        bulk_g2s(st + 2 * GT_TILE_BYTES, B_hi + kt * tb, GT_TILE_BYTES, &full_bar[s]);
+        bulk_g2s(st + 3 * GT_TILE_BYTES, B_lo + kt * tb, GT_TILE_BYTES, &full_bar[s]);
+        ++fills[s];
       }
-      const uint32_t st = base + (uint32_t)s * STAGE_BYTES;
-      mbar_expect_tx(&full_bar[s], STAGE_BYTES);
-      bulk_g2s(st + 0 * GT_TILE_BYTES, A_hi + kt * tile, GT_TILE_BYTES, &full_bar[s]);
-      bulk_g2s(st + 1 * GT_TILE_BYTES, A_lo + kt * tile, GT_TILE_BYTES, &full_bar[s]);
-      bulk_g2s(st + 2 * GT_TILE_BYTES, B_hi + kt * tile, GT_TILE_BYTES, &full_bar[s]);
-      bulk_g2s(st + 3 * GT_TILE_BYTES, B_lo + kt * tile, GT_TILE_BYTES, &full_bar[s]);
-      copies_pending = kt;
-      ok = mbar_wait(&full_bar[s], (kt >> 1) & 1);
-      if (!ok) break;
-      copies_pending = -1;
-      tc_fence_after();
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {  // 4 MMAs of 32 bytes of K per 128-byte tile row
-        const uint32_t off = (uint32_t)j * 256u;
-        mma<KIND>(tmem_d, sdesc(st + off), sdesc(st + 2 * GT_TILE_BYTES + off), (kt > 0 || j > 0) ? 1u : 0u);
-        mma<KIND>(tmem_d, sdesc(st + off), sdesc(st + 3 * GT_TILE_BYTES + off), 1u);
-        mma<KIND>(tmem_d, sdesc(st + GT_TILE_BYTES + off), sdesc(st + 2 * GT_TILE_BYTES + off), 1u);
-      }
-      mma_commit(&mma_bar[s]);
-      mma_pending = kt;
-    }
-    if (ok && mma_pending >= 0) {
-      ok = mbar_wait(&mma_bar[mma_pending & 1], (mma_pending >> 1) & 1);
-      if (ok) mma_pending = -1;
     }
     if (!ok) {
       s_fail = 1;
       atomicExch(a.status, 1);
-      // drain what this thread issued before the block frees its resources
-      if (copies_pending >= 0) mbar_wait(&full_bar[copies_pending & 1], (copies_pending >> 1) & 1);
-      if (mma_pending >= 0) mbar_wait(&mma_bar[mma_pending & 1], (mma_pending >> 1) & 1);
     }
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  if (!s_fail && a.out_c) {
-    const int row = rt * GT_ROWS + warp * 32 + lane;
-    float* crow = a.out_c + ((long long)b * a.row_tiles_a * GT_ROWS + row) * a.ldc + (long long)ct * 128;
-#pragma unroll 1
-    for (int chunk = 0; chunk < 4; ++chunk) {
-      float v[32];
-      tmem_ld32(tmem_d + ((uint32_t)(warp * 32) << 16) + (uint32_t)(chunk * 32), v);
+    // every issued copy has landed before the block can exit
+    for (int s = 0; s < N_STAGES; ++s)
+      if (fills[s] > 0) mbar_wait(&full_bar[s], (fills[s] - 1) & 1);
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer
+    long long g = 0;
+    bool ok = true, issued = false;
+    long long i = 0;
+    for (long long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++i) {
+      const int buf = (int)(i & 1);
+      const long long j = i >> 1;
+      if (j >= 1 && !mbar_wait(&tempty_bar[buf], (uint32_t)((j - 1) & 1))) {  // epilogue done with buffer buf
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t tmem_d = tmem_base + (uint32_t)buf * 128u;
+      for (int kt = 0; kt < a.k_tiles; ++kt, ++g) {
+        const int s = (int)(g % N_STAGES);
+        const long long n = g / N_STAGES;
+        if (!mbar_wait(&full_bar[s], (uint32_t)(n & 1)) || s_fail) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t st = base + (uint32_t)s * STAGE_BYTES;
 #pragma unroll
-      for (int i = 0; i < 32; i += 4)
-        *reinterpret_cast<float4*>(crow + chunk * 32 + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+        for (int q = 0; q < 4; ++q) {  // 4 MMAs of 32 bytes of K per 128-byte tile row
+          const uint32_t off = (uint32_t)q * 256u;
+          mma<KIND>(tmem_d, sdesc(st + off), sdesc(st + 2 * GT_TILE_BYTES + off), (kt > 0 || q > 0) ? 1u : 0u);
+          mma<KIND>(tmem_d, sdesc(st + off), sdesc(st + 3 * GT_TILE_BYTES + off), 1u);
+          mma<KIND>(tmem_d, sdesc(st + GT_TILE_BYTES + off), sdesc(st + 2 * GT_TILE_BYTES + off), 1u);
+        }
+        mma_commit(&empty_bar[s]);
+        issued = true;
+      }
+      if (ok) mma_commit(&tfull_bar[buf]);
     }
-  } else if (!s_fail) {
-    // bucket epilogue: row = X assignment, column pair (2n, 2n+1) = (Re, Im) of Y assignment n
-    const GemmEpilogue& ep = a.ep;
-    const int m = rt * GT_ROWS + warp * 32 + lane;
-    const long long item = b >> ep.ns, sidx = b & ((1ll << ep.ns) - 1);
-    float tmax = 0.f;
-    const bool row_ok = m < (1 << ep.nx);
-    long long base = ep.dep ? item * ep.istride : 0ll;
-    for (int i = 0; i < ep.ns; ++i)
-      if ((sidx >> i) & 1) base += ep.s[i];
-    for (int i = 0; i < ep.nx; ++i)
-      if ((m >> i) & 1) base += ep.x[i];
-#pragma unroll 1
-    for (int chunk = 0; chunk < 4; ++chunk) {
-      float v[32];
-      // warp-collective: every lane loads, whether or not its row is written
-      tmem_ld32(tmem_d + ((uint32_t)(warp * 32) << 16) + (uint32_t)(chunk * 32), v);
-      if (row_ok) {
-#pragma unroll 1
-        for (int i = 0; i < 32; i += 2) {
-          const int n = (ct * 128 + chunk * 32 + i) >> 1;
-          if (n >= (1 << ep.ny)) break;
-          long long off = base;
+    if (!ok) {
+      s_fail = 1;
+      atomicExch(a.status, 2);
+    }
+    if (issued) {  // every issued MMA has completed before the block frees tensor memory
+      mma_commit(&drain_bar);
+      mbar_wait(&drain_bar, 0);
+    }
+  } else if (warp >= 2) {
+    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 = tile rows
+    const int quarter = warp & 3;
+    const int r_in = quarter * 32 + lane;
+    const int e = tid - 64;  // 0..127
+    long long i = 0;
+    for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++i) {
+      const int buf = (int)(i & 1);
+      const long long j = i >> 1;
+      const int ct = (int)(tile % a.row_tiles_b);
+      const int rt = (int)((tile / a.row_tiles_b) % a.row_tiles_a);
+      const long long b = tile / ((long long)a.row_tiles_b * a.row_tiles_a);
+      const GemmEpilogue& ep = a.ep;
+      if (!a.out_c && e < 64) {  // column offsets of this tile (complex column n = ct * 64 + e)
+        const int n = ct * 64 + e;
+        long long off = -1;
+        if (n < (1 << ep.ny)) {
+          off = 0;
           for (int q = 0; q < ep.ny; ++q)
             if ((n >> q) & 1) off += ep.y[q];
-          ep.out[off] = make_float2(v[i], v[i + 1]);
-          tmax = fmaxf(tmax, fmaxf(fabsf(v[i]), fabsf(v[i + 1])));
+        }
+        s_yoff[buf][e] = off;
+      }
+      // the four warps take the same decision: a failed wait is published in
+      // this tile parity's flag before the barrier and read after it
+      if (!mbar_wait(&tfull_bar[buf], (uint32_t)(j & 1)) || s_fail) s_epi_stop[buf] = 1;
+      epi_sync();
+      if (s_epi_stop[buf]) {
+        s_fail = 1;
+        atomicExch(a.status, 2);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)buf * 128u;
+      if (a.out_c) {
+        float* crow = a.out_c + ((long long)b * a.row_tiles_a * GT_ROWS + rt * GT_ROWS + r_in) * a.ldc +
+                      (long long)ct * 128;
+#pragma unroll 1
+        for (int chunk = 0; chunk < 4; ++chunk) {
+          float v[32];
+          tmem_ld32(taddr + (uint32_t)(chunk * 32), v);
+#pragma unroll
+          for (int q = 0; q < 32; q += 4)
+            *reinterpret_cast<float4*>(crow + chunk * 32 + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+        }
+      } else {
+        // row = X assignment m, column pair (2n, 2n+1) = (Re, Im) of Y assignment n
+        const int m = rt * GT_ROWS + r_in;
+        const long long item = b >> ep.ns, sidx = b & ((1ll << ep.ns) - 1);
+        const bool row_ok = m < (1 << ep.nx);
+        long long rbase = ep.dep ? item * ep.istride : 0ll;
+        for (int q = 0; q < ep.ns; ++q)
+          if ((sidx >> q) & 1) rbase += ep.s[q];
+        for (int q = 0; q < ep.nx; ++q)
+          if ((m >> q) & 1) rbase += ep.x[q];
+        float tmax = 0.f;
+#pragma unroll 1
+        for (int chunk = 0; chunk < 4; ++chunk) {
+          float v[32];
+          tmem_ld32(taddr + (uint32_t)(chunk * 32), v);  // warp-collective: every lane loads
+          if (row_ok) {
+#pragma unroll
+            for (int q = 0; q < 32; q += 2) {
+              const long long yo = s_yoff[buf][chunk * 16 + (q >> 1)];
+              if (yo >= 0) {
+                ep.out[rbase + yo] = make_float2(v[q], v[q + 1]);
+                tmax = fmaxf(tmax, fmaxf(fabsf(v[q]), fabsf(v[q + 1])));
+              }
+            }
+          }
+        }
+        for (int off = 16; off > 0; off >>= 1) tmax = fmaxf(tmax, __shfl_xor_sync(0xffffffffu, tmax, off));
+        if (lane == 0 && tmax > 0.f) {
+          unsigned* p = &ep.meta_m[(long long)ep.meta * ep.B + (ep.dep ? item : 0ll)];
+          const unsigned bits = __float_as_uint(tmax);
+          if (bits > *reinterpret_cast<volatile unsigned*>(p)) atomicMax(p, bits);
         }
       }
-    }
-    for (int off = 16; off > 0; off >>= 1) tmax = fmaxf(tmax, __shfl_xor_sync(0xffffffffu, tmax, off));
-    if (lane == 0 && tmax > 0.f) {
-      unsigned* p = &ep.meta_m[(long long)ep.meta * ep.B + (ep.dep ? item : 0ll)];
-      const unsigned bits = __float_as_uint(tmax);
-      if (bits > *reinterpret_cast<volatile unsigned*>(p)) atomicMax(p, bits);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty_bar[buf]);
     }
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_d), "r"(128u) : "memory");
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS) : "memory");
+  }
 }
 
 // Split of real matrices (rows x K per batch, row-major FP32) into hi/lo
@@ -422,13 +524,20 @@ __global__ void k_gemm_pack(const GemmBucketArgs g, int side) {
 
 void gemm_tc_launch(int kind, const GemmArgs& args, void* stream) {
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  dim3 grid(args.row_tiles_b, args.row_tiles_a, args.batch);
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      sms = 148;
+  }
+  const long long tiles = (long long)args.batch * args.row_tiles_a * args.row_tiles_b;
+  const unsigned grid = (unsigned)std::max<long long>(1, std::min<long long>(tiles, sms));  // one block per SM
   if (kind == GEMM_BF16) {
     cudaFuncSetAttribute(k_gemm_tc<GEMM_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    k_gemm_tc<GEMM_BF16><<<grid, 128, SMEM_BYTES, s>>>(args);
+    k_gemm_tc<GEMM_BF16><<<grid, GEMM_THREADS, SMEM_BYTES, s>>>(args);
   } else {
     cudaFuncSetAttribute(k_gemm_tc<GEMM_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    k_gemm_tc<GEMM_TF32><<<grid, 128, SMEM_BYTES, s>>>(args);
+    k_gemm_tc<GEMM_TF32><<<grid, GEMM_THREADS, SMEM_BYTES, s>>>(args);
   }
 }
 
