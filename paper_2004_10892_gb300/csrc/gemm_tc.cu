@@ -419,55 +419,52 @@ __device__ __forceinline__ float pack_scale(unsigned mbits, int* mexp) {
   return __int_as_float((127 - m) << 23);
 }
 
-__device__ __forceinline__ float2 operand_value(const GemmOperand& o, long long item, long long s, long long r,
-                                                long long k, int ns, int nr, int nk, float f) {
-  long long off = o.dep ? item * o.istride : 0ll;
-  for (int i = 0; i < ns; ++i)
-    if ((s >> i) & 1) off += o.sstride[i];
-  for (int i = 0; i < nr; ++i)
-    if ((r >> i) & 1) off += o.rstride[i];
-  for (int i = 0; i < nk; ++i)
-    if ((k >> i) & 1) off += o.kstride[i];
-  const float2 v = o.ptr[off];
-  return make_float2(v.x * f, v.y * f);
-}
-
-__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
-  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-
-template <int KIND>
-__device__ __forceinline__ void store_split(void* hi, void* lo, size_t off, float x) {
+// 16 bytes of hi and lo parts of CH consecutive values (CH = 8 BF16 or 4 TF32).
+template <int KIND, int CH>
+__device__ __forceinline__ void split16(const float* x, uint4* hi, uint4* lo) {
+  uint32_t h[4], l[4];
   if (KIND == GEMM_BF16) {
-    const __nv_bfloat16 h = __float2bfloat16_rn(x);
-    const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
-    *reinterpret_cast<__nv_bfloat16*>((char*)hi + off) = h;
-    *reinterpret_cast<__nv_bfloat16*>((char*)lo + off) = l;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const __nv_bfloat16 h0 = __float2bfloat16_rn(x[2 * q]), h1 = __float2bfloat16_rn(x[2 * q + 1]);
+      const __nv_bfloat16 l0 = __float2bfloat16_rn(x[2 * q] - __bfloat162float(h0));
+      const __nv_bfloat16 l1 = __float2bfloat16_rn(x[2 * q + 1] - __bfloat162float(h1));
+      h[q] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+      l[q] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+    }
   } else {
-    uint32_t h, l;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
-    const float rest = x - __uint_as_float(h);
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(rest));
-    *reinterpret_cast<uint32_t*>((char*)hi + off) = h;
-    *reinterpret_cast<uint32_t*>((char*)lo + off) = l;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h[q]) : "f"(x[q]));
+      const float rest = x[q] - __uint_as_float(h[q]);
+      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l[q]) : "f"(rest));
+    }
   }
+  *hi = make_uint4(h[0], h[1], h[2], h[3]);
+  *lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
 // side 0: A rows = X assignments, columns [Re | Im] over K.
 // side 1: B rows 2n, 2n+1 = [Re | -Im], [Im | Re] over K for Y assignment n.
+// A thread forms CH consecutive K values of one row (one 16-byte chunk of a
+// core-matrix row per part); consecutive threads take consecutive rows, so
+// eight threads fill one 128-byte core matrix.
 template <int KIND>
 __global__ void k_gemm_pack(const GemmBucketArgs g, int side) {
-  const int esize = KIND == GEMM_BF16 ? 2 : 4;
+  constexpr int ES = KIND == GEMM_BF16 ? 2 : 4;
+  constexpr int CH = 16 / ES;
+  constexpr int CHB = KIND == GEMM_BF16 ? 3 : 2;  // log2 CH
   const GemmOperand* ops = side == 0 ? g.a : g.b;
   const int nops = side == 0 ? g.na : g.nb;
   const int nr = side == 0 ? g.nx : g.ny;
   const long long rows = side == 0 ? g.m_pad : g.n_pad;  // complex rows
   const long long batch = (long long)g.items << g.ns;
-  const long long n = batch * rows * g.k_pad;
-  const int kt_count = 2 * g.k_pad * esize / GT_KBYTES;
+  const int kch = g.k_pad / CH;  // chunks per row (k_pad is a multiple of 64 / ES)
+  const long long n = batch * rows * kch;
+  const int kt_count = 2 * g.k_pad * ES / GT_KBYTES;
   const int rt_count = (int)((side == 0 ? rows : 2 * rows) / GT_ROWS);
-  void* hi = side == 0 ? g.a_hi : g.b_hi;
-  void* lo = side == 0 ? g.a_lo : g.b_lo;
+  char* hi = (char*)(side == 0 ? g.a_hi : g.b_hi);
+  char* lo = (char*)(side == 0 ? g.a_lo : g.b_lo);
   if (side == 0 && blockIdx.x == 0) {
     // output exponent per item: sum over every operand of its exponent and scale shift
     for (int it = threadIdx.x; it < g.items; it += blockDim.x) {
@@ -484,13 +481,19 @@ __global__ void k_gemm_pack(const GemmBucketArgs g, int side) {
     }
   }
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const long long k = i % g.k_pad;
-    const long long r = (i / g.k_pad) % rows;
-    const long long bi = i / ((long long)g.k_pad * rows);
-    const long long item = bi >> g.ns, s = bi & ((1ll << g.ns) - 1);
-    float2 v = make_float2(0.f, 0.f);
-    if (r < (1ll << nr) && k < (1ll << g.nk)) {
-      v = make_float2(1.f, 0.f);
+    const long long r = i % rows;
+    const int kc = (int)((i / rows) % kch);
+    const long long bi = i / (rows * kch);
+    const long long item = bi >> g.ns, sidx = bi & ((1ll << g.ns) - 1);
+    const int k0 = kc * CH;
+    float re[CH], im[CH];
+    const bool row_ok = r < (1ll << nr);
+#pragma unroll
+    for (int q = 0; q < CH; ++q) {
+      re[q] = row_ok && (k0 + q) < (1 << g.nk) ? 1.f : 0.f;
+      im[q] = 0.f;
+    }
+    if (row_ok && k0 < (1 << g.nk)) {
       for (int j = 0; j < nops; ++j) {
         const GemmOperand& o = ops[j];
         float f = 1.f;
@@ -498,24 +501,66 @@ __global__ void k_gemm_pack(const GemmBucketArgs g, int side) {
           int m;
           f = pack_scale(g.meta_m[(long long)o.meta * g.B + (o.dep ? item : 0ll)], &m);
         }
-        v = cmulf(v, operand_value(o, item, s, r, k, g.ns, nr, g.nk, f));
+        long long base = o.dep ? item * o.istride : 0ll;
+        for (int b = 0; b < g.ns; ++b)
+          if ((sidx >> b) & 1) base += o.sstride[b];
+        for (int b = 0; b < nr; ++b)
+          if ((r >> b) & 1) base += o.rstride[b];
+        for (int b = CHB; b < g.nk; ++b)
+          if ((k0 >> b) & 1) base += o.kstride[b];
+#pragma unroll
+        for (int q = 0; q < CH; ++q) {
+          if (k0 + q >= (1 << g.nk)) continue;
+          long long off = base;
+#pragma unroll
+          for (int b = 0; b < CHB; ++b)
+            if (((q >> b) & 1) && b < g.nk) off += o.kstride[b];
+          const float2 v = o.ptr[off];
+          const float vx = v.x * f, vy = v.y * f;
+          const float nre = re[q] * vx - im[q] * vy, nim = re[q] * vy + im[q] * vx;
+          re[q] = nre;
+          im[q] = nim;
+        }
       }
     }
+    uint4 h, l;
     const size_t tb = (size_t)GT_TILE_BYTES;
+    const int kre = k0, kim = g.k_pad + k0;
     if (side == 0) {
-      const size_t t0 = ((size_t)(bi * rt_count + r / GT_ROWS) * kt_count);
-      const int kre = (int)k, kim = (int)(g.k_pad + k);
-      store_split<KIND>(hi, lo, (t0 + (size_t)(kre * esize / GT_KBYTES)) * tb + gt_offset((int)(r % GT_ROWS), kre, esize), v.x);
-      store_split<KIND>(hi, lo, (t0 + (size_t)(kim * esize / GT_KBYTES)) * tb + gt_offset((int)(r % GT_ROWS), kim, esize), v.y);
+      const size_t t0 = (size_t)(bi * rt_count + r / GT_ROWS) * kt_count;
+      split16<KIND, CH>(re, &h, &l);
+      size_t off = (t0 + (size_t)(kre * ES / GT_KBYTES)) * tb + gt_offset((int)(r % GT_ROWS), kre, ES);
+      *reinterpret_cast<uint4*>(hi + off) = h;
+      *reinterpret_cast<uint4*>(lo + off) = l;
+      split16<KIND, CH>(im, &h, &l);
+      off = (t0 + (size_t)(kim * ES / GT_KBYTES)) * tb + gt_offset((int)(r % GT_ROWS), kim, ES);
+      *reinterpret_cast<uint4*>(hi + off) = h;
+      *reinterpret_cast<uint4*>(lo + off) = l;
     } else {
+      float nim[CH];
+#pragma unroll
+      for (int q = 0; q < CH; ++q) nim[q] = -im[q];
       const long long r0 = 2 * r, r1 = 2 * r + 1;
-      const int kre = (int)k, kim = (int)(g.k_pad + k);
-      const size_t t0 = ((size_t)(bi * rt_count + r0 / GT_ROWS) * kt_count);
-      const size_t t1 = ((size_t)(bi * rt_count + r1 / GT_ROWS) * kt_count);
-      store_split<KIND>(hi, lo, (t0 + (size_t)(kre * esize / GT_KBYTES)) * tb + gt_offset((int)(r0 % GT_ROWS), kre, esize), v.x);
-      store_split<KIND>(hi, lo, (t0 + (size_t)(kim * esize / GT_KBYTES)) * tb + gt_offset((int)(r0 % GT_ROWS), kim, esize), -v.y);
-      store_split<KIND>(hi, lo, (t1 + (size_t)(kre * esize / GT_KBYTES)) * tb + gt_offset((int)(r1 % GT_ROWS), kre, esize), v.y);
-      store_split<KIND>(hi, lo, (t1 + (size_t)(kim * esize / GT_KBYTES)) * tb + gt_offset((int)(r1 % GT_ROWS), kim, esize), v.x);
+      const size_t t0 = (size_t)(bi * rt_count + r0 / GT_ROWS) * kt_count;
+      const size_t t1 = (size_t)(bi * rt_count + r1 / GT_ROWS) * kt_count;
+      // row 2r: [Re | -Im]
+      split16<KIND, CH>(re, &h, &l);
+      size_t off = (t0 + (size_t)(kre * ES / GT_KBYTES)) * tb + gt_offset((int)(r0 % GT_ROWS), kre, ES);
+      *reinterpret_cast<uint4*>(hi + off) = h;
+      *reinterpret_cast<uint4*>(lo + off) = l;
+      split16<KIND, CH>(nim, &h, &l);
+      off = (t0 + (size_t)(kim * ES / GT_KBYTES)) * tb + gt_offset((int)(r0 % GT_ROWS), kim, ES);
+      *reinterpret_cast<uint4*>(hi + off) = h;
+      *reinterpret_cast<uint4*>(lo + off) = l;
+      // row 2r + 1: [Im | Re]
+      split16<KIND, CH>(im, &h, &l);
+      off = (t1 + (size_t)(kre * ES / GT_KBYTES)) * tb + gt_offset((int)(r1 % GT_ROWS), kre, ES);
+      *reinterpret_cast<uint4*>(hi + off) = h;
+      *reinterpret_cast<uint4*>(lo + off) = l;
+      split16<KIND, CH>(re, &h, &l);
+      off = (t1 + (size_t)(kim * ES / GT_KBYTES)) * tb + gt_offset((int)(r1 % GT_ROWS), kim, ES);
+      *reinterpret_cast<uint4*>(hi + off) = h;
+      *reinterpret_cast<uint4*>(lo + off) = l;
     }
   }
 }
@@ -545,7 +590,8 @@ void gemm_bucket_launch(const GemmBucketArgs& g, const GemmEpilogue& ep, int* st
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int esize = g.kind == GEMM_BF16 ? 2 : 4;
   const long long batch = (long long)g.items << g.ns;
-  const long long na = batch * g.m_pad * g.k_pad, nb = batch * g.n_pad * g.k_pad;
+  const int ch = 16 / esize;  // K values per thread of k_gemm_pack
+  const long long na = batch * g.m_pad * (g.k_pad / ch), nb = batch * g.n_pad * (g.k_pad / ch);
   const int blocks_a = (int)std::min<long long>((na + 255) / 256, 152 * 16);
   const int blocks_b = (int)std::min<long long>((nb + 255) / 256, 152 * 16);
   if (g.kind == GEMM_BF16) {
