@@ -253,6 +253,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--precision", default="c64", choices=["c64", "bf16x3", "tf32x3"],
                     help="merged GEMM-shaped buckets on tensor cores in split precision")
+    ap.add_argument("--gemm-min-k", type=int, default=4,
+                    help="split precision: chains summing >= 2^this values run as GEMMs")
     ap.add_argument("--plain", action="store_true",
                     help="plain complex64 per-slice form: one kernel per bucket, no fusion or leaf absorption, "
                          "one slice per launch (a comparison line, not the headline)")
@@ -286,7 +288,8 @@ def main():
         args.precision, prec, args.max_batch, args.no_autotune = "c64", 0, 1, True
         plan = tnq.Plan(circ, max_bag_log2=mb, min_p=pmin, max_p=pmax, fuse_min_rank=0, leaf_absorb=0)
     else:
-        plan = tnq.Plan(circ, max_bag_log2=mb, min_p=pmin, max_p=pmax, precision=prec, gemm_min_k_log2=4)
+        plan = tnq.Plan(circ, max_bag_log2=mb, min_p=pmin, max_p=pmax, precision=prec,
+                        gemm_min_k_log2=args.gemm_min_k)
     t_plan = time.perf_counter() - t_plan
     n_sl = plan.info()["n_slices"]
     stream = torch.cuda.current_stream()
