@@ -1075,23 +1075,6 @@ static GParams group_gparams(const tnq_plan& P, const Layout& L, const FusedGrou
   if (last.size() + g.tile_vars.size() != o.vars.size()) return G;
   *smem = GROUP_SMEM_BYTES;
   (void)maxbits;
-  if (getenv("TNQ_DEBUG_GROUPS")) {
-    fprintf(stderr, "group out rank %d tile bits %d ext %d\n", o.rank(), G.n_h, G.n_gin);
-    for (int s2 = 0; s2 < G.n_st; ++s2) {
-      fprintf(stderr, "  stage %d nbits %d:", s2, G.st[s2].nbits);
-      for (int j = 0; j < G.st[s2].n_in; ++j) {
-        const int src = G.st[s2].src[j];
-        fprintf(stderr, " [%s r%d u%d c:", src < 0 ? "chain" : "in", src < 0 ? -1 : prog.tensors[g.ext_inputs[src]].rank(),
-                G.st[s2].ustride[j]);
-        for (int b2 = 0; b2 < G.st[s2].nbits; ++b2) fprintf(stderr, "%d,", G.st[s2].cstride[j][b2]);
-        fprintf(stderr, "]");
-      }
-      fprintf(stderr, "\n");
-    }
-    fprintf(stderr, "  out c:");
-    for (int b2 = 0; b2 < G.st[G.n_st - 1].nbits; ++b2) fprintf(stderr, "%d,", G.out_cstride[b2]);
-    fprintf(stderr, "\n");
-  }
   *ok = true;
   return G;
 }
