@@ -97,8 +97,16 @@ class ClockSampler:
 # DRAM bytes (read + write) of the largest fused-chain launch per slice, from
 # the ncu capture in profiles/k_group_7x7_d1+32+1.md, valid only for the
 # kernel source it was taken from (reported as null once runtime.cu changes).
-MEASURED_TRAFFIC = {"k_group": {"source_sha1": "3fd6ece8901074bd9f6dfb360ae02ebd21a65871", "bytes_per_slice": 76.627712e6 + 30.664448e6,
-                                "launch": "largest k_group launch (5-bucket chain, bags 28 -> 24)"}}
+# ncu DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of every
+# k_group launch of a one-slice batch of this workload (no autotune: all 17
+# fused chains), valid for the runtime.cu with this SHA-1. Per launch at batch
+# B: bytes_one_slice x B / k_group launches per batch (traffic scales with the
+# slices of a batch; item-invariant operands are read once per batch, so this
+# slightly overstates it).
+MEASURED_TRAFFIC = {"k_group": {"source_sha1": "28d8678cdaf832624e7b78f1344d0ffd85001158",
+                                "bytes_one_slice": 199153408.0, "launches": 17,
+                                "capture": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:k_group "
+                                           "-c 17 on a one-slice batch"}}
 
 
 def runtime_source_sha1():
@@ -175,9 +183,9 @@ def launch_roofline(L, plan, bits, ws, B, n_sl, stream, peaks, info):
         out["largest_launch"] = {"ms": ms[big], "flops": fl[big], "algorithmic_bytes": by[big],
                                  "achieved_tflops": fl[big] / (ms[big] / 1e3) / 1e12 if ms[big] > 0 else None}
         mt = MEASURED_TRAFFIC["k_group"]
-        if mt["source_sha1"] == runtime_source_sha1():
-            out["traffic"] = mt["bytes_per_slice"] * b_out.value
-            out["traffic_launch"] = mt["launch"] + ", ncu dram bytes scaled by the batch"
+        if mt["source_sha1"] == runtime_source_sha1() and mt["bytes_one_slice"] > 0:
+            out["traffic"] = mt["bytes_one_slice"] * b_out.value / len(grp)
+            out["traffic_source"] = mt["capture"] + ", x batch / k_group launches per batch"
     out["peak_source"] = dom.get("peak_source", "measured (MEASURED_PEAKS.json hbm_gbs)")
     out["batch"] = b_out.value
     out["other_kernel"] = other
