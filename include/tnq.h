@@ -79,7 +79,8 @@ typedef enum {
   TNQ_SLICER_TREE_TRIMMING = 0, /* Section III.B score (default) */
   TNQ_SLICER_DEGREE = 1,        /* largest degree (Section III.A) */
   TNQ_SLICER_DIRECT = 2,        /* direct treewidth reduction (Algorithm 3) */
-  TNQ_SLICER_LEARNED = 3        /* learned proposer, tree-trimming fallback */
+  TNQ_SLICER_LEARNED = 3,       /* learned proposer, tree-trimming fallback */
+  TNQ_SLICER_BETWEENNESS = 4    /* largest betweenness centrality (Section III.A) */
 } tnq_slicer;
 
 typedef enum {
@@ -297,12 +298,29 @@ tnq_status tnq_graph_tree_decomposition(int32_t n, size_t n_edges, const int32_t
                                         int32_t* bag_vertices, int32_t* parent);
 
 /* Algorithm 2: delete m vertices greedily by the score `slicer` (tree-trimming,
- * degree or direct). out_mu[j] = j-th deleted vertex; out_tau[j] = treewidth
- * of the reduced order after j+1 deletions (Algorithm 1). */
+ * degree, direct, learned or betweenness; the degree, direct and betweenness
+ * scores are recomputed on the reduced graph at every step). out_mu[j] = j-th
+ * deleted vertex; out_tau[j] = treewidth of the reduced order after j+1
+ * deletions (Algorithm 1). */
 tnq_status tnq_graph_greedy_deletion(int32_t n, size_t n_edges, const int32_t* edges,
                                      const int32_t* order, int32_t m, int32_t slicer,
                                      uint64_t seed, int32_t td_rebuild,
                                      int32_t* out_mu, int32_t* out_tau);
+
+/* The free-variable graph of a circuit (Section II.A: vertices are the free
+ * wire variables after the input and output wires are fixed, edges join
+ * variables that share a gate tensor) -- the graph the planner orders and
+ * slices. *out_n = vertices, *out_n_edges = edges (a < b, each once) written
+ * as pairs to edges[2e], edges[2e+1] when cap >= *out_n_edges; TNQ_EINVAL
+ * (with the count set) if cap is short or the circuit is invalid. */
+tnq_status tnq_circuit_graph(int32_t n_qubits, const tnq_gate* gates, size_t n_gates, size_t cap,
+                             int32_t* out_n, size_t* out_n_edges, int32_t* edges);
+
+/* Betweenness centrality (Section III.A, the score of TNQ_SLICER_BETWEENNESS):
+ * out_scores[v] = sum over unordered pairs {s, t}, s != v != t, of the
+ * fraction of shortest s-t paths that pass through v (Brandes' algorithm,
+ * O(n m)); n doubles, caller-owned. TNQ_EINVAL on a bad edge list. */
+tnq_status tnq_graph_betweenness(int32_t n, size_t n_edges, const int32_t* edges, double* out_scores);
 
 #ifdef __cplusplus
 }

@@ -72,7 +72,7 @@ tnq_status tnq_plan_from_circuit(int32_t n_qubits, const tnq_gate* gates, size_t
   tnq_plan_opts o;
   tnq_plan_opts_default(&o);
   if (opts) o = *opts;
-  if (o.slicer < 0 || o.slicer > TNQ_SLICER_LEARNED || o.min_p < 0 || o.max_p < o.min_p ||
+  if (o.slicer < 0 || o.slicer > TNQ_SLICER_BETWEENNESS || o.min_p < 0 || o.max_p < o.min_p ||
       o.max_p > 62 || o.max_bag_log2 < 0 || o.max_bag_log2 > 40 || o.precision < 0 ||
       o.precision > TNQ_PREC_SPLIT_TF32 || o.ordering < 0 || o.ordering > TNQ_ORDER_MIN_DEGREE ||
       o.fuse_min_rank < 0 || o.fuse_min_rank > 40 || o.leaf_absorb < 0 || o.leaf_absorb > 1) {
@@ -266,7 +266,7 @@ tnq_status tnq_graph_tree_decomposition(int32_t n, size_t n_edges, const int32_t
 tnq_status tnq_graph_greedy_deletion(int32_t n, size_t n_edges, const int32_t* edges, const int32_t* order,
                                      int32_t m, int32_t slicer, uint64_t seed, int32_t td_rebuild,
                                      int32_t* out_mu, int32_t* out_tau) {
-  if (m < 0 || m > n || (m && (!out_mu || !out_tau)) || slicer < 0 || slicer > TNQ_SLICER_LEARNED) {
+  if (m < 0 || m > n || (m && (!out_mu || !out_tau)) || slicer < 0 || slicer > TNQ_SLICER_BETWEENNESS) {
     set_error("bad arguments");
     return TNQ_EINVAL;
   }
@@ -280,6 +280,51 @@ tnq_status tnq_graph_greedy_deletion(int32_t n, size_t n_edges, const int32_t* e
       out_mu[j] = R.mu[j];
       out_tau[j] = R.tau_after[j];
     }
+    return TNQ_OK;
+  })
+}
+
+tnq_status tnq_circuit_graph(int32_t n_qubits, const tnq_gate* gates, size_t n_gates, size_t cap,
+                             int32_t* out_n, size_t* out_n_edges, int32_t* edges) {
+  if ((!gates && n_gates) || !out_n || !out_n_edges) { set_error("NULL argument"); return TNQ_EINVAL; }
+  TNQ_TRY({
+    std::vector<GateIn> gi(n_gates);
+    for (size_t i = 0; i < n_gates; ++i) {
+      gi[i].kind = gates[i].kind;
+      gi[i].q0 = gates[i].q0;
+      gi[i].q1 = gates[i].q1;
+      std::memcpy(gi[i].m, gates[i].m, sizeof(gi[i].m));
+    }
+    Network net;
+    std::string err = build_network(n_qubits, gi.data(), n_gates, net);
+    if (!err.empty()) { set_error(err); return TNQ_EINVAL; }
+    const Graph g = network_graph(net);
+    size_t ne = 0;
+    for (int a = 0; a < g.n; ++a)
+      for (int b = a + 1; b < g.n; ++b)
+        if (g.has(a, b)) {
+          if (ne < cap && edges) {
+            edges[2 * ne] = a;
+            edges[2 * ne + 1] = b;
+          }
+          ++ne;
+        }
+    *out_n = g.n;
+    *out_n_edges = ne;
+    if (ne > cap) { set_error("edge capacity too small"); return TNQ_EINVAL; }
+    return TNQ_OK;
+  })
+}
+
+tnq_status tnq_graph_betweenness(int32_t n, size_t n_edges, const int32_t* edges, double* out_scores) {
+  if (!out_scores) { set_error("out_scores is NULL"); return TNQ_EINVAL; }
+  TNQ_TRY({
+    Graph g;
+    if (!read_graph(n, n_edges, edges, g)) return TNQ_EINVAL;
+    std::vector<int> all(n);
+    for (int v = 0; v < n; ++v) all[v] = v;
+    const std::vector<double> cb = betweenness(g, all);
+    std::copy(cb.begin(), cb.end(), out_scores);
     return TNQ_OK;
   })
 }

@@ -298,6 +298,63 @@ int score_degree(const Graph& g, const std::vector<int>& order, const std::vecto
   return break_tie(ties, pos, rng);
 }
 
+std::vector<double> betweenness(const Graph& g, const std::vector<int>& verts) {
+  // Brandes' algorithm (J. Math. Sociol. 25, 2001) for an unweighted graph:
+  // per source s one BFS counts the shortest paths sigma[v]; walking the BFS
+  // order backwards accumulates the dependency
+  //   delta[v] = sum over successors w of sigma[v] / sigma[w] * (1 + delta[w]),
+  // and CB[w] += delta[w] for w != s. Every unordered pair is met from both
+  // ends, hence the final halving.
+  const int n = g.n;
+  std::vector<std::vector<int>> adj(n);
+  for (int v : verts)
+    for (int w : verts)
+      if (w != v && g.has(v, w)) adj[v].push_back(w);
+  std::vector<double> cb(n, 0.0), sigma(n, 0.0), delta(n, 0.0);
+  std::vector<int> dist(n, -1), bfs;
+  bfs.reserve(verts.size());
+  for (int s : verts) {
+    for (int v : verts) {
+      sigma[v] = 0.0;
+      delta[v] = 0.0;
+      dist[v] = -1;
+    }
+    bfs.clear();
+    sigma[s] = 1.0;
+    dist[s] = 0;
+    bfs.push_back(s);
+    for (size_t head = 0; head < bfs.size(); ++head) {
+      const int v = bfs[head];
+      for (int w : adj[v]) {
+        if (dist[w] < 0) {
+          dist[w] = dist[v] + 1;
+          bfs.push_back(w);
+        }
+        if (dist[w] == dist[v] + 1) sigma[w] += sigma[v];
+      }
+    }
+    for (size_t i = bfs.size(); i-- > 0;) {
+      const int w = bfs[i];
+      for (int v : adj[w])
+        if (dist[v] == dist[w] - 1) delta[v] += sigma[v] / sigma[w] * (1.0 + delta[w]);
+      if (w != s) cb[w] += delta[w];
+    }
+  }
+  for (double& c : cb) c *= 0.5;
+  return cb;
+}
+
+int score_betweenness(const Graph& g, const std::vector<int>& order, const std::vector<int>& pos,
+                      uint64_t* rng) {
+  const std::vector<double> cb = betweenness(g, order);
+  double best = -1.0;
+  for (int v : order) best = std::max(best, cb[v]);
+  std::vector<int> ties;  // equal up to the rounding of the accumulated fractions
+  for (int v : order)
+    if (cb[v] >= best - 1e-9 * std::max(1.0, best)) ties.push_back(v);
+  return break_tie(ties, pos, rng);
+}
+
 int score_direct(const Graph& g, const std::vector<int>& order, const std::vector<int>& pos,
                  uint64_t* rng) {
   // Algorithm 3 (read with u deleted in the trial and the best gain kept):
@@ -348,6 +405,7 @@ DeletionResult greedy_deletion(const Graph& g0, const std::vector<int>& order0, 
     switch (slicer) {
       case SLICER_DEGREE: u = score_degree(g, order, pos, rng); break;
       case SLICER_DIRECT: u = score_direct(g, order, pos, rng); break;
+      case SLICER_BETWEENNESS: u = score_betweenness(g, order, pos, rng); break;
       case SLICER_LEARNED:
         if (proposer) u = proposer(proposer_ctx, g, order, td, p);
         if (u < 0 || u >= g.n || pos[u] < 0) u = score_tree_trimming(td, pos, rng);  // fallback

@@ -32,7 +32,8 @@ struct TreeDecomposition {
 };
 
 enum OrderMethod { ORDER_MIN_FILL = 0, ORDER_MIN_DEGREE = 1 };
-enum Slicer { SLICER_TREE_TRIMMING = 0, SLICER_DEGREE = 1, SLICER_DIRECT = 2, SLICER_LEARNED = 3 };
+enum Slicer { SLICER_TREE_TRIMMING = 0, SLICER_DEGREE = 1, SLICER_DIRECT = 2, SLICER_LEARNED = 3,
+              SLICER_BETWEENNESS = 4 };
 
 // Greedy elimination order; `alive` (may be empty) restricts to a vertex subset.
 std::vector<int> greedy_order(const Graph& g, int method);
@@ -54,7 +55,8 @@ TreeDecomposition tree_decomposition(const Graph& g, const std::vector<int>& ord
 // tree neighbour (the TD stays valid for the graph without v).
 void td_remove_vertex(TreeDecomposition& td, int v);
 
-// Score functions of Algorithm 2; each returns the vertex to delete.
+// Score functions of Algorithm 2; each returns the vertex to delete (degree,
+// direct and betweenness are recomputed on the reduced graph at every step).
 // `pos[v]` = position of v in the current order (-1 if deleted); ties go to the
 // earliest position, or to a seeded random choice when rng_state != nullptr.
 int score_tree_trimming(const TreeDecomposition& td, const std::vector<int>& pos, uint64_t* rng_state);
@@ -62,6 +64,12 @@ int score_degree(const Graph& g, const std::vector<int>& order, const std::vecto
                  uint64_t* rng_state);
 int score_direct(const Graph& g, const std::vector<int>& order, const std::vector<int>& pos,
                  uint64_t* rng_state);
+// Betweenness centrality (Section III.A): the number of shortest paths between
+// pairs of the listed vertices that pass through each vertex (Brandes'
+// algorithm; a pair with several shortest paths counts fractionally).
+std::vector<double> betweenness(const Graph& g, const std::vector<int>& verts);
+int score_betweenness(const Graph& g, const std::vector<int>& order, const std::vector<int>& pos,
+                      uint64_t* rng_state);
 
 // Tree-trimming candidates with their (length, weight) as the learned proposer's features.
 struct TrimCandidate {

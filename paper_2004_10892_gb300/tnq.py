@@ -17,7 +17,7 @@ LIB_PATH = os.environ.get("TNQ_LIB", os.path.join(_HERE, "_build", "libtnq.so"))
 _lib = None
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = range(6)
-SLICER_TREE_TRIMMING, SLICER_DEGREE, SLICER_DIRECT, SLICER_LEARNED = range(4)
+SLICER_TREE_TRIMMING, SLICER_DEGREE, SLICER_DIRECT, SLICER_LEARNED, SLICER_BETWEENNESS = range(5)
 PREC_C64, PREC_SPLIT_BF16, PREC_SPLIT_TF32 = range(3)
 ORDER_MIN_FILL, ORDER_MIN_DEGREE = range(2)
 
@@ -93,6 +93,8 @@ SIGNATURES = {
                                                     ctypes.c_int32, _i32p, _i32p, _i32p, _i32p]),
     "tnq_graph_greedy_deletion": (ctypes.c_int, [ctypes.c_int32, ctypes.c_size_t, _i32p, _i32p, ctypes.c_int32,
                                                  ctypes.c_int32, ctypes.c_uint64, ctypes.c_int32, _i32p, _i32p]),
+    "tnq_graph_betweenness": (ctypes.c_int, [ctypes.c_int32, ctypes.c_size_t, _i32p, _f64p]),
+    "tnq_circuit_graph": (ctypes.c_int, [ctypes.c_int32, _P(Gate), ctypes.c_size_t, ctypes.c_size_t, _i32p, _szp, _i32p]),
 }
 
 
@@ -351,3 +353,26 @@ def graph_greedy_deletion(n, edges, order, m, slicer=SLICER_TREE_TRIMMING, seed=
     _check(lib().tnq_graph_greedy_deletion(n, ne, _ptr(e, ctypes.c_int32), _ptr(o, ctypes.c_int32), m, slicer, seed,
                                            int(td_rebuild), _ptr(mu, ctypes.c_int32), _ptr(tau, ctypes.c_int32)))
     return [int(x) for x in mu[:m]], [int(x) for x in tau[:m]]
+
+
+def graph_betweenness(n, edges):
+    """Betweenness centrality of every vertex (tnq_graph_betweenness)."""
+    e, ne = _edges_array(edges)
+    out = np.zeros(max(n, 1), np.float64)
+    _check(lib().tnq_graph_betweenness(n, ne, _ptr(e, ctypes.c_int32), _ptr(out, ctypes.c_double)))
+    return out[:n]
+
+
+def circuit_graph(circ):
+    """(n_vertices, edges) of the circuit's free-variable graph (tnq_circuit_graph)."""
+    arr = gates_array(circ)
+    n = ctypes.c_int32()
+    ne = ctypes.c_size_t()
+    L = lib()
+    rc = L.tnq_circuit_graph(circ.n_qubits, arr, len(circ.gates), 0, ctypes.byref(n), ctypes.byref(ne), None)
+    if rc != OK and ne.value == 0:
+        _check(rc)
+    e = np.zeros(2 * max(ne.value, 1), np.int32)
+    _check(L.tnq_circuit_graph(circ.n_qubits, arr, len(circ.gates), ne.value, ctypes.byref(n), ctypes.byref(ne),
+                               _ptr(e, ctypes.c_int32)))
+    return n.value, e[:2 * ne.value].reshape(-1, 2)

@@ -277,3 +277,64 @@ def test_leaf_absorption_moves_multiplies_to_smaller_buckets(tnq_lib):
         for plan, rows in ((off, r0), (on, r1)):
             flops = sum(6.0 * (k - 1) * 2.0 ** r + (2.0 ** r if sm else 0.0) for r, k, _, sm in rows)
             assert plan.info()["flops_per_slice"] == flops
+
+
+def test_betweenness_closed_forms(tnq_lib):
+    """Betweenness centrality (Section III.A) on graphs with known values:
+    path P_n: vertex i lies on i (n-1-i) shortest paths; star: the centre on
+    all C(n-1, 2); cycle C_5: each vertex on one path (between its two
+    neighbours); complete graph: 0; 4-cycle: each vertex carries half of the
+    two shortest paths between its neighbours."""
+    n = 9
+    path = [(i, i + 1) for i in range(n - 1)]
+    assert np.allclose(tnq_lib.graph_betweenness(n, path), [i * (n - 1 - i) for i in range(n)])
+    star = [(0, i) for i in range(1, n)]
+    assert np.allclose(tnq_lib.graph_betweenness(n, star), [(n - 1) * (n - 2) / 2] + [0] * (n - 1))
+    c5 = [(i, (i + 1) % 5) for i in range(5)]
+    assert np.allclose(tnq_lib.graph_betweenness(5, c5), [1.0] * 5)
+    k5 = list(itertools.combinations(range(5), 2))
+    assert np.allclose(tnq_lib.graph_betweenness(5, k5), [0.0] * 5)
+    c4 = [(i, (i + 1) % 4) for i in range(4)]
+    assert np.allclose(tnq_lib.graph_betweenness(4, c4), [0.5] * 4)
+
+
+def test_betweenness_matches_networkx(tnq_lib):
+    nx = pytest.importorskip("networkx")
+    rng = np.random.default_rng(3)
+    for trial in range(6):
+        n = int(rng.integers(5, 40))
+        G = nx.gnm_random_graph(n, int(rng.integers(n, 3 * n)), seed=int(rng.integers(1 << 30)))
+        ref = nx.betweenness_centrality(G, normalized=False)
+        got = tnq_lib.graph_betweenness(n, list(G.edges()))
+        assert np.allclose(got, [ref[v] for v in range(n)], rtol=1e-12, atol=1e-9), trial
+
+
+def test_betweenness_slicer(tnq_lib):
+    """Algorithm 2 with the betweenness score: on a path the first deletion is
+    the middle vertex; on a circuit graph it lowers the treewidth like the
+    other scores, and the plan option runs end to end."""
+    n = 9
+    path = [(i, i + 1) for i in range(n - 1)]
+    mu, tau = tnq_lib.graph_greedy_deletion(n, path, list(range(n)), 1, slicer=tnq_lib.SLICER_BETWEENNESS)
+    assert mu == [4] and tau == [1]
+    circ = I.random_grid_circuit(5, 5, 20, 0)
+    base = tnq_lib.Plan(circ)
+    plan = tnq_lib.Plan(circ, slicer=tnq_lib.SLICER_BETWEENNESS, min_p=6, max_p=6)
+    assert plan.info()["p"] == 6 and plan.info()["tau"] < base.info()["tau"]
+
+
+def test_score_comparison_experiment(tnq_lib):
+    """The Section IV score comparison on a small circuit: every score's
+    treewidth of the fixed reduced order is non-increasing over the deletions
+    (it may drop by more than one: the order is not re-optimised), the
+    recorded deletions are distinct, and after ten deletions tree-trimming is
+    at least as good as degree (the paper's ordering of the two scores)."""
+    from paper_2004_10892_gb300 import score_compare
+
+    row = score_compare.compare(I.random_grid_circuit(6, 6, 24, 0), 10, list(score_compare.SCORES))
+    assert row["vertices"] > 0 and row["tau0"] > 0
+    for name, r in row["scores"].items():
+        tau = [row["tau0"]] + r["tau"]
+        assert len(r["mu"]) == 10 and len(set(r["mu"])) == 10, name
+        assert all(a >= b for a, b in zip(tau, tau[1:])), (name, tau)
+    assert row["scores"]["tree_trimming"]["tau"][-1] <= row["scores"]["degree"]["tau"][-1]
