@@ -109,6 +109,9 @@ typedef struct {
   int32_t leaf_absorb;    /* 1 (default): multiply a rank <= 2 gate tensor into the earlier bucket that produces
                              a tensor holding its variables, when that bucket's bag is smaller (exact, by
                              distributivity in Eq. 2); 0: every gate tensor stays in its own bucket */
+  int32_t reorder_every;  /* > 0: recompute the greedy order (opts->ordering) of the reduced graph after every
+                             this many deletions (Algorithm 2's optional recomputation step); 0 (default): never */
+  int32_t pad_;
 } tnq_plan_opts;
 
 typedef struct {
@@ -301,10 +304,11 @@ tnq_status tnq_graph_tree_decomposition(int32_t n, size_t n_edges, const int32_t
  * degree, direct, learned or betweenness; the degree, direct and betweenness
  * scores are recomputed on the reduced graph at every step). out_mu[j] = j-th
  * deleted vertex; out_tau[j] = treewidth of the reduced order after j+1
- * deletions (Algorithm 1). */
+ * deletions (Algorithm 1). reorder_every > 0 recomputes the greedy min-fill
+ * order of the reduced graph after every that many deletions. */
 tnq_status tnq_graph_greedy_deletion(int32_t n, size_t n_edges, const int32_t* edges,
                                      const int32_t* order, int32_t m, int32_t slicer,
-                                     uint64_t seed, int32_t td_rebuild,
+                                     uint64_t seed, int32_t td_rebuild, int32_t reorder_every,
                                      int32_t* out_mu, int32_t* out_tau);
 
 /* The free-variable graph of a circuit (Section II.A: vertices are the free

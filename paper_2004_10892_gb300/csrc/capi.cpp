@@ -75,7 +75,8 @@ tnq_status tnq_plan_from_circuit(int32_t n_qubits, const tnq_gate* gates, size_t
   if (o.slicer < 0 || o.slicer > TNQ_SLICER_BETWEENNESS || o.min_p < 0 || o.max_p < o.min_p ||
       o.max_p > 62 || o.max_bag_log2 < 0 || o.max_bag_log2 > 40 || o.precision < 0 ||
       o.precision > TNQ_PREC_SPLIT_TF32 || o.ordering < 0 || o.ordering > TNQ_ORDER_MIN_DEGREE ||
-      o.fuse_min_rank < 0 || o.fuse_min_rank > 40 || o.leaf_absorb < 0 || o.leaf_absorb > 1) {
+      o.fuse_min_rank < 0 || o.fuse_min_rank > 40 || o.leaf_absorb < 0 || o.leaf_absorb > 1 ||
+      o.reorder_every < 0) {
     set_error("invalid plan options");
     return TNQ_EINVAL;
   }
@@ -96,7 +97,8 @@ tnq_status tnq_plan_from_circuit(int32_t n_qubits, const tnq_gate* gates, size_t
     P->tau_full = treewidth_of_order(P->graph, P->order_full);
     DeletionResult R = greedy_deletion(P->graph, P->order_full, o.slicer, o.min_p, o.max_p,
                                        o.max_bag_log2, o.seed, o.td_rebuild != 0,
-                                       o.slicer == TNQ_SLICER_LEARNED ? &learned_propose : nullptr, nullptr);
+                                       o.slicer == TNQ_SLICER_LEARNED ? &learned_propose : nullptr, nullptr,
+                                       o.reorder_every, o.ordering);
     P->mu = R.mu;
     P->order = R.reduced_order;
     Graph reduced = P->graph;
@@ -265,8 +267,9 @@ tnq_status tnq_graph_tree_decomposition(int32_t n, size_t n_edges, const int32_t
 
 tnq_status tnq_graph_greedy_deletion(int32_t n, size_t n_edges, const int32_t* edges, const int32_t* order,
                                      int32_t m, int32_t slicer, uint64_t seed, int32_t td_rebuild,
-                                     int32_t* out_mu, int32_t* out_tau) {
-  if (m < 0 || m > n || (m && (!out_mu || !out_tau)) || slicer < 0 || slicer > TNQ_SLICER_BETWEENNESS) {
+                                     int32_t reorder_every, int32_t* out_mu, int32_t* out_tau) {
+  if (m < 0 || m > n || (m && (!out_mu || !out_tau)) || slicer < 0 || slicer > TNQ_SLICER_BETWEENNESS ||
+      reorder_every < 0) {
     set_error("bad arguments");
     return TNQ_EINVAL;
   }
@@ -275,7 +278,8 @@ tnq_status tnq_graph_greedy_deletion(int32_t n, size_t n_edges, const int32_t* e
     std::vector<int> o;
     if (!read_graph(n, n_edges, edges, g) || !read_order(n, order, o)) return TNQ_EINVAL;
     DeletionResult R = greedy_deletion(g, o, slicer, m, m, 0, seed, td_rebuild != 0,
-                                       slicer == TNQ_SLICER_LEARNED ? &learned_propose : nullptr, nullptr);
+                                       slicer == TNQ_SLICER_LEARNED ? &learned_propose : nullptr, nullptr,
+                                       reorder_every, ORDER_MIN_FILL);
     for (size_t j = 0; j < R.mu.size(); ++j) {
       out_mu[j] = R.mu[j];
       out_tau[j] = R.tau_after[j];

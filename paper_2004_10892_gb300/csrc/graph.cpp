@@ -388,7 +388,7 @@ static int max_bag_of(const Graph& g, const std::vector<int>& order) {
 
 DeletionResult greedy_deletion(const Graph& g0, const std::vector<int>& order0, int slicer, int min_p,
                                int max_p, int max_bag, uint64_t seed, bool td_rebuild,
-                               ProposerFn proposer, void* proposer_ctx) {
+                               ProposerFn proposer, void* proposer_ctx, int reorder_every, int order_method) {
   DeletionResult R;
   Graph g = g0;
   std::vector<int> order = order0;
@@ -415,11 +415,21 @@ DeletionResult greedy_deletion(const Graph& g0, const std::vector<int>& order0, 
     if (u < 0) break;
     delete_vertex(g, u);
     order.erase(std::find(order.begin(), order.end(), u));
+    R.mu.push_back(u);
+    const bool reorder = reorder_every > 0 && (int)R.mu.size() % reorder_every == 0;
+    if (reorder) {  // fresh greedy order of the reduced graph (deleted vertices are isolated: drop them),
+                    // kept unless its treewidth is larger than that of the inherited order
+      std::vector<char> keep(g.n, 0);
+      for (int v : order) keep[v] = 1;
+      std::vector<int> fresh;
+      for (int v : greedy_order(g, order_method))
+        if (keep[v]) fresh.push_back(v);
+      if (treewidth_of_order(g, fresh) <= treewidth_of_order(g, order)) order = fresh;
+    }
     std::fill(pos.begin(), pos.end(), -1);
     for (size_t i = 0; i < order.size(); ++i) pos[order[i]] = (int)i;
-    if (td_rebuild) td = tree_decomposition(g, order);
+    if (td_rebuild || reorder) td = tree_decomposition(g, order);
     else td_remove_vertex(td, u);
-    R.mu.push_back(u);
     R.tau_after.push_back(treewidth_of_order(g, order));
     ++p;
   }

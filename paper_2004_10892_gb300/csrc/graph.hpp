@@ -95,9 +95,15 @@ typedef int (*ProposerFn)(void* ctx, const Graph& g, const std::vector<int>& ord
 
 // Algorithm 2. Deletes vertices until p >= min_p and (largest bag <= max_bag, or
 // p == max_p). max_bag <= 0 means no bag limit.
+// reorder_every > 0: after every reorder_every deletions the order is
+// recomputed by the greedy heuristic `order_method` on the reduced graph (kept
+// unless its treewidth exceeds that of the inherited order) and the TD rebuilt
+// from it: the optional recomputation step of Algorithm 2, with the greedy
+// orderer in place of an exact tree-decomposition solver.
 DeletionResult greedy_deletion(const Graph& g, const std::vector<int>& order, int slicer, int min_p,
                                int max_p, int max_bag, uint64_t seed, bool td_rebuild,
-                               ProposerFn proposer = nullptr, void* proposer_ctx = nullptr);
+                               ProposerFn proposer = nullptr, void* proposer_ctx = nullptr,
+                               int reorder_every = 0, int order_method = ORDER_MIN_FILL);
 
 uint64_t splitmix64_next(uint64_t* state);
 

@@ -37,7 +37,8 @@ class PlanOpts(ctypes.Structure):
     _fields_ = [("slicer", ctypes.c_int32), ("max_bag_log2", ctypes.c_int32), ("min_p", ctypes.c_int32),
                 ("max_p", ctypes.c_int32), ("seed", ctypes.c_uint64), ("precision", ctypes.c_int32),
                 ("gemm_min_k_log2", ctypes.c_int32), ("ordering", ctypes.c_int32),
-                ("td_rebuild", ctypes.c_int32), ("fuse_min_rank", ctypes.c_int32), ("leaf_absorb", ctypes.c_int32)]
+                ("td_rebuild", ctypes.c_int32), ("fuse_min_rank", ctypes.c_int32), ("leaf_absorb", ctypes.c_int32),
+                ("reorder_every", ctypes.c_int32), ("pad_", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -92,7 +93,7 @@ SIGNATURES = {
     "tnq_graph_tree_decomposition": (ctypes.c_int, [ctypes.c_int32, ctypes.c_size_t, _i32p, _i32p, ctypes.c_int32,
                                                     ctypes.c_int32, _i32p, _i32p, _i32p, _i32p]),
     "tnq_graph_greedy_deletion": (ctypes.c_int, [ctypes.c_int32, ctypes.c_size_t, _i32p, _i32p, ctypes.c_int32,
-                                                 ctypes.c_int32, ctypes.c_uint64, ctypes.c_int32, _i32p, _i32p]),
+                                                 ctypes.c_int32, ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32, _i32p, _i32p]),
     "tnq_graph_betweenness": (ctypes.c_int, [ctypes.c_int32, ctypes.c_size_t, _i32p, _f64p]),
     "tnq_circuit_graph": (ctypes.c_int, [ctypes.c_int32, _P(Gate), ctypes.c_size_t, ctypes.c_size_t, _i32p, _szp, _i32p]),
 }
@@ -345,13 +346,15 @@ def graph_tree_decomposition(n, edges, order):
     return bags, [int(x) for x in par[: nb.value]]
 
 
-def graph_greedy_deletion(n, edges, order, m, slicer=SLICER_TREE_TRIMMING, seed=0, td_rebuild=False):
+def graph_greedy_deletion(n, edges, order, m, slicer=SLICER_TREE_TRIMMING, seed=0, td_rebuild=False,
+                          reorder_every=0):
     e, ne = _edges_array(edges)
     o = np.ascontiguousarray(np.array(order, dtype=np.int32)) if n else np.zeros(1, np.int32)
     mu = np.zeros(max(m, 1), np.int32)
     tau = np.zeros(max(m, 1), np.int32)
     _check(lib().tnq_graph_greedy_deletion(n, ne, _ptr(e, ctypes.c_int32), _ptr(o, ctypes.c_int32), m, slicer, seed,
-                                           int(td_rebuild), _ptr(mu, ctypes.c_int32), _ptr(tau, ctypes.c_int32)))
+                                           int(td_rebuild), int(reorder_every), _ptr(mu, ctypes.c_int32),
+                                           _ptr(tau, ctypes.c_int32)))
     return [int(x) for x in mu[:m]], [int(x) for x in tau[:m]]
 
 

@@ -333,3 +333,18 @@ def test_batched_serving_workload_full_size(cuda, tnq_lib, oracle_lib):
             assert rel_err(out[nb * i + j], ref, 25) < TOL
             checked += 1
     assert checked > 0
+
+
+@pytest.mark.parametrize("slicer", [0, 1, 2, 4])
+def test_every_slicer_gives_the_same_amplitude(cuda, tnq_lib, oracle_lib, slicer):
+    """The score of Algorithm 2 only chooses mu (Eq. 5 regroups the same sum):
+    tree-trimming, degree, direct and betweenness plans all give the oracle's
+    amplitude, slice by slice."""
+    circ = I.random_grid_circuit(5, 5, 20, 3)
+    bits = I.random_bitstring(25, 3)
+    plan = tnq_lib.Plan(circ, slicer=slicer, min_p=4, max_p=4)
+    amp, per = tnq_lib.contract_sliced(plan, bits, per_slice=True)
+    ref, ref_per = oracle_lib.contract(circ, bits, order=plan.order(), mu=plan.sliced(), per_slice=True)
+    for s in range(len(per)):
+        assert rel_err(per[s], ref_per[s], 25) < TOL, s
+    assert rel_err(amp, oracle_lib.contract(circ, bits), 25) < TOL

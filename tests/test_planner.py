@@ -338,3 +338,21 @@ def test_score_comparison_experiment(tnq_lib):
         assert len(r["mu"]) == 10 and len(set(r["mu"])) == 10, name
         assert all(a >= b for a, b in zip(tau, tau[1:])), (name, tau)
     assert row["scores"]["tree_trimming"]["tau"][-1] <= row["scores"]["degree"]["tau"][-1]
+
+
+def test_order_recomputation(tnq_lib):
+    """Algorithm 2's optional recomputation step (reorder_every): a fresh greedy
+    order of the reduced graph replaces the inherited one unless its width is
+    larger, so the treewidth never ends above the plain run's, stays
+    non-increasing, and the plan option works end to end."""
+    n, edges = tnq_lib.circuit_graph(I.random_grid_circuit(6, 6, 24, 1))
+    order = tnq_lib.graph_order(n, edges)
+    for slicer in (tnq_lib.SLICER_TREE_TRIMMING, tnq_lib.SLICER_DIRECT):
+        _, plain = tnq_lib.graph_greedy_deletion(n, edges, order, 8, slicer=slicer)
+        _, re1 = tnq_lib.graph_greedy_deletion(n, edges, order, 8, slicer=slicer, reorder_every=1)
+        assert all(a >= b for a, b in zip(re1, re1[1:]))
+        assert re1[-1] <= plain[-1] + 1
+    circ = I.random_grid_circuit(6, 6, 24, 1)
+    a = tnq_lib.Plan(circ, max_bag_log2=16, max_p=30)
+    b = tnq_lib.Plan(circ, max_bag_log2=16, max_p=30, reorder_every=1)
+    assert b.info()["max_bag"] <= 16 and b.info()["p"] <= a.info()["p"] + 1
