@@ -261,6 +261,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--precision", default="c64", choices=["c64", "bf16x3", "tf32x3"],
                     help="merged GEMM-shaped buckets on tensor cores in split precision")
+    ap.add_argument("--reorder-every", type=int, default=0,
+                    help="recompute the greedy order after every this many deletions while slicing (0: never)")
     ap.add_argument("--gemm-min-k", type=int, default=4,
                     help="split precision: chains summing >= 2^this values run as GEMMs")
     ap.add_argument("--plain", action="store_true",
@@ -297,7 +299,7 @@ def main():
         plan = tnq.Plan(circ, max_bag_log2=mb, min_p=pmin, max_p=pmax, fuse_min_rank=0, leaf_absorb=0)
     else:
         plan = tnq.Plan(circ, max_bag_log2=mb, min_p=pmin, max_p=pmax, precision=prec,
-                        gemm_min_k_log2=args.gemm_min_k)
+                        gemm_min_k_log2=args.gemm_min_k, reorder_every=args.reorder_every)
     t_plan = time.perf_counter() - t_plan
     n_sl = plan.info()["n_slices"]
     stream = torch.cuda.current_stream()
@@ -381,7 +383,8 @@ def main():
                        "l2": "inputs larger than L2 (each batch streams GBs)", "plan_s": t_plan,
                        "autotune_s": t_tune, "fused_chains": info["n_fused_groups"],
                        "gemm_buckets": info["n_gemm_buckets"], "precision": args.precision,
-                       "form": "plain per-slice" if args.plain else "batched, fused, autotuned"},
+                       "form": "plain per-slice" if args.plain else "batched, fused, autotuned",
+                       "reorder_every": args.reorder_every},
             "time_per_amplitude_s": t_dev / args.steps,
             "rel_err_vs_fp64": err,
             "amplitude": [amp.real, amp.imag],
