@@ -223,7 +223,7 @@ def run_reference(args, cfg_name):
     rows, cols, cyc, mb, pmin, pmax = CONFIGS[cfg_name]
     circ = inputs.random_grid_circuit(rows, cols, cyc, 0)
     bits = inputs.random_bitstring(circ.n_qubits, 0)
-    plan = tnq.Plan(circ, max_bag_log2=mb, min_p=pmin, max_p=pmax)
+    plan = tnq.Plan(circ, max_bag_log2=mb, min_p=pmin, max_p=pmax, reorder_every=args.reorder_every)
     order, mu = plan.order(), plan.sliced()
     n_sl = plan.info()["n_slices"]
     oracle.build()
@@ -259,15 +259,18 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-profile", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--precision", default="c64", choices=["c64", "bf16x3", "tf32x3"],
+    ap.add_argument("--precision", default="bf16x3", choices=["c64", "bf16x3", "tf32x3"],
                     help="merged GEMM-shaped buckets on tensor cores in split precision")
-    ap.add_argument("--reorder-every", type=int, default=0,
+    ap.add_argument("--reorder-every", type=int, default=1,
                     help="recompute the greedy order after every this many deletions while slicing (0: never)")
     ap.add_argument("--gemm-min-k", type=int, default=4,
                     help="split precision: chains summing >= 2^this values run as GEMMs")
     ap.add_argument("--plain", action="store_true",
                     help="plain complex64 per-slice form: one kernel per bucket, no fusion or leaf absorption, "
                          "one slice per launch (a comparison line, not the headline)")
+    ap.add_argument("--tune-file", default=None,
+                    help="JSON of the autotuner's kept chains: loaded instead of tuning if it exists, else written "
+                         "after tuning (lets a profiler run reuse the decisions of a plain run)")
     ap.add_argument("--tune-batch", type=int, default=16, help="slices per batch while autotuning")
     ap.add_argument("--tune-gb", type=int, default=48, help="workspace GiB while autotuning")
     args = ap.parse_args()
@@ -296,7 +299,8 @@ def main():
     prec = {"c64": 0, "bf16x3": 1, "tf32x3": 2}[args.precision]
     if args.plain:
         args.precision, prec, args.max_batch, args.no_autotune = "c64", 0, 1, True
-        plan = tnq.Plan(circ, max_bag_log2=mb, min_p=pmin, max_p=pmax, fuse_min_rank=0, leaf_absorb=0)
+        plan = tnq.Plan(circ, max_bag_log2=mb, min_p=pmin, max_p=pmax, fuse_min_rank=0, leaf_absorb=0,
+                        reorder_every=args.reorder_every)
     else:
         plan = tnq.Plan(circ, max_bag_log2=mb, min_p=pmin, max_p=pmax, precision=prec,
                         gemm_min_k_log2=args.gemm_min_k, reorder_every=args.reorder_every)
@@ -307,10 +311,17 @@ def main():
     # autotune (untimed, part of planning): keep each fused chain only where it measures faster
     t_tune = time.perf_counter()
     n_fused = None
-    if not args.no_autotune:
+    if args.tune_file and os.path.exists(args.tune_file) and not args.no_autotune:
+        with open(args.tune_file) as f:
+            plan.keep_chains(json.load(f)["kept_chains"])
+        n_fused = len(plan.fused_chains())
+    elif not args.no_autotune:
         tune_ws = torch.empty(args.tune_gb << 30, dtype=torch.uint8, device="cuda")
         n_fused = plan.autotune(bits, workspace=tune_ws, max_batch=min(args.tune_batch, n_sl), stream=stream)
         del tune_ws
+        if args.tune_file and rank == 0:
+            with open(args.tune_file, "w") as f:
+                json.dump({"kept_chains": plan.fused_chains()}, f)
     t_tune = time.perf_counter() - t_tune
     info = plan.info()
     B = min(args.max_batch, n_sl)

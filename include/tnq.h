@@ -203,6 +203,20 @@ tnq_status tnq_contract_sliced(const tnq_plan* plan, const uint8_t* bits,
 tnq_status tnq_plan_autotune(tnq_plan* plan, const uint8_t* bits, void* workspace, size_t ws_bytes,
                              uint32_t max_batch, void* stream, int32_t* out_n_fused);
 
+/* The chains the plan runs fused (fused kernel or GEMM), each identified by the
+ * index of its last bucket in the plan's bucket program: *out_n = count, and
+ * last_bucket[0..count) when cap >= count (TNQ_EINVAL otherwise; last_bucket
+ * may be NULL to query the count). With tnq_plan_keep_chains this lets a caller
+ * store an autotuning result and apply it to a plan built later with the same
+ * circuit and options (planning is deterministic). */
+tnq_status tnq_plan_fused_chains(const tnq_plan* plan, int32_t* last_bucket, size_t cap, size_t* out_n);
+
+/* Keeps fused only the chains whose last bucket is listed; every other chain
+ * runs bucket by bucket (the results do not change: Eq. 2 either way).
+ * Indices that name no chain are ignored. Drops the plan's cached device
+ * configurations. */
+tnq_status tnq_plan_keep_chains(tnq_plan* plan, const int32_t* last_bucket, size_t n);
+
 /* tnq_amplitudes_batch: amplitudes of many bitstrings of many plans.
  * Plan i has bitstrings bits_offset[i] .. bits_offset[i+1]-1 (bits_offset has
  * n_plans+1 entries, bits_offset[0] = 0); bitstring b occupies

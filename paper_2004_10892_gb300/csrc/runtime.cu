@@ -354,20 +354,14 @@ struct GParams {
 // per entry only the NV varying operands are loaded (one 16-byte load each:
 // the eliminated variable is bit 0 of every operand), and the last operand's
 // multiply is fused with the sum over u.
-template <int NV, bool K, int NHI = 0>
+template <int NV, bool K>
 __device__ __forceinline__ void group_stage(const GSt& S, int t, const float2* prev, float2* cur, float2* out,
-                                            bool last, const float2* const* s_ptr, const float* s_scale,
-                                            const int (*tab)[48], const int* s_out_hi, long long out_base, int out_lo,
-                                            float* tmax) {
+                                            bool last, const float2* const* s_ptr, float F, const int (*tab)[48],
+                                            const int* s_out_hi, long long out_base, int out_lo, float* tmax) {
   static_assert(K || NV > 0, "a stage without constant inputs has a varying operand");
-  // NHI > 0: the stage has exactly 2^(8 + log2 NHI) local entries (the caller
-  // checked nbits), so the entry loop is unrolled completely and unguarded
   const int nb = S.nbits;
-  const int n_hi = NHI > 0 ? NHI : (nb > 8 ? (1 << (nb - 8)) : 1);
-  const int nent = NHI > 0 ? (NHI << 8) : (1 << nb);
-  float F = 1.f;
-  for (int j = 0; j < S.n_in; ++j)
-    if (S.src[j] >= 0) F *= s_scale[S.src[j]];
+  const int n_hi = nb > 8 ? (1 << (nb - 8)) : 1;
+  const int nent = 1 << nb;
   float2 k0 = make_float2(F, 0.f), k1 = make_float2(F, 0.f);
   if (K) {
     for (int j = NV; j < S.n_in; ++j) {
@@ -385,10 +379,10 @@ __device__ __forceinline__ void group_stage(const GSt& S, int t, const float2* p
     ptr[j] = src < 0 ? prev : s_ptr[src];
     lo[j] = tab[j][t & 15] + tab[j][16 + ((t >> 4) & 15)];
   }
-#pragma unroll (NHI > 0 ? NHI : 2)
+#pragma unroll 2
   for (int it = 0; it < n_hi; ++it) {
     const int c = t + (it << 8);
-    if (NHI > 0 || c < nent) {
+    if (c < nent) {
       float2 p0 = k0, p1 = k1;
       constexpr int J0 = K ? 0 : 1;
       if (!K) {
@@ -437,14 +431,10 @@ __device__ __forceinline__ void group_stage(const GSt& S, int t, const float2* p
 // this kernel). K as in group_stage.
 template <int NV, bool K, int NHI>
 __device__ __forceinline__ void stage_pf(const GSt& S, int t, const float2* prev, float2* cur, float2* out,
-                                         bool last, const float2* const* s_ptr, const float* s_scale,
-                                         const int (*tab)[48], const int* s_out_hi, long long out_base, int out_lo,
-                                         float* tmax) {
+                                         bool last, const float2* const* s_ptr, float F, const int (*tab)[48],
+                                         const int* s_out_hi, long long out_base, int out_lo, float* tmax) {
   static_assert(NV >= 1 && NV <= 3, "one to three varying operands");
   constexpr int PF = NHI < 2 ? NHI : 2;
-  float F = 1.f;
-  for (int j = 0; j < S.n_in; ++j)
-    if (S.src[j] >= 0) F *= s_scale[S.src[j]];
   float2 k0 = make_float2(F, 0.f), k1 = make_float2(F, 0.f);
   if (K) {
     for (int j = NV; j < S.n_in; ++j) {
@@ -463,14 +453,18 @@ __device__ __forceinline__ void stage_pf(const GSt& S, int t, const float2* prev
   for (int i = 0; i < PF; ++i)
 #pragma unroll
     for (int j = 0; j < NV; ++j) v[i][j] = *reinterpret_cast<const float4*>(pj[j] + tab[j][32 + i]);
+  constexpr int U = NHI < 4 ? NHI : 4;  // entries per unrolled step (a multiple of PF)
+#pragma unroll 1
+  for (int it0 = 0; it0 < NHI; it0 += U)
 #pragma unroll
-  for (int it = 0; it < NHI; ++it) {
+  for (int u = 0; u < U; ++u) {
+    const int it = it0 + u;
     float4 cv[NV];
 #pragma unroll
-    for (int j = 0; j < NV; ++j) cv[j] = v[it % PF][j];
+    for (int j = 0; j < NV; ++j) cv[j] = v[u % PF][j];
     if (it + PF < NHI) {
 #pragma unroll
-      for (int j = 0; j < NV; ++j) v[it % PF][j] = *reinterpret_cast<const float4*>(pj[j] + tab[j][32 + it + PF]);
+      for (int j = 0; j < NV; ++j) v[u % PF][j] = *reinterpret_cast<const float4*>(pj[j] + tab[j][32 + it + PF]);
     }
     float2 p0 = k0, p1 = k1;
     if (!K) {
@@ -513,10 +507,9 @@ __device__ __forceinline__ void stage_pf(const GSt& S, int t, const float2* prev
 // Dispatch of stage_pf over (NV, K, NHI); false if the stage has another shape.
 template <int NV, bool K>
 __device__ __forceinline__ bool stage_pf_nhi(const GSt& S, int t, const float2* prev, float2* cur, float2* out,
-                                             bool last, const float2* const* s_ptr, const float* s_scale,
-                                             const int (*tab)[48], const int* s_out_hi, long long out_base,
-                                             int out_lo, float* tmax) {
-#define TNQ_PF(n) stage_pf<NV, K, n>(S, t, prev, cur, out, last, s_ptr, s_scale, tab, s_out_hi, out_base, out_lo, tmax)
+                                             bool last, const float2* const* s_ptr, float F, const int (*tab)[48],
+                                             const int* s_out_hi, long long out_base, int out_lo, float* tmax) {
+#define TNQ_PF(n) stage_pf<NV, K, n>(S, t, prev, cur, out, last, s_ptr, F, tab, s_out_hi, out_base, out_lo, tmax)
   switch (S.nbits) {
     case 12: TNQ_PF(16); return true;
     case 11: TNQ_PF(8); return true;
@@ -532,14 +525,14 @@ __device__ __forceinline__ bool stage_pf_nhi(const GSt& S, int t, const float2* 
 
 template <int NV>
 __device__ __forceinline__ void run_stage(bool with_k, const GSt& S, int t, const float2* prev, float2* cur,
-                                          float2* out, bool last, const float2* const* s_ptr, const float* s_scale,
+                                          float2* out, bool last, const float2* const* s_ptr, float F,
                                           const int (*tab)[48], const int* s_out_hi, long long out_base, int out_lo,
                                           float* tmax) {
   if (NV == 0 || with_k)
-    group_stage<NV, true>(S, t, prev, cur, out, last, s_ptr, s_scale, tab, s_out_hi, out_base, out_lo, tmax);
+    group_stage<NV, true>(S, t, prev, cur, out, last, s_ptr, F, tab, s_out_hi, out_base, out_lo, tmax);
   else
-    group_stage<(NV > 0 ? NV : 1), false>(S, t, prev, cur, out, last, s_ptr, s_scale, tab, s_out_hi, out_base,
-                                          out_lo, tmax);
+    group_stage<(NV > 0 ? NV : 1), false>(S, t, prev, cur, out, last, s_ptr, F, tab, s_out_hi, out_base, out_lo,
+                                          tmax);
 }
 
 // Persistent fused-group kernel: every block builds the stage tables once,
@@ -548,7 +541,7 @@ __global__ void __launch_bounds__(TPB, 4) k_group(const __grid_constant__ GParam
   extern __shared__ float2 g_stage[];  // stage regions A (2^(GL_MAX-1) entries) and B (half of A)
   __shared__ int s_hstr[GIN_MAX + 1][GH_MAX];  // row GIN_MAX: the output (within-item offsets < 2^31)
   __shared__ const float2* s_ptr[GIN_MAX];
-  __shared__ float s_scale[GIN_MAX];
+  __shared__ float s_F[GM_MAX];  // per stage: product of its memory inputs' power-of-two scales
   __shared__ int s_e[GIN_MAX];
   __shared__ int s_tab[PAIR_MAX][48];
   __shared__ int s_out_hi[16];
@@ -617,14 +610,24 @@ __global__ void __launch_bounds__(TPB, 4) k_group(const __grid_constant__ GParam
         if ((h >> i) & 1ll) b += s_hstr[t][i];
       s_ptr[t] = g.ptr + b;
       if (g.meta < 0) {
-        s_scale[t] = 1.f;
         s_e[t] = 0;
       } else {
         const long long row = (long long)g.meta * P.B + (g.dep ? item : 0ll);
         int m;
-        s_scale[t] = scale_of_max(P.meta_m[row], &m);
+        scale_of_max(P.meta_m[row], &m);
         s_e[t] = P.meta_e[row] + m;
       }
+    } else if (t < P.n_gin + P.n_st) {
+      const GSt& S = P.st[t - P.n_gin];
+      float f = 1.f;
+      for (int j = 0; j < S.n_in; ++j) {
+        if (S.src[j] < 0) continue;
+        const GIn& g = P.gin[S.src[j]];
+        if (g.meta < 0) continue;
+        int m;
+        f *= scale_of_max(P.meta_m[(long long)g.meta * P.B + (g.dep ? item : 0ll)], &m);
+      }
+      s_F[t - P.n_gin] = f;
     }
     if (t == TPB - 1) {
       long long b = P.out_dep ? item * P.out_istride : 0ll;
@@ -642,13 +645,14 @@ __global__ void __launch_bounds__(TPB, 4) k_group(const __grid_constant__ GParam
       const bool last = (s == P.n_st - 1);
       const bool with_k = S.n_in > S.n_var;
       bool done = false;
-#define TNQ_PFK(n) done = with_k ? stage_pf_nhi<n, true>(S, t, prev, cur, P.out, last, s_ptr, s_scale, s_tab + S.q0, s_out_hi, s_out_base, out_lo, &tmax) \
-                                 : stage_pf_nhi<n, false>(S, t, prev, cur, P.out, last, s_ptr, s_scale, s_tab + S.q0, s_out_hi, s_out_base, out_lo, &tmax)
+      const float F = s_F[s];
+#define TNQ_PFK(n) done = with_k ? stage_pf_nhi<n, true>(S, t, prev, cur, P.out, last, s_ptr, F, s_tab + S.q0, s_out_hi, s_out_base, out_lo, &tmax) \
+                                 : stage_pf_nhi<n, false>(S, t, prev, cur, P.out, last, s_ptr, F, s_tab + S.q0, s_out_hi, s_out_base, out_lo, &tmax)
       if (S.n_var == 1) TNQ_PFK(1);
       else if (S.n_var == 2) TNQ_PFK(2);
 #undef TNQ_PFK
       if (!done) switch (S.n_var) {
-#define TNQ_STAGE(n) run_stage<n>(with_k, S, t, prev, cur, P.out, last, s_ptr, s_scale, s_tab + S.q0, s_out_hi, s_out_base, out_lo, &tmax)
+#define TNQ_STAGE(n) run_stage<n>(with_k, S, t, prev, cur, P.out, last, s_ptr, F, s_tab + S.q0, s_out_hi, s_out_base, out_lo, &tmax)
         case 0: TNQ_STAGE(0); break;
         case 1: TNQ_STAGE(1); break;
         case 2: TNQ_STAGE(2); break;
@@ -1837,6 +1841,27 @@ tnq_status tnq_plan_autotune(tnq_plan* plan, const uint8_t* bits, void* workspac
     reset_device_state(*plan);
   }
   if (out_n_fused) *out_n_fused = (int32_t)prog.groups.size();
+  return TNQ_OK;
+}
+
+tnq_status tnq_plan_fused_chains(const tnq_plan* plan, int32_t* last_bucket, size_t cap, size_t* out_n) {
+  if (!plan || !out_n) { set_error("NULL argument"); return TNQ_EINVAL; }
+  const auto& groups = plan->prog.groups;
+  *out_n = groups.size();
+  if (last_bucket)
+    for (size_t i = 0; i < groups.size() && i < cap; ++i) last_bucket[i] = groups[i].buckets.back();
+  if (last_bucket && cap < groups.size()) { set_error("capacity too small"); return TNQ_EINVAL; }
+  return TNQ_OK;
+}
+
+tnq_status tnq_plan_keep_chains(tnq_plan* plan, const int32_t* last_bucket, size_t n) {
+  if (!plan || (n && !last_bucket)) { set_error("NULL argument"); return TNQ_EINVAL; }
+  Program& prog = plan->prog;
+  std::vector<FusedGroup> keep;
+  for (const auto& g : prog.groups)
+    if (std::find(last_bucket, last_bucket + n, g.buckets.back()) != last_bucket + n) keep.push_back(g);
+  set_groups(prog, keep);
+  reset_device_state(*plan);
   return TNQ_OK;
 }
 

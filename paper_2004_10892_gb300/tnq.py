@@ -95,6 +95,8 @@ SIGNATURES = {
     "tnq_graph_greedy_deletion": (ctypes.c_int, [ctypes.c_int32, ctypes.c_size_t, _i32p, _i32p, ctypes.c_int32,
                                                  ctypes.c_int32, ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32, _i32p, _i32p]),
     "tnq_graph_betweenness": (ctypes.c_int, [ctypes.c_int32, ctypes.c_size_t, _i32p, _f64p]),
+    "tnq_plan_fused_chains": (ctypes.c_int, [_vp, _i32p, ctypes.c_size_t, _szp]),
+    "tnq_plan_keep_chains": (ctypes.c_int, [_vp, _i32p, ctypes.c_size_t]),
     "tnq_circuit_graph": (ctypes.c_int, [ctypes.c_int32, _P(Gate), ctypes.c_size_t, ctypes.c_size_t, _i32p, _szp, _i32p]),
 }
 
@@ -189,6 +191,19 @@ class Plan:
         _check(lib().tnq_plan_buckets(self.handle, _ptr(bag, ctypes.c_int32), _ptr(k, ctypes.c_int32),
                                       _ptr(gm, ctypes.c_int32)))
         return bag[:n].copy(), k[:n].copy(), gm[:n].copy()
+
+    def fused_chains(self):
+        """Last-bucket indices of the chains this plan runs fused (tnq_plan_fused_chains)."""
+        n = ctypes.c_size_t()
+        _check(lib().tnq_plan_fused_chains(self.handle, None, 0, ctypes.byref(n)))
+        out = np.zeros(max(n.value, 1), np.int32)
+        _check(lib().tnq_plan_fused_chains(self.handle, _ptr(out, ctypes.c_int32), n.value, ctypes.byref(n)))
+        return [int(x) for x in out[: n.value]]
+
+    def keep_chains(self, last_buckets):
+        """Keep fused only the listed chains (tnq_plan_keep_chains)."""
+        arr = np.ascontiguousarray(np.array(list(last_buckets) or [0], dtype=np.int32))
+        _check(lib().tnq_plan_keep_chains(self.handle, _ptr(arr, ctypes.c_int32), len(last_buckets)))
 
     def workspace_bytes(self, batch: int = 1) -> int:
         return int(lib().tnq_plan_workspace_bytes(self.handle, batch))

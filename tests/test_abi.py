@@ -137,3 +137,19 @@ def test_step_kinds_of_the_7x7_plan(tnq_lib):
     kinds = [kind[i] for i in range(n.value)]
     assert kinds.count(1) == info["n_fused_groups"] and set(kinds) <= {0, 1}
     assert sum(nbk[i] for i in range(n.value)) == info["n_buckets"]
+
+
+def test_fused_chain_selection_roundtrip(tnq_lib):
+    """A plan's fused-chain selection can be read and applied to a plan built
+    later from the same circuit and options (planning is deterministic)."""
+    circ = I.random_grid_circuit(6, 6, 24, 0)
+    a = tnq_lib.Plan(circ, max_bag_log2=20, max_p=12)
+    chains = a.fused_chains()
+    assert len(chains) == a.info()["n_fused_groups"] > 1
+    b = tnq_lib.Plan(circ, max_bag_log2=20, max_p=12)
+    assert b.fused_chains() == chains
+    b.keep_chains(chains[::2] + [10 ** 6])
+    assert b.fused_chains() == chains[::2] and b.info()["n_fused_groups"] == len(chains[::2])
+    b.keep_chains([])
+    assert b.fused_chains() == [] and b.info()["n_fused_groups"] == 0
+    assert b.info()["bytes_per_slice"] > a.info()["bytes_per_slice"]

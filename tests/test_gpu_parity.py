@@ -297,6 +297,23 @@ def test_split_precision_gemm_buckets_match_oracle(cuda, tnq_lib, oracle_lib, pr
     assert n_gemm > 0
 
 
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_reordered_plans_match_oracle(cuda, tnq_lib, oracle_lib, precision):
+    """Plans whose order is recomputed after every deletion (the bench's 7x7
+    configuration) contract to the oracle's slices in complex64 and in both
+    split precisions."""
+    circ = I.random_grid_circuit(6, 6, 24, 5)
+    bits = I.random_bitstring(36, 5)
+    plan = tnq_lib.Plan(circ, max_bag_log2=18, max_p=20, reorder_every=1, precision=precision, gemm_min_k_log2=3)
+    assert plan.info()["max_bag"] <= 18
+    amp, per = tnq_lib.contract_sliced(plan, bits, per_slice=True)
+    ref, ref_per = oracle_lib.contract(circ, bits, order=plan.order(), mu=plan.sliced(), per_slice=True)
+    tol = TOL if precision == 0 else SPLIT_TOL
+    for s in range(len(per)):
+        assert rel_err(per[s], ref_per[s], 36) < tol, s
+    assert rel_err(amp, oracle_lib.contract(circ, bits), 36) < tol
+
+
 def test_split_precision_agrees_with_c64(cuda, tnq_lib):
     circ = I.random_grid_circuit(6, 6, 24, 3)
     bits = I.random_bitstring(36, 3)
