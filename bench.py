@@ -94,19 +94,18 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-# DRAM bytes (read + write) of the largest fused-chain launch per slice, from
-# the ncu capture in profiles/k_group_7x7_d1+32+1.md, valid only for the
-# kernel source it was taken from (reported as null once runtime.cu changes).
 # ncu DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of every
-# k_group launch of a one-slice batch of this workload (no autotune: all 17
-# fused chains), valid for the runtime.cu with this SHA-1. Per launch at batch
-# B: bytes_one_slice x B / k_group launches per batch (traffic scales with the
+# k_group launch of a one-slice batch of this workload (the autotuned chain
+# selection, reused through --tune-file; capture command in
+# profiles/k_group_7x7_d1+32+1.md), valid only for the runtime.cu with this
+# SHA-1 (reported as null once it changes). Per launch at batch B:
+# bytes_one_slice x B / k_group launches per batch (traffic scales with the
 # slices of a batch; item-invariant operands are read once per batch, so this
 # slightly overstates it).
-MEASURED_TRAFFIC = {"k_group": {"source_sha1": "28d8678cdaf832624e7b78f1344d0ffd85001158",
-                                "bytes_one_slice": 199153408.0, "launches": 17,
+MEASURED_TRAFFIC = {"k_group": {"source_sha1": "23420507be7e1e618024506446ae9de9d577bfab",
+                                "bytes_one_slice": 490433280.0, "launches": 12,
                                 "capture": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:k_group "
-                                           "-c 17 on a one-slice batch"}}
+                                           "on a one-slice batch of the tuned default plan (12 launches)"}}
 
 
 def runtime_source_sha1():
