@@ -1832,10 +1832,40 @@ tnq_status tnq_plan_autotune(tnq_plan* plan, const uint8_t* bits, void* workspac
       return st;
     }
     std::vector<FusedGroup> keep;
+    bool gemm_dropped = false;
     for (size_t g = 0; g < all.size(); ++g) {
       float t_unfused = 0.f;
       for (int b : all[g].buckets) t_unfused += tu[b];
       if (group_ms[g] < t_unfused) keep.push_back(all[g]);
+      else gemm_dropped |= all[g].gemm;
+    }
+    if (gemm_dropped && plan->opts.fuse_min_rank > 0) {
+      // buckets of a rejected GEMM chain may still fuse as a shared-memory
+      // chain (possibly joined with their neighbours): propose those chains
+      // around the kept GEMM chains and time them against the unfused form
+      std::vector<FusedGroup> gemms;
+      for (const auto& g : keep)
+        if (g.gemm) gemms.push_back(g);
+      set_groups(prog, gemms);
+      fuse_chains(prog, plan->order, plan->opts.fuse_min_rank);
+      const std::vector<FusedGroup> all2 = prog.groups;
+      reset_device_state(*plan);
+      std::vector<float> tf2;
+      st = profile_steps(plan, bits, 0, n_sl, workspace, ws_bytes, (uint32_t)B, stream, tf2, &C);
+      if (st != TNQ_OK) {
+        set_groups(prog, keep);
+        reset_device_state(*plan);
+        return st;
+      }
+      std::vector<float> ms2(all2.size(), 0.f);
+      for (size_t i = 0; i < C->steps.size(); ++i)
+        if (C->step_group[i] >= 0) ms2[C->step_group[i]] = tf2[i];
+      keep.clear();
+      for (size_t g = 0; g < all2.size(); ++g) {
+        float t_unfused = 0.f;
+        for (int b : all2[g].buckets) t_unfused += tu[b];
+        if (all2[g].gemm || ms2[g] < t_unfused) keep.push_back(all2[g]);
+      }
     }
     set_groups(prog, keep);
     reset_device_state(*plan);
