@@ -212,9 +212,11 @@ tnq_status tnq_plan_autotune(tnq_plan* plan, const uint8_t* bits, void* workspac
 tnq_status tnq_plan_fused_chains(const tnq_plan* plan, int32_t* last_bucket, size_t cap, size_t* out_n);
 
 /* Keeps fused only the chains whose last bucket is listed; every other chain
- * runs bucket by bucket (the results do not change: Eq. 2 either way).
- * Indices that name no chain are ignored. Drops the plan's cached device
- * configurations. */
+ * runs bucket by bucket (the results do not change: Eq. 2 either way). The
+ * listed GEMM chains are kept first and the shared-memory chains are then
+ * proposed around them, as the autotuner does, so a selection read from a
+ * tuned plan reproduces it. Indices that name no chain are ignored. Drops the
+ * plan's cached device configurations. */
 tnq_status tnq_plan_keep_chains(tnq_plan* plan, const int32_t* last_bucket, size_t n);
 
 /* tnq_amplitudes_batch: amplitudes of many bitstrings of many plans.

@@ -1887,9 +1887,20 @@ tnq_status tnq_plan_fused_chains(const tnq_plan* plan, int32_t* last_bucket, siz
 tnq_status tnq_plan_keep_chains(tnq_plan* plan, const int32_t* last_bucket, size_t n) {
   if (!plan || (n && !last_bucket)) { set_error("NULL argument"); return TNQ_EINVAL; }
   Program& prog = plan->prog;
+  auto listed = [&](const FusedGroup& g) {
+    return std::find(last_bucket, last_bucket + n, g.buckets.back()) != last_bucket + n;
+  };
+  // the listed GEMM chains, then the shared-memory chains the fusion pass
+  // proposes around them (as the autotuner's second round does), listed ones kept
   std::vector<FusedGroup> keep;
   for (const auto& g : prog.groups)
-    if (std::find(last_bucket, last_bucket + n, g.buckets.back()) != last_bucket + n) keep.push_back(g);
+    if (g.gemm && listed(g)) keep.push_back(g);
+  set_groups(prog, keep);
+  if (plan->opts.fuse_min_rank > 0) fuse_chains(prog, plan->order, plan->opts.fuse_min_rank);
+  std::vector<FusedGroup> all = prog.groups;
+  keep.clear();
+  for (const auto& g : all)
+    if (listed(g)) keep.push_back(g);
   set_groups(prog, keep);
   reset_device_state(*plan);
   return TNQ_OK;

@@ -153,3 +153,24 @@ def test_fused_chain_selection_roundtrip(tnq_lib):
     b.keep_chains([])
     assert b.fused_chains() == [] and b.info()["n_fused_groups"] == 0
     assert b.info()["bytes_per_slice"] > a.info()["bytes_per_slice"]
+
+
+def test_chain_selection_reproduces_after_refusion(tnq_lib):
+    """With GEMM chains (split precision), dropping a chain lets the fusion pass
+    propose new shared-memory chains over its buckets; whatever selection
+    results, applying it to a fresh plan of the same circuit reproduces it."""
+    circ = I.random_grid_circuit(6, 6, 24, 4)
+    kw = dict(max_bag_log2=20, max_p=12, precision=1, gemm_min_k_log2=3)
+    a = tnq_lib.Plan(circ, **kw)
+    assert a.info()["n_gemm_buckets"] > 0
+    chains = a.fused_chains()
+    for drop in range(len(chains)):
+        a = tnq_lib.Plan(circ, **kw)
+        # every bucket index but the dropped chain's: new chains over its buckets are kept too
+        a.keep_chains([i for i in range(20000) if i != chains[drop]])
+        sel = a.fused_chains()
+        assert chains[drop] not in sel
+        b = tnq_lib.Plan(circ, **kw)
+        b.keep_chains(sel)
+        assert b.fused_chains() == sel, drop
+        assert b.info()["bytes_per_slice"] == a.info()["bytes_per_slice"]
