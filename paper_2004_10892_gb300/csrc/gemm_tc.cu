@@ -569,12 +569,9 @@ __global__ void k_gemm_pack(const GemmBucketArgs g, int side) {
 
 void gemm_tc_launch(int kind, const GemmArgs& args, void* stream) {
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-      sms = 148;
-  }
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    sms = 148;
   const long long tiles = (long long)args.batch * args.row_tiles_a * args.row_tiles_b;
   const unsigned grid = (unsigned)std::max<long long>(1, std::min<long long>(tiles, sms));  // one block per SM
   if (kind == GEMM_BF16) {
