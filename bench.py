@@ -262,6 +262,8 @@ def main():
                     help="merged GEMM-shaped buckets on tensor cores in split precision")
     ap.add_argument("--reorder-every", type=int, default=1,
                     help="recompute the greedy order after every this many deletions while slicing (0: never)")
+    ap.add_argument("--fuse-min-rank", type=int, default=12,
+                    help="fuse chains whose intermediate results have >= 2^this entries (0: no fusion)")
     ap.add_argument("--gemm-min-k", type=int, default=4,
                     help="split precision: chains summing >= 2^this values run as GEMMs")
     ap.add_argument("--plain", action="store_true",
@@ -302,7 +304,8 @@ def main():
                         reorder_every=args.reorder_every)
     else:
         plan = tnq.Plan(circ, max_bag_log2=mb, min_p=pmin, max_p=pmax, precision=prec,
-                        gemm_min_k_log2=args.gemm_min_k, reorder_every=args.reorder_every)
+                        gemm_min_k_log2=args.gemm_min_k, reorder_every=args.reorder_every,
+                        fuse_min_rank=args.fuse_min_rank)
     t_plan = time.perf_counter() - t_plan
     n_sl = plan.info()["n_slices"]
     stream = torch.cuda.current_stream()
