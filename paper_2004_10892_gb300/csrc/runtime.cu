@@ -877,6 +877,8 @@ struct ExecConfig {
   std::vector<int> step_group;       // group index of each step (-1 for a single bucket)
   std::vector<double> step_bytes;    // algorithmic bytes of each step (all items)
   std::vector<double> step_flops;    // algorithmic flops of each step (all items; cost model of Section IV)
+  std::vector<std::vector<int>> step_deps;  // earlier steps each step must wait for (concurrent launches)
+  std::vector<int> step_stream;      // side stream of each step in a captured batch
   void* ws = nullptr;                // workspace the graph was captured for
   cudaGraphExec_t exec = nullptr;
 };
@@ -1168,6 +1170,61 @@ static bool gemm_params(const tnq_plan& P, const Layout& L, const FusedGroup& g,
   return true;
 }
 
+// Dependencies between the steps of one batch, for concurrent launches: step
+// i waits for the producer of every tensor it reads, for every earlier step
+// that reads or writes arena memory its output overwrites (the layout reuses
+// the space of dead tensors), and GEMM steps (one shared operand scratch) run
+// in program order. Each step goes to the side stream of its latest
+// dependency (chains stay on one stream), or round-robin when it has none.
+constexpr int N_SIDE_STREAMS = 4;
+static void step_dependencies(const tnq_plan& P, const Layout& L, ExecConfig& C) {
+  const Program& prog = P.prog;
+  const int n = (int)C.steps.size();
+  std::vector<std::vector<int>> reads(n);
+  std::vector<int> write(n, -1);
+  std::vector<int> producer(prog.tensors.size(), -1);
+  {
+    size_t si = 0;
+    for (size_t bi = 0; bi < prog.buckets.size() && si < (size_t)n; ++bi) {
+      const int gi = prog.group_of.empty() ? -1 : prog.group_of[bi];
+      if (gi < 0) {
+        reads[si] = prog.buckets[bi].inputs;
+        write[si] = prog.buckets[bi].output;
+      } else if ((int)bi == prog.groups[gi].buckets.back()) {
+        reads[si] = prog.groups[gi].ext_inputs;
+        write[si] = prog.groups[gi].output;
+      } else {
+        continue;
+      }
+      producer[write[si]] = (int)si;
+      ++si;
+    }
+  }
+  auto lo = [&](int t) { return L.off[t]; };
+  auto hi = [&](int t) { return L.off[t] + ((long long)1 << prog.tensors[t].rank()) * (L.dep[t] ? L.B : 1); };
+  auto overlap = [&](int a, int b) { return lo(a) < hi(b) && lo(b) < hi(a); };
+  C.step_deps.assign(n, {});
+  C.step_stream.assign(n, 0);
+  int last_gemm = -1, rr = 0;
+  for (int i = 0; i < n; ++i) {
+    std::vector<int>& d = C.step_deps[i];
+    for (int t : reads[i])
+      if (producer[t] >= 0 && producer[t] < i) d.push_back(producer[t]);
+    for (int j = 0; j < i; ++j) {
+      bool hit = overlap(write[j], write[i]);
+      for (size_t q = 0; q < reads[j].size() && !hit; ++q) hit = overlap(reads[j][q], write[i]);
+      if (hit) d.push_back(j);
+    }
+    if (C.steps[i].first == 2) {
+      if (last_gemm >= 0) d.push_back(last_gemm);
+      last_gemm = i;
+    }
+    std::sort(d.begin(), d.end());
+    d.erase(std::unique(d.begin(), d.end()), d.end());
+    C.step_stream[i] = d.empty() ? (rr++ % N_SIDE_STREAMS) : C.step_stream[d.back()];
+  }
+}
+
 static bool build_steps(const tnq_plan& P, const Layout& L, ExecConfig& C) {
   const Program& prog = P.prog;
   C.kp.clear();
@@ -1231,6 +1288,7 @@ static bool build_steps(const tnq_plan& P, const Layout& L, ExecConfig& C) {
       C.step_flops.push_back(fl);
     }
   }
+  step_dependencies(P, L, C);
   return true;
 }
 
@@ -1491,7 +1549,17 @@ static void launch_step(const ExecConfig& C, int i, float2* arena, int* me, unsi
 }
 
 // Enqueues one batch (everything after the header upload) on stream s.
-static void enqueue_batch(const tnq_plan& P, ExecConfig& C, char* ws, cudaStream_t s) {
+// Side streams and per-step events used while a batch is captured into a graph
+// (fork from the capturing stream, join before the final kernels).
+struct SideStreams {
+  cudaStream_t st[N_SIDE_STREAMS] = {};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[N_SIDE_STREAMS] = {};
+  std::vector<cudaEvent_t> done;  // one per step
+};
+
+static void enqueue_batch(const tnq_plan& P, ExecConfig& C, char* ws, cudaStream_t s,
+                          const SideStreams* side = nullptr) {
   const Layout& L = C.L;
   const int B = L.B;
   const int T = (int)P.prog.tensors.size();
@@ -1510,7 +1578,23 @@ static void enqueue_batch(const tnq_plan& P, ExecConfig& C, char* ws, cudaStream
   }
   k_scalar_init<<<(B + 127) / 128, 128, 0, s>>>(C.d_scalars, C.n_scalars, C.d_inout, C.n_inout, hdr, bits, scal, B);
   int* status = reinterpret_cast<int*>(ws + L.status_off);
-  for (size_t i = 0; i < C.steps.size(); ++i) launch_step(C, (int)i, arena, me, mm, status, s);
+  if (!side) {
+    for (size_t i = 0; i < C.steps.size(); ++i) launch_step(C, (int)i, arena, me, mm, status, s);
+  } else {
+    cudaEventRecord(side->fork, s);
+    for (int k = 0; k < N_SIDE_STREAMS; ++k) cudaStreamWaitEvent(side->st[k], side->fork, 0);
+    for (size_t i = 0; i < C.steps.size(); ++i) {
+      const int k = C.step_stream[i];
+      for (int j : C.step_deps[i])
+        if (C.step_stream[j] != k) cudaStreamWaitEvent(side->st[k], side->done[j], 0);
+      launch_step(C, (int)i, arena, me, mm, status, side->st[k]);
+      cudaEventRecord(side->done[i], side->st[k]);
+    }
+    for (int k = 0; k < N_SIDE_STREAMS; ++k) {
+      cudaEventRecord(side->join[k], side->st[k]);
+      cudaStreamWaitEvent(s, side->join[k], 0);
+    }
+  }
   const double sc = P.amp_scale_log2;  // = -n_sqrt2 / 2
   const int n_sqrt2 = (int)std::lround(-2.0 * sc);
   const int scale_exp = -(n_sqrt2 / 2), scale_half = n_sqrt2 & 1;
@@ -1539,14 +1623,31 @@ static tnq_status run_batch(const tnq_plan& P, ExecConfig& C, char* ws, cudaStre
   if (!C.exec) {
     cudaStream_t cap;
     CU(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    SideStreams side;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < N_SIDE_STREAMS && e == cudaSuccess; ++k) {
+      e = cudaStreamCreateWithFlags(&side.st[k], cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&side.join[k], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&side.fork, cudaEventDisableTiming);
+    side.done.assign(C.steps.size(), nullptr);
+    for (size_t i = 0; i < side.done.size() && e == cudaSuccess; ++i)
+      e = cudaEventCreateWithFlags(&side.done[i], cudaEventDisableTiming);
     cudaGraph_t g = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      enqueue_batch(P, C, ws, cap);
+      enqueue_batch(P, C, ws, cap, &side);
       e = cudaStreamEndCapture(cap, &g);
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&C.exec, g, 0);
     if (g) cudaGraphDestroy(g);
+    for (cudaEvent_t ev : side.done)
+      if (ev) cudaEventDestroy(ev);
+    for (int k = 0; k < N_SIDE_STREAMS; ++k) {
+      if (side.join[k]) cudaEventDestroy(side.join[k]);
+      if (side.st[k]) cudaStreamDestroy(side.st[k]);
+    }
+    if (side.fork) cudaEventDestroy(side.fork);
     cudaStreamDestroy(cap);
     if (e != cudaSuccess) {
       C.exec = nullptr;
