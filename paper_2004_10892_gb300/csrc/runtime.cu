@@ -1767,6 +1767,56 @@ int tnq_internal_step_kinds(const tnq_plan* plan, int mode, uint32_t batch, int3
   return 0;
 }
 
+// Internal hook (not in include/tnq.h; host only): the concurrency structure of
+// configuration (mode, batch) for checking it on the host. Per step: its side
+// stream, the tensor it writes, up to 16 tensors it reads (-1 past the end) and
+// its dependencies (CSR: dep_off[n+1], deps); per tensor: arena offset and
+// length in elements (-1 when not stored). Returns 1 if a capacity is short.
+int tnq_internal_step_deps(const tnq_plan* plan, int mode, uint32_t batch, int cap_steps, int cap_deps,
+                           int cap_tensors, int32_t* n_steps, int32_t* stream, int32_t* write, int32_t* reads16,
+                           int32_t* dep_off, int32_t* deps, int64_t* t_off, int64_t* t_len) {
+  if (!plan || !n_steps) return 1;
+  ExecConfig C;
+  C.L = make_layout(*plan, mode, (int)batch);
+  if (!build_steps(*plan, C.L, C)) return 1;
+  const Program& prog = plan->prog;
+  const int n = (int)C.steps.size();
+  *n_steps = n;
+  if (n > cap_steps || (int)prog.tensors.size() > cap_tensors) return 1;
+  size_t nd = 0;
+  for (int i = 0; i < n; ++i) nd += C.step_deps[i].size();
+  if ((int)nd > cap_deps) return 1;
+  const Liveness LV = tensor_liveness(prog);
+  for (size_t t = 0; t < prog.tensors.size(); ++t) {
+    const bool stored = !LV.internal[t];
+    t_off[t] = stored ? C.L.off[t] : -1;
+    t_len[t] = stored ? ((int64_t)1 << prog.tensors[t].rank()) * (C.L.dep[t] ? C.L.B : 1) : -1;
+  }
+  size_t si = 0, k = 0;
+  for (size_t bi = 0; bi < prog.buckets.size() && si < (size_t)n; ++bi) {
+    const int gi = prog.group_of.empty() ? -1 : prog.group_of[bi];
+    const std::vector<int>* rd;
+    int w;
+    if (gi < 0) {
+      rd = &prog.buckets[bi].inputs;
+      w = prog.buckets[bi].output;
+    } else if ((int)bi == prog.groups[gi].buckets.back()) {
+      rd = &prog.groups[gi].ext_inputs;
+      w = prog.groups[gi].output;
+    } else {
+      continue;
+    }
+    stream[si] = C.step_stream[si];
+    write[si] = w;
+    for (int q = 0; q < 16; ++q) reads16[16 * si + q] = q < (int)rd->size() ? (*rd)[q] : -1;
+    dep_off[si] = (int32_t)k;
+    for (int j : C.step_deps[si]) deps[k++] = j;
+    ++si;
+  }
+  dep_off[n] = (int32_t)k;
+  return 0;
+}
+
 // Internal measurement hook (not in include/tnq.h): runs the first batch of
 // tnq_contract_sliced(plan, bits, s0, s1, ...) with direct launches and a
 // CUDA event pair around every bucket launch on `stream`. Per bucket it

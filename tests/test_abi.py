@@ -174,3 +174,72 @@ def test_chain_selection_reproduces_after_refusion(tnq_lib):
         b.keep_chains(sel)
         assert b.fused_chains() == sel, drop
         assert b.info()["bytes_per_slice"] == a.info()["bytes_per_slice"]
+
+
+def _step_structure(tnq_lib, plan, batch):
+    L = tnq_lib.lib()
+    f = L.tnq_internal_step_deps
+    P = ctypes.POINTER
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                  P(ctypes.c_int32), P(ctypes.c_int32), P(ctypes.c_int32), P(ctypes.c_int32), P(ctypes.c_int32),
+                  P(ctypes.c_int32), P(ctypes.c_int64), P(ctypes.c_int64)]
+    cs, cd, ct = 4096, 1 << 20, 16384
+    n = ctypes.c_int32()
+    stream, write = (ctypes.c_int32 * cs)(), (ctypes.c_int32 * cs)()
+    reads = (ctypes.c_int32 * (16 * cs))()
+    off, deps = (ctypes.c_int32 * (cs + 1))(), (ctypes.c_int32 * cd)()
+    toff, tlen = (ctypes.c_int64 * ct)(), (ctypes.c_int64 * ct)()
+    assert f(plan.handle, 0, batch, cs, cd, ct, ctypes.byref(n), stream, write, reads, off, deps, toff, tlen) == 0
+    m = n.value
+    steps = []
+    for i in range(m):
+        rd = [x for x in reads[16 * i:16 * i + 16] if x >= 0]
+        steps.append((stream[i], write[i], rd, list(deps[off[i]:off[i + 1]])))
+    return steps, toff, tlen
+
+
+def test_concurrent_step_schedule_never_reads_a_clobbered_tensor(tnq_lib):
+    """The dependencies of a captured batch (four side streams) are sufficient:
+    in many random schedules that respect them and each stream's order, every
+    step's inputs still hold the values their producers wrote (or the leaf
+    values written before the steps) when it runs, checked on an interval
+    model of the arena."""
+    import random
+
+    for circ, kw, batch in [(I.random_grid_circuit(6, 6, 24, 0), dict(max_bag_log2=20, max_p=12), 8),
+                            (I.random_grid_circuit(7, 7, 32, 0), dict(max_bag_log2=28, max_p=40, reorder_every=1,
+                                                                      precision=1), 64)]:
+        plan = tnq_lib.Plan(circ, **kw)
+        steps, toff, tlen = _step_structure(tnq_lib, plan, batch)
+        n = len(steps)
+        assert n > 10 and len({s[0] for s in steps}) > 1  # more than one stream in use
+        rng = random.Random(1)
+        for trial in range(20):
+            done = [False] * n
+            owner = []  # arena intervals (lo, hi, tensor) currently holding valid data
+            stream_steps = {}
+            for i, st in enumerate(steps):
+                stream_steps.setdefault(st[0], []).append(i)
+            pos = {k: 0 for k in stream_steps}
+            outputs = {s_[1] for s_ in steps}
+            leaves = {t for s_ in steps for t in s_[2] if t not in outputs}  # written before the steps
+            for t in leaves:
+                owner.append((toff[t], toff[t] + tlen[t], t))
+            executed = 0
+            while executed < n:
+                ready = [k for k, lst in stream_steps.items() if pos[k] < len(lst)
+                         and all(done[j] for j in steps[lst[pos[k]]][3])]
+                assert ready, "schedule deadlock"
+                k = rng.choice(ready)
+                i = stream_steps[k][pos[k]]
+                pos[k] += 1
+                _, w, rd, _ = steps[i]
+                for t in rd:  # each input must still be owned by itself
+                    lo, hi = toff[t], toff[t] + tlen[t]
+                    assert any(o == t for (a, b, o) in owner if a == lo and b == hi), (trial, i, t)
+                    assert not any(o != t and a < hi and lo < b for (a, b, o) in owner), (trial, i, t)
+                lo, hi = toff[w], toff[w] + tlen[w]
+                owner = [(a, b, o) for (a, b, o) in owner if not (a < hi and lo < b)]
+                owner.append((lo, hi, w))
+                done[i] = True
+                executed += 1
