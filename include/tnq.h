@@ -20,7 +20,11 @@
  *    and streams. Its small device tables are uploaded on first use on each
  *    device and freed by tnq_plan_destroy. The large intermediate tensors live
  *    in a caller-provided device workspace (tnq_plan_workspace_bytes), so
- *    concurrent calls on one plan are safe when each has its own workspace.
+ *    concurrent calls on one plan are safe when each has its own workspace
+ *    (the launch sequences of one plan are serialised internally). The two
+ *    exceptions are tnq_plan_autotune and tnq_plan_keep_chains, which choose
+ *    the plan's fused chains: call them before sharing the plan, not while
+ *    another call uses it.
  *  - Contraction calls are ordered on the given CUDA stream (NULL = the legacy
  *    default stream) and synchronise that stream before they return; results
  *    are FP64 values in host memory.
