@@ -262,6 +262,8 @@ def main():
                     help="merged GEMM-shaped buckets on tensor cores in split precision")
     ap.add_argument("--reorder-every", type=int, default=1,
                     help="recompute the greedy order after every this many deletions while slicing (0: never)")
+    ap.add_argument("--order-trials", type=int, default=1,
+                    help="plan from this many greedy orders (seeded random ties) and keep the cheapest")
     ap.add_argument("--fuse-min-rank", type=int, default=12,
                     help="fuse chains whose intermediate results have >= 2^this entries (0: no fusion)")
     ap.add_argument("--gemm-min-k", type=int, default=4,
@@ -305,7 +307,7 @@ def main():
     else:
         plan = tnq.Plan(circ, max_bag_log2=mb, min_p=pmin, max_p=pmax, precision=prec,
                         gemm_min_k_log2=args.gemm_min_k, reorder_every=args.reorder_every,
-                        fuse_min_rank=args.fuse_min_rank)
+                        fuse_min_rank=args.fuse_min_rank, order_trials=args.order_trials)
     t_plan = time.perf_counter() - t_plan
     n_sl = plan.info()["n_slices"]
     stream = torch.cuda.current_stream()
@@ -397,7 +399,7 @@ def main():
                        "autotune_s": t_tune, "fused_chains": info["n_fused_groups"],
                        "gemm_buckets": info["n_gemm_buckets"], "precision": args.precision,
                        "form": "plain per-slice" if args.plain else "batched, fused, autotuned",
-                       "reorder_every": args.reorder_every},
+                       "reorder_every": args.reorder_every, "order_trials": args.order_trials},
             "time_per_amplitude_s": t_dev / args.steps,
             "rel_err_vs_fp64": err,
             "amplitude": [amp.real, amp.imag],

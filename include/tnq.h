@@ -115,7 +115,9 @@ typedef struct {
                              distributivity in Eq. 2); 0: every gate tensor stays in its own bucket */
   int32_t reorder_every;  /* > 0: recompute the greedy order (opts->ordering) of the reduced graph after every
                              this many deletions (Algorithm 2's optional recomputation step); 0 (default): never */
-  int32_t pad_;
+  int32_t order_trials;   /* > 1: also plan from this many - 1 greedy orders with seeded random ties (seeded by
+                             opts->seed) and keep the plan with the lowest 2^p * sum over steps 2^bag; 0 or 1
+                             (default): the deterministic greedy order only */
 } tnq_plan_opts;
 
 typedef struct {

@@ -76,7 +76,7 @@ tnq_status tnq_plan_from_circuit(int32_t n_qubits, const tnq_gate* gates, size_t
       o.max_p > 62 || o.max_bag_log2 < 0 || o.max_bag_log2 > 40 || o.precision < 0 ||
       o.precision > TNQ_PREC_SPLIT_TF32 || o.ordering < 0 || o.ordering > TNQ_ORDER_MIN_DEGREE ||
       o.fuse_min_rank < 0 || o.fuse_min_rank > 40 || o.leaf_absorb < 0 || o.leaf_absorb > 1 ||
-      o.reorder_every < 0) {
+      o.reorder_every < 0 || o.order_trials < 0 || o.order_trials > 4096) {
     set_error("invalid plan options");
     return TNQ_EINVAL;
   }
@@ -93,17 +93,41 @@ tnq_status tnq_plan_from_circuit(int32_t n_qubits, const tnq_gate* gates, size_t
     std::string err = build_network(n_qubits, gi.data(), n_gates, P->net);
     if (!err.empty()) { set_error(err); return TNQ_EINVAL; }
     P->graph = network_graph(P->net);
-    P->order_full = greedy_order(P->graph, o.ordering);
+    // order_trials > 1: also try greedy orders with seeded random ties and keep
+    // the trial whose sliced plan has the lowest cost 2^p * sum over steps 2^bag
+    // (bag limit met first); trial 0 is the deterministic order
+    const int trials = std::max(1, o.order_trials);
+    double best_cost = 0;
+    bool best_fits = false;
+    for (int trial = 0; trial < trials; ++trial) {
+      uint64_t rs = (o.seed ^ 0x9E3779B97F4A7C15ull) + (uint64_t)trial;
+      std::vector<int> ord = greedy_order(P->graph, o.ordering, trial ? &rs : nullptr);
+      DeletionResult R = greedy_deletion(P->graph, ord, o.slicer, o.min_p, o.max_p, o.max_bag_log2, o.seed,
+                                         o.td_rebuild != 0,
+                                         o.slicer == TNQ_SLICER_LEARNED ? &learned_propose : nullptr, nullptr,
+                                         o.reorder_every, o.ordering);
+      Graph reduced = P->graph;
+      for (int v : R.mu) delete_vertex(reduced, v);
+      std::vector<int> bags;
+      const int tau = treewidth_of_order(reduced, R.reduced_order, &bags);
+      double cost = 0;
+      int max_bag = 0;
+      for (int b : bags) {
+        cost += std::ldexp(1.0, b);
+        max_bag = std::max(max_bag, b);
+      }
+      cost = std::ldexp(cost, (int)R.mu.size());
+      const bool fits = o.max_bag_log2 <= 0 || max_bag <= o.max_bag_log2;
+      if (trial == 0 || (fits && !best_fits) || (fits == best_fits && cost < best_cost)) {
+        best_cost = cost;
+        best_fits = fits;
+        P->order_full = ord;
+        P->mu = R.mu;
+        P->order = R.reduced_order;
+        P->tau = tau;
+      }
+    }
     P->tau_full = treewidth_of_order(P->graph, P->order_full);
-    DeletionResult R = greedy_deletion(P->graph, P->order_full, o.slicer, o.min_p, o.max_p,
-                                       o.max_bag_log2, o.seed, o.td_rebuild != 0,
-                                       o.slicer == TNQ_SLICER_LEARNED ? &learned_propose : nullptr, nullptr,
-                                       o.reorder_every, o.ordering);
-    P->mu = R.mu;
-    P->order = R.reduced_order;
-    Graph reduced = P->graph;
-    for (int v : P->mu) delete_vertex(reduced, v);
-    P->tau = treewidth_of_order(reduced, P->order);
     P->prog = compile_program(P->net, P->order, P->mu);
     if (o.precision != TNQ_PREC_C64)
       find_gemm_chains(P->prog, P->order, o.gemm_min_k_log2 > 0 ? o.gemm_min_k_log2 : 4, 8);

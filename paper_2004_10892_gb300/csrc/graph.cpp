@@ -84,15 +84,17 @@ std::vector<int> bits_to_list(const std::vector<uint64_t>& b) {
 }
 }  // namespace
 
-std::vector<int> greedy_order(const Graph& g0, int method) {
+std::vector<int> greedy_order(const Graph& g0, int method, uint64_t* rng) {
   Elim E(g0);
   for (int v = 0; v < g0.n; ++v) E.set_alive(v);
   std::vector<int> order;
   order.reserve(g0.n);
   std::vector<uint64_t> N, best_N;
+  std::vector<int> ties;
   for (int step = 0; step < g0.n; ++step) {
     int best = -1;
     long best_fill = -1, best_deg = -1;
+    ties.clear();
     for (int v = 0; v < g0.n; ++v) {
       if (!E.is_alive(v)) continue;
       E.nbrs(v, N);
@@ -114,16 +116,27 @@ std::vector<int> greedy_order(const Graph& g0, int method) {
         }
         fill /= 2;
       }
-      bool better;
-      if (best < 0) better = true;
-      else if (method == ORDER_MIN_FILL) better = fill < best_fill || (fill == best_fill && d < best_deg);
-      else better = d < best_deg;
+      bool better, tie;
+      if (best < 0) {
+        better = true;
+        tie = false;
+      } else if (method == ORDER_MIN_FILL) {
+        better = fill < best_fill || (fill == best_fill && d < best_deg);
+        tie = fill == best_fill && d == best_deg;
+      } else {
+        better = d < best_deg;
+        tie = d == best_deg;
+      }
       if (better) {
         best = v;
         best_fill = fill;
         best_deg = d;
+        ties.assign(1, v);
+      } else if (tie) {
+        ties.push_back(v);
       }
     }
+    if (rng && ties.size() > 1) best = ties[splitmix64_next(rng) % ties.size()];
     E.nbrs(best, N);
     E.eliminate(best, N);
     order.push_back(best);

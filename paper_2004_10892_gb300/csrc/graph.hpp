@@ -35,8 +35,10 @@ enum OrderMethod { ORDER_MIN_FILL = 0, ORDER_MIN_DEGREE = 1 };
 enum Slicer { SLICER_TREE_TRIMMING = 0, SLICER_DEGREE = 1, SLICER_DIRECT = 2, SLICER_LEARNED = 3,
               SLICER_BETWEENNESS = 4 };
 
-// Greedy elimination order; `alive` (may be empty) restricts to a vertex subset.
-std::vector<int> greedy_order(const Graph& g, int method);
+// Greedy elimination order (min-fill: fewest fill edges, then lowest degree;
+// min-degree). Ties go to the lowest vertex id, or to a seeded random choice
+// when rng != nullptr.
+std::vector<int> greedy_order(const Graph& g, int method, uint64_t* rng = nullptr);
 
 // Algorithm 1: simulates the elimination of `order` (vertices absent from the
 // order are treated as deleted) and returns the largest neighbourhood seen,

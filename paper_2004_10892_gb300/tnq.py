@@ -38,7 +38,7 @@ class PlanOpts(ctypes.Structure):
                 ("max_p", ctypes.c_int32), ("seed", ctypes.c_uint64), ("precision", ctypes.c_int32),
                 ("gemm_min_k_log2", ctypes.c_int32), ("ordering", ctypes.c_int32),
                 ("td_rebuild", ctypes.c_int32), ("fuse_min_rank", ctypes.c_int32), ("leaf_absorb", ctypes.c_int32),
-                ("reorder_every", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+                ("reorder_every", ctypes.c_int32), ("order_trials", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):

@@ -356,3 +356,17 @@ def test_order_recomputation(tnq_lib):
     a = tnq_lib.Plan(circ, max_bag_log2=16, max_p=30)
     b = tnq_lib.Plan(circ, max_bag_log2=16, max_p=30, reorder_every=1)
     assert b.info()["max_bag"] <= 16 and b.info()["p"] <= a.info()["p"] + 1
+
+
+def test_order_trials(tnq_lib):
+    """Planning from several greedy orders with seeded random ties keeps the
+    bag limit, is deterministic for a seed, and with one trial is the plain
+    deterministic plan."""
+    circ = I.random_grid_circuit(6, 6, 24, 2)
+    one = tnq_lib.Plan(circ, max_bag_log2=16, max_p=30)
+    same = tnq_lib.Plan(circ, max_bag_log2=16, max_p=30, order_trials=1)
+    assert one.order() == same.order() and one.sliced() == same.sliced()
+    a = tnq_lib.Plan(circ, max_bag_log2=16, max_p=30, order_trials=8, seed=3)
+    b = tnq_lib.Plan(circ, max_bag_log2=16, max_p=30, order_trials=8, seed=3)
+    assert a.order() == b.order() and a.sliced() == b.sliced()
+    assert a.info()["max_bag"] <= 16 and a.info()["p"] <= one.info()["p"] + 1
