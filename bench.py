@@ -222,7 +222,8 @@ def run_reference(args, cfg_name):
     rows, cols, cyc, mb, pmin, pmax = CONFIGS[cfg_name]
     circ = inputs.random_grid_circuit(rows, cols, cyc, 0)
     bits = inputs.random_bitstring(circ.n_qubits, 0)
-    plan = tnq.Plan(circ, max_bag_log2=mb, min_p=pmin, max_p=pmax, reorder_every=args.reorder_every)
+    plan = tnq.Plan(circ, max_bag_log2=mb, min_p=pmin, max_p=pmax, reorder_every=args.reorder_every,
+                    order_trials=args.order_trials)
     order, mu = plan.order(), plan.sliced()
     n_sl = plan.info()["n_slices"]
     oracle.build()
@@ -262,7 +263,7 @@ def main():
                     help="merged GEMM-shaped buckets on tensor cores in split precision")
     ap.add_argument("--reorder-every", type=int, default=1,
                     help="recompute the greedy order after every this many deletions while slicing (0: never)")
-    ap.add_argument("--order-trials", type=int, default=1,
+    ap.add_argument("--order-trials", type=int, default=32,
                     help="plan from this many greedy orders (seeded random ties) and keep the cheapest")
     ap.add_argument("--fuse-min-rank", type=int, default=12,
                     help="fuse chains whose intermediate results have >= 2^this entries (0: no fusion)")
@@ -303,7 +304,7 @@ def main():
     if args.plain:
         args.precision, prec, args.max_batch, args.no_autotune = "c64", 0, 1, True
         plan = tnq.Plan(circ, max_bag_log2=mb, min_p=pmin, max_p=pmax, fuse_min_rank=0, leaf_absorb=0,
-                        reorder_every=args.reorder_every)
+                        reorder_every=args.reorder_every, order_trials=args.order_trials)
     else:
         plan = tnq.Plan(circ, max_bag_log2=mb, min_p=pmin, max_p=pmax, precision=prec,
                         gemm_min_k_log2=args.gemm_min_k, reorder_every=args.reorder_every,
