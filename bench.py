@@ -102,10 +102,10 @@ class ClockSampler:
 # bytes_one_slice x B / k_group launches per batch (traffic scales with the
 # slices of a batch; item-invariant operands are read once per batch, so this
 # slightly overstates it).
-MEASURED_TRAFFIC = {"k_group": {"source_sha1": "77d6b6525c5aee73369918b32a3d20c72de25ea3",
-                                "bytes_one_slice": 99669504.0, "launches": 14,
+MEASURED_TRAFFIC = {"k_group": {"source_sha1": "a58f59d456b00f184822d386b44b5d981c2b1ec7",
+                                "bytes_one_slice": 104498432.0, "launches": 12,
                                 "capture": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:k_group "
-                                           "on a one-slice batch of the tuned default plan (14 launches)"}}
+                                           "on a one-slice batch of the tuned default plan (12 launches)"}}
 
 
 def runtime_source_sha1():
