@@ -448,9 +448,19 @@ __device__ __forceinline__ void split16(const float* x, uint4* hi, uint4* lo) {
 // side 1: B rows 2n, 2n+1 = [Re | -Im], [Im | Re] over K for Y assignment n.
 // A thread forms CH consecutive K values of one row (one 16-byte chunk of a
 // core-matrix row per part); consecutive threads take consecutive rows, so
-// eight threads fill one 128-byte core matrix.
+// eight threads fill one 128-byte core matrix. An operand's offset is linear
+// in the bits of W = batch | row << ns | (k >> log2 CH) << (ns + nr); per
+// operand the block keeps only the bits with a nonzero stride (a small folded
+// tensor has at most two), and an operand that does not vary with the low K
+// bits is loaded once per chunk.
+constexpr int PK_BITS = 3 * GB_BITS;
 template <int KIND>
 __global__ void k_gemm_pack(const GemmBucketArgs g, int side) {
+  __shared__ int s_nz[GB_SIDE];
+  __shared__ unsigned char s_pos[GB_SIDE][PK_BITS];
+  __shared__ long long s_str[GB_SIDE][PK_BITS];
+  __shared__ int s_klo[GB_SIDE][8];
+  __shared__ int s_kdep[GB_SIDE];
   constexpr int ES = KIND == GEMM_BF16 ? 2 : 4;
   constexpr int CH = 16 / ES;
   constexpr int CHB = KIND == GEMM_BF16 ? 3 : 2;  // log2 CH
@@ -465,6 +475,31 @@ __global__ void k_gemm_pack(const GemmBucketArgs g, int side) {
   const int rt_count = (int)((side == 0 ? rows : 2 * rows) / GT_ROWS);
   char* hi = (char*)(side == 0 ? g.a_hi : g.b_hi);
   char* lo = (char*)(side == 0 ? g.a_lo : g.b_lo);
+  const int wbits = g.ns + nr + (g.nk > CHB ? g.nk - CHB : 0);
+  if ((int)threadIdx.x < nops) {
+    const int j = threadIdx.x;
+    const GemmOperand& o = ops[j];
+    int n = 0;
+    for (int p = 0; p < wbits; ++p) {
+      const long long st = p < g.ns ? o.sstride[p] : (p < g.ns + nr ? o.rstride[p - g.ns] : o.kstride[p - g.ns - nr + CHB]);
+      if (st) {
+        s_pos[j][n] = (unsigned char)p;
+        s_str[j][n] = st;
+        ++n;
+      }
+    }
+    s_nz[j] = n;
+    int kdep = 0;
+    for (int q = 0; q < CH; ++q) {
+      int a = 0;
+      for (int b = 0; b < CHB && b < g.nk; ++b)
+        if ((q >> b) & 1) a += (int)o.kstride[b];
+      s_klo[j][q] = a;
+      kdep |= a != 0;
+    }
+    s_kdep[j] = kdep;
+  }
+  __syncthreads();
   if (side == 0 && blockIdx.x == 0) {
     // output exponent per item: sum over every operand of its exponent and scale shift
     for (int it = threadIdx.x; it < g.items; it += blockDim.x) {
@@ -502,24 +537,30 @@ __global__ void k_gemm_pack(const GemmBucketArgs g, int side) {
           f = pack_scale(g.meta_m[(long long)o.meta * g.B + (o.dep ? item : 0ll)], &m);
         }
         long long base = o.dep ? item * o.istride : 0ll;
-        for (int b = 0; b < g.ns; ++b)
-          if ((sidx >> b) & 1) base += o.sstride[b];
-        for (int b = 0; b < nr; ++b)
-          if ((r >> b) & 1) base += o.rstride[b];
-        for (int b = CHB; b < g.nk; ++b)
-          if ((k0 >> b) & 1) base += o.kstride[b];
-#pragma unroll
-        for (int q = 0; q < CH; ++q) {
-          if (k0 + q >= (1 << g.nk)) continue;
-          long long off = base;
-#pragma unroll
-          for (int b = 0; b < CHB; ++b)
-            if (((q >> b) & 1) && b < g.nk) off += o.kstride[b];
-          const float2 v = o.ptr[off];
+        const unsigned long long W = (unsigned long long)sidx | ((unsigned long long)r << g.ns) |
+                                     ((unsigned long long)(k0 >> CHB) << (g.ns + nr));
+        const int nz = s_nz[j];
+        for (int i = 0; i < nz; ++i)
+          if ((W >> s_pos[j][i]) & 1ull) base += s_str[j][i];
+        if (!s_kdep[j]) {  // the same value for every K of the chunk
+          const float2 v = o.ptr[base];
           const float vx = v.x * f, vy = v.y * f;
-          const float nre = re[q] * vx - im[q] * vy, nim = re[q] * vy + im[q] * vx;
-          re[q] = nre;
-          im[q] = nim;
+#pragma unroll
+          for (int q = 0; q < CH; ++q) {
+            const float nre = re[q] * vx - im[q] * vy, nim = re[q] * vy + im[q] * vx;
+            re[q] = nre;
+            im[q] = nim;
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < CH; ++q) {
+            if (k0 + q >= (1 << g.nk)) continue;
+            const float2 v = o.ptr[base + s_klo[j][q]];
+            const float vx = v.x * f, vy = v.y * f;
+            const float nre = re[q] * vx - im[q] * vy, nim = re[q] * vy + im[q] * vx;
+            re[q] = nre;
+            im[q] = nim;
+          }
         }
       }
     }
