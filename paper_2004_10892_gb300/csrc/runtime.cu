@@ -434,7 +434,7 @@ __device__ __forceinline__ void stage_pf(const GSt& S, int t, const float2* prev
                                          bool last, const float2* const* s_ptr, float F, const int (*tab)[48],
                                          const int* s_out_hi, long long out_base, int out_lo, float* tmax) {
   static_assert(NV >= 1 && NV <= 3, "one to three varying operands");
-  constexpr int PF = NHI < 2 ? NHI : 2;
+  constexpr int PF = NHI < 2 ? NHI : (NV >= 3 ? 1 : 2);
   float2 k0 = make_float2(F, 0.f), k1 = make_float2(F, 0.f);
   if (K) {
     for (int j = NV; j < S.n_in; ++j) {
@@ -650,6 +650,7 @@ __global__ void __launch_bounds__(TPB, 4) k_group(const __grid_constant__ GParam
                                  : stage_pf_nhi<n, false>(S, t, prev, cur, P.out, last, s_ptr, F, s_tab + S.q0, s_out_hi, s_out_base, out_lo, &tmax)
       if (S.n_var == 1) TNQ_PFK(1);
       else if (S.n_var == 2) TNQ_PFK(2);
+      else if (S.n_var == 3) TNQ_PFK(3);
 #undef TNQ_PFK
       if (!done) switch (S.n_var) {
 #define TNQ_STAGE(n) run_stage<n>(with_k, S, t, prev, cur, P.out, last, s_ptr, F, s_tab + S.q0, s_out_hi, s_out_base, out_lo, &tmax)
