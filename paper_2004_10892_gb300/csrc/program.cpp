@@ -443,6 +443,15 @@ void find_gemm_chains(Program& P, const std::vector<int>& order, int min_k_log2,
     if (g.xvars.size() > 12 || g.yvars.size() > 12 || g.kvars.size() > 12 ||
         g.svars.size() > (size_t)GEMM_BITS_MAX)
       continue;
+    {  // orientation: A rows pad to 128, B's 2^|Y| complex columns to 64; keep the smaller padded product
+      auto up = [](long long v, long long a) { return (v + a - 1) / a * a; };
+      const long long nx = 1ll << g.xvars.size(), ny = 1ll << g.yvars.size();
+      if (up(ny, 128) * up(nx, 64) < up(nx, 128) * up(ny, 64)) {
+        std::swap(g.ga, g.gb);
+        std::swap(g.a_side, g.b_side);
+        std::swap(g.xvars, g.yvars);
+      }
+    }
     g.ext_inputs = {g.ga, g.gb};
     g.ext_inputs.insert(g.ext_inputs.end(), g.a_side.begin(), g.a_side.end());
     g.ext_inputs.insert(g.ext_inputs.end(), g.b_side.begin(), g.b_side.end());

@@ -1943,6 +1943,25 @@ int tnq_internal_profile(const tnq_plan* plan, const uint8_t* bits, uint64_t s0,
   return TNQ_OK;
 }
 
+namespace tnq {
+// profile_steps run `reps` times with the same configuration, keeping each
+// step's shortest time (the first run of a configuration also pays one-time
+// costs: table uploads, module loading, cold caches).
+static tnq_status profile_steps_min(const tnq_plan* plan, const uint8_t* bits, uint64_t s0, uint64_t s1,
+                                    void* workspace, size_t ws_bytes, uint32_t max_batch, void* stream,
+                                    std::vector<float>& ms, ExecConfig** cfg, int reps = 3) {
+  std::vector<float> t;
+  for (int r = 0; r < reps; ++r) {
+    tnq_status st = profile_steps(plan, bits, s0, s1, workspace, ws_bytes, max_batch, stream, t, cfg);
+    if (st != TNQ_OK) return st;
+    if (r == 0) ms = t;
+    else
+      for (size_t i = 0; i < ms.size() && i < t.size(); ++i) ms[i] = std::min(ms[i], t[i]);
+  }
+  return TNQ_OK;
+}
+}  // namespace tnq
+
 tnq_status tnq_plan_autotune(tnq_plan* plan, const uint8_t* bits, void* workspace, size_t ws_bytes,
                              uint32_t max_batch, void* stream, int32_t* out_n_fused) {
   if (!plan || !bits || !workspace) { set_error("NULL argument"); return TNQ_EINVAL; }
@@ -1969,7 +1988,7 @@ tnq_status tnq_plan_autotune(tnq_plan* plan, const uint8_t* bits, void* workspac
     // every candidate chain fused
     std::vector<float> tf, tu;
     ExecConfig* C = nullptr;
-    st = profile_steps(plan, bits, 0, n_sl, workspace, ws_bytes, (uint32_t)B, stream, tf, &C);
+    st = profile_steps_min(plan, bits, 0, n_sl, workspace, ws_bytes, (uint32_t)B, stream, tf, &C);
     if (st != TNQ_OK) return st;
     std::vector<float> group_ms(all.size(), 0.f);
     for (size_t i = 0; i < C->steps.size(); ++i)
@@ -1977,7 +1996,7 @@ tnq_status tnq_plan_autotune(tnq_plan* plan, const uint8_t* bits, void* workspac
     // no chain fused: one step per bucket, in bucket order
     set_groups(prog, {});
     reset_device_state(*plan);
-    st = profile_steps(plan, bits, 0, n_sl, workspace, ws_bytes, (uint32_t)B, stream, tu, &C);
+    st = profile_steps_min(plan, bits, 0, n_sl, workspace, ws_bytes, (uint32_t)B, stream, tu, &C);
     if (st != TNQ_OK) {
       set_groups(prog, all);
       reset_device_state(*plan);
@@ -2003,7 +2022,7 @@ tnq_status tnq_plan_autotune(tnq_plan* plan, const uint8_t* bits, void* workspac
       const std::vector<FusedGroup> all2 = prog.groups;
       reset_device_state(*plan);
       std::vector<float> tf2;
-      st = profile_steps(plan, bits, 0, n_sl, workspace, ws_bytes, (uint32_t)B, stream, tf2, &C);
+      st = profile_steps_min(plan, bits, 0, n_sl, workspace, ws_bytes, (uint32_t)B, stream, tf2, &C);
       if (st != TNQ_OK) {
         set_groups(prog, keep);
         reset_device_state(*plan);
