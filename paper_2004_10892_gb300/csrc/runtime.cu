@@ -309,8 +309,14 @@ __global__ void __launch_bounds__(TPB) k_bucket(const __grid_constant__ KParams 
 //   stage_s[c] = sum_{u_s} prod_j in_j[c, u_s],
 // where in_j is a tensor read from memory at the block's H, or the previous
 // stage's buffer. Offsets are linear in the bits of the stage's local index c;
-// per varying operand a 48-entry table holds the offset of each value of bits
-// 0-3, 4-7 and 8-11 of c (built once per block).
+// per varying operand a table holds the offset of each value of bits 0-3,
+// bits 4..GTB-1 (the rest of the thread index) and bits GTB..11 (the entry
+// counter of the thread) of c, built once per block.
+constexpr int GTB = 7;              // log2 threads per k_group block
+constexpr int GTPB = 1 << GTB;      // threads per k_group block
+constexpr int GT_MID = 16;          // table entries of bits 4..GTB-1 start here
+constexpr int GT_HI = GT_MID + (1 << (GTB - 4));  // ... and of bits GTB..GL_MAX-2 here
+constexpr int TABW = GT_HI + (1 << (GL_MAX - 1 - GTB));
 constexpr int GH_MAX = 32;  // tile bits (output variables outside the block; a bag of 2^40 entries has < 32)
 constexpr int PAIR_MAX = GIN_MAX + GM_MAX - 1;  // varying (stage, operand) pairs: at most every input of every stage
 constexpr int GROUP_SMEM_BYTES = (1 << (GL_MAX - 1)) * 3 / 2 * (int)sizeof(float2);  // regions A + B
@@ -331,6 +337,7 @@ struct GSt {
   int cstride[KMAX][GL_MAX];   // element stride of local output bit b, per input
   int ustride[KMAX];           // stride of the eliminated variable, per input
   int q0;                      // offset table of varying input j is pair q0 + j
+  int pd;                      // 1: input 0 is the previous stage's buffer at offset 2c (u at bit 0)
 };
 
 struct GParams {
@@ -350,17 +357,17 @@ struct GParams {
 // local bits: their (u=0, u=1) pairs, times the stage's power-of-two scales,
 // are multiplied once into a constant pair (K = true). Without such inputs
 // (K = false) the product starts from the first varying operand and the
-// scales multiply the sum. Each thread handles local entries c = t + 256 it;
+// scales multiply the sum. Each thread handles local entries c = t + GTPB it;
 // per entry only the NV varying operands are loaded (one 16-byte load each:
 // the eliminated variable is bit 0 of every operand), and the last operand's
 // multiply is fused with the sum over u.
 template <int NV, bool K>
 __device__ __forceinline__ void group_stage(const GSt& S, int t, const float2* prev, float2* cur, float2* out,
-                                            bool last, const float2* const* s_ptr, float F, const int (*tab)[48],
+                                            bool last, const float2* const* s_ptr, float F, const int (*tab)[TABW],
                                             const int* s_out_hi, long long out_base, int out_lo, float* tmax) {
   static_assert(K || NV > 0, "a stage without constant inputs has a varying operand");
   const int nb = S.nbits;
-  const int n_hi = nb > 8 ? (1 << (nb - 8)) : 1;
+  const int n_hi = nb > GTB ? (1 << (nb - GTB)) : 1;
   const int nent = 1 << nb;
   float2 k0 = make_float2(F, 0.f), k1 = make_float2(F, 0.f);
   if (K) {
@@ -377,28 +384,28 @@ __device__ __forceinline__ void group_stage(const GSt& S, int t, const float2* p
   for (int j = 0; j < NV; ++j) {
     const int src = S.src[j];
     ptr[j] = src < 0 ? prev : s_ptr[src];
-    lo[j] = tab[j][t & 15] + tab[j][16 + ((t >> 4) & 15)];
+    lo[j] = tab[j][t & 15] + tab[j][GT_MID + (t >> 4)];
   }
 #pragma unroll 2
   for (int it = 0; it < n_hi; ++it) {
-    const int c = t + (it << 8);
+    const int c = t + (it << GTB);
     if (c < nent) {
       float2 p0 = k0, p1 = k1;
       constexpr int J0 = K ? 0 : 1;
       if (!K) {
-        const float4 v = *reinterpret_cast<const float4*>(ptr[0] + lo[0] + tab[0][32 + it]);
+        const float4 v = *reinterpret_cast<const float4*>(ptr[0] + lo[0] + tab[0][GT_HI + it]);
         p0 = make_float2(v.x, v.y);
         p1 = make_float2(v.z, v.w);
       }
 #pragma unroll
       for (int j = J0; j < NV - 1; ++j) {
-        const float4 v = *reinterpret_cast<const float4*>(ptr[j] + lo[j] + tab[j][32 + it]);
+        const float4 v = *reinterpret_cast<const float4*>(ptr[j] + lo[j] + tab[j][GT_HI + it]);
         p0 = cmul(p0, make_float2(v.x, v.y));
         p1 = cmul(p1, make_float2(v.z, v.w));
       }
       float2 r;
       if (NV >= 1 && (K || NV >= 2)) {
-        const float4 v = *reinterpret_cast<const float4*>(ptr[NV - 1] + lo[NV - 1] + tab[NV - 1][32 + it]);
+        const float4 v = *reinterpret_cast<const float4*>(ptr[NV - 1] + lo[NV - 1] + tab[NV - 1][GT_HI + it]);
         float rx = p0.x * v.x;
         rx = fmaf(-p0.y, v.y, rx);
         rx = fmaf(p1.x, v.z, rx);
@@ -422,101 +429,155 @@ __device__ __forceinline__ void group_stage(const GSt& S, int t, const float2* p
   }
 }
 
-// Stage with NV = 1..3 varying operands and exactly 2^nbits = 256 NHI local
-// entries (NHI = 1 also covers nbits < 8: threads past the end compute a
+// Stage with NV = 1..3 varying operands and exactly 2^nbits = GTPB NHI local
+// entries (NHI = 1 also covers nbits < GTB: threads past the end compute a
 // duplicate entry from in-range offsets, since the tables hold 0 for bits >=
-// nbits, and do not store it). The entry loop is unrolled and each operand's
-// 16-byte loads run PF entries ahead of the arithmetic, so that several loads
-// per operand are in flight per thread (the loads are the latency that bounds
-// this kernel). K as in group_stage.
-template <int NV, bool K, int NHI>
+// nbits, and do not store it). Thread t handles entries c = t + GTPB it.
+//   * The entry counter runs in blocks of U entries: an operand's offset is
+//     the sum of the table values of its set bits, so entry it0 + u of a
+//     block is at (offset of it0) + (offset of u) -- one table read per block
+//     and operand, the U inner offsets stay in registers.
+//   * Each operand's 16-byte loads run PF entries ahead of the arithmetic
+//     (global operands through the read-only path); the last block is peeled
+//     so that no entry tests whether its prefetch is in range.
+//   * PD: operand 0 is the previous stage's buffer read densely (entry c at
+//     2c): shared memory at a constant step per entry.
+//   * LAST: the stage writes the group's output (global) and its maximum.
+// K as in group_stage.
+template <bool B>
+struct BoolTag {
+  static constexpr bool value = B;
+};
+
+template <int NV, bool K, int NHI, bool PD, bool LAST>
 __device__ __forceinline__ void stage_pf(const GSt& S, int t, const float2* prev, float2* cur, float2* out,
-                                         bool last, const float2* const* s_ptr, float F, const int (*tab)[48],
+                                         const float2* const* s_ptr, float F, const int (*tab)[TABW],
                                          const int* s_out_hi, long long out_base, int out_lo, float* tmax) {
   static_assert(NV >= 1 && NV <= 3, "one to three varying operands");
-  constexpr int PF = NHI < 2 ? NHI : (NV >= 3 ? 1 : 2);
+  constexpr int PF = NHI < 2 ? NHI : ((NV >= 3 && GTB >= 8) ? 1 : 2);  // 64 registers at 256 threads
+  constexpr int U = NHI < 4 ? NHI : 4;  // entries per block (a multiple of PF)
+  constexpr int NB = NHI / U;
   float2 k0 = make_float2(F, 0.f), k1 = make_float2(F, 0.f);
   if (K) {
     for (int j = NV; j < S.n_in; ++j) {
-      const float2* q = S.src[j] < 0 ? prev : s_ptr[S.src[j]];
-      const float4 v = *reinterpret_cast<const float4*>(q);
+      const float4 v = __ldg(reinterpret_cast<const float4*>(s_ptr[S.src[j]]));
       k0 = cmul(k0, make_float2(v.x, v.y));
       k1 = cmul(k1, make_float2(v.z, v.w));
     }
   }
-  const float2* pj[NV];
+  const float4* base[NV];  // operand at entry t of block 0
+  int ti[NV][U];           // inner offsets (float4 units)
 #pragma unroll
-  for (int j = 0; j < NV; ++j)
-    pj[j] = (S.src[j] < 0 ? prev : s_ptr[S.src[j]]) + tab[j][t & 15] + tab[j][16 + ((t >> 4) & 15)];
+  for (int j = 0; j < NV; ++j) {
+    if (PD && j == 0) {
+      base[0] = reinterpret_cast<const float4*>(prev) + t;
+#pragma unroll
+      for (int u = 0; u < U; ++u) ti[0][u] = u * GTPB;
+    } else {
+      base[j] = reinterpret_cast<const float4*>(s_ptr[S.src[j]] + tab[j][t & 15] + tab[j][GT_MID + (t >> 4)]);
+#pragma unroll
+      for (int u = 0; u < U; ++u) ti[j][u] = tab[j][GT_HI + u] >> 1;
+    }
+  }
+  auto load = [&](int j, const float4* q) -> float4 { return (PD && j == 0) ? *q : __ldg(q); };
+  const float4* ob[NV];   // this block
+  const float4* obn[NV];  // next block
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    ob[j] = base[j];
+    obn[j] = base[j] + ((PD && j == 0) ? U * GTPB : (NB > 1 ? (tab[j][GT_HI + U] >> 1) : 0));
+  }
   float4 v[PF][NV];
 #pragma unroll
   for (int i = 0; i < PF; ++i)
 #pragma unroll
-    for (int j = 0; j < NV; ++j) v[i][j] = *reinterpret_cast<const float4*>(pj[j] + tab[j][32 + i]);
-  constexpr int U = NHI < 4 ? NHI : 4;  // entries per unrolled step (a multiple of PF)
-#pragma unroll 1
-  for (int it0 = 0; it0 < NHI; it0 += U)
+    for (int j = 0; j < NV; ++j) v[i][j] = load(j, ob[j] + ti[j][i]);
+  int so[U];
+  float2* dst = nullptr;
+  if (LAST) {
 #pragma unroll
-  for (int u = 0; u < U; ++u) {
-    const int it = it0 + u;
-    float4 cv[NV];
+    for (int u = 0; u < U; ++u) so[u] = s_out_hi[u];
+    dst = out + out_base + out_lo;
+  }
+  // one block of U entries; TAIL: the last block (no prefetch past the end)
+  auto block = [&](int it0, auto tail_tag) {
+    constexpr bool TAIL = decltype(tail_tag)::value;
+    const int oh = LAST ? s_out_hi[it0] : 0;
 #pragma unroll
-    for (int j = 0; j < NV; ++j) cv[j] = v[u % PF][j];
-    if (it + PF < NHI) {
+    for (int u = 0; u < U; ++u) {
+      float4 cv[NV];
 #pragma unroll
-      for (int j = 0; j < NV; ++j) v[u % PF][j] = *reinterpret_cast<const float4*>(pj[j] + tab[j][32 + it + PF]);
-    }
-    float2 p0 = k0, p1 = k1;
-    if (!K) {
-      p0 = make_float2(cv[0].x, cv[0].y);
-      p1 = make_float2(cv[0].z, cv[0].w);
-    }
+      for (int j = 0; j < NV; ++j) cv[j] = v[u % PF][j];
+      if (!TAIL || u + PF < U) {
 #pragma unroll
-    for (int j = K ? 0 : 1; j < NV - 1; ++j) {
-      p0 = cmul(p0, make_float2(cv[j].x, cv[j].y));
-      p1 = cmul(p1, make_float2(cv[j].z, cv[j].w));
-    }
-    float2 r;
-    if (K || NV >= 2) {
-      const float4 b = cv[NV - 1];
-      float rx = p0.x * b.x;
-      rx = fmaf(-p0.y, b.y, rx);
-      rx = fmaf(p1.x, b.z, rx);
-      rx = fmaf(-p1.y, b.w, rx);
-      float ry = p0.x * b.y;
-      ry = fmaf(p0.y, b.x, ry);
-      ry = fmaf(p1.x, b.w, ry);
-      ry = fmaf(p1.y, b.z, ry);
-      r = make_float2(rx, ry);
-    } else {
-      r = make_float2(p0.x + p1.x, p0.y + p1.y);
-    }
-    if (!K) r = make_float2(r.x * F, r.y * F);
-    const int c = t + (it << 8);
-    if (NHI > 1 || c < (1 << S.nbits)) {
-      if (last) {
-        out[out_base + out_lo + s_out_hi[it]] = r;
-        *tmax = fmaxf(*tmax, fmaxf(fabsf(r.x), fabsf(r.y)));
+        for (int j = 0; j < NV; ++j)
+          v[u % PF][j] = load(j, u + PF < U ? ob[j] + ti[j][u + PF] : obn[j] + ti[j][u + PF - U]);
+      }
+      float2 p0 = k0, p1 = k1;
+      if (!K) {
+        p0 = make_float2(cv[0].x, cv[0].y);
+        p1 = make_float2(cv[0].z, cv[0].w);
+      }
+#pragma unroll
+      for (int j = K ? 0 : 1; j < NV - 1; ++j) {
+        p0 = cmul(p0, make_float2(cv[j].x, cv[j].y));
+        p1 = cmul(p1, make_float2(cv[j].z, cv[j].w));
+      }
+      float2 r;
+      if (K || NV >= 2) {
+        const float4 b = cv[NV - 1];
+        float rx = p0.x * b.x;
+        rx = fmaf(-p0.y, b.y, rx);
+        rx = fmaf(p1.x, b.z, rx);
+        rx = fmaf(-p1.y, b.w, rx);
+        float ry = p0.x * b.y;
+        ry = fmaf(p0.y, b.x, ry);
+        ry = fmaf(p1.x, b.w, ry);
+        ry = fmaf(p1.y, b.z, ry);
+        r = make_float2(rx, ry);
       } else {
-        cur[c] = r;
+        r = make_float2(p0.x + p1.x, p0.y + p1.y);
+      }
+      if (!K) r = make_float2(r.x * F, r.y * F);
+      if (NHI > 1 || t < (1 << S.nbits)) {
+        if (LAST) {
+          dst[oh + so[u]] = r;
+          *tmax = fmaxf(*tmax, fmaxf(fabsf(r.x), fabsf(r.y)));
+        } else {
+          cur[t + (it0 + u) * GTPB] = r;
+        }
       }
     }
+  };
+#pragma unroll 1
+  for (int b = 0; b < NB - 1; ++b) {
+    block(b * U, BoolTag<false>{});
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      ob[j] = obn[j];
+      if (b + 2 < NB) obn[j] = base[j] + ((PD && j == 0) ? (b + 2) * U * GTPB : (tab[j][GT_HI + (b + 2) * U] >> 1));
+    }
   }
+  block((NB - 1) * U, BoolTag<true>{});
 }
 
-// Dispatch of stage_pf over (NV, K, NHI); false if the stage has another shape.
-template <int NV, bool K>
+// Dispatch of stage_pf over (NV, K, NHI, PD, LAST); false if the stage has another shape.
+template <int NV, bool K, bool PD>
 __device__ __forceinline__ bool stage_pf_nhi(const GSt& S, int t, const float2* prev, float2* cur, float2* out,
-                                             bool last, const float2* const* s_ptr, float F, const int (*tab)[48],
+                                             bool last, const float2* const* s_ptr, float F, const int (*tab)[TABW],
                                              const int* s_out_hi, long long out_base, int out_lo, float* tmax) {
-#define TNQ_PF(n) stage_pf<NV, K, n>(S, t, prev, cur, out, last, s_ptr, F, tab, s_out_hi, out_base, out_lo, tmax)
-  switch (S.nbits) {
-    case 12: TNQ_PF(16); return true;
-    case 11: TNQ_PF(8); return true;
-    case 10: TNQ_PF(4); return true;
-    case 9: TNQ_PF(2); return true;
+#define TNQ_PF(n)                                                                                          \
+  (last ? stage_pf<NV, K, n, PD, true>(S, t, prev, cur, out, s_ptr, F, tab, s_out_hi, out_base, out_lo, tmax) \
+        : stage_pf<NV, K, n, PD, false>(S, t, prev, cur, out, s_ptr, F, tab, s_out_hi, out_base, out_lo, tmax))
+  static_assert(GL_MAX - 1 - GTB <= 5, "entries per thread above 32");
+  switch (S.nbits - GTB) {
+    case 5: TNQ_PF(32); return true;
+    case 4: TNQ_PF(16); return true;
+    case 3: TNQ_PF(8); return true;
+    case 2: TNQ_PF(4); return true;
+    case 1: TNQ_PF(2); return true;
     default:
-      if (S.nbits > 8) return false;
+      if (S.nbits > GTB) return false;
       TNQ_PF(1);
       return true;
   }
@@ -526,7 +587,7 @@ __device__ __forceinline__ bool stage_pf_nhi(const GSt& S, int t, const float2* 
 template <int NV>
 __device__ __forceinline__ void run_stage(bool with_k, const GSt& S, int t, const float2* prev, float2* cur,
                                           float2* out, bool last, const float2* const* s_ptr, float F,
-                                          const int (*tab)[48], const int* s_out_hi, long long out_base, int out_lo,
+                                          const int (*tab)[TABW], const int* s_out_hi, long long out_base, int out_lo,
                                           float* tmax) {
   if (NV == 0 || with_k)
     group_stage<NV, true>(S, t, prev, cur, out, last, s_ptr, F, tab, s_out_hi, out_base, out_lo, tmax);
@@ -537,19 +598,19 @@ __device__ __forceinline__ void run_stage(bool with_k, const GSt& S, int t, cons
 
 // Persistent fused-group kernel: every block builds the stage tables once,
 // then loops over tiles (item, H assignment) tile = blockIdx.x + k*gridDim.x.
-__global__ void __launch_bounds__(TPB, 4) k_group(const __grid_constant__ GParams P, long long n_tiles) {
+__global__ void __launch_bounds__(GTPB, 4) k_group(const __grid_constant__ GParams P, long long n_tiles) {
   extern __shared__ float2 g_stage[];  // stage regions A (2^(GL_MAX-1) entries) and B (half of A)
   __shared__ int s_hstr[GIN_MAX + 1][GH_MAX];  // row GIN_MAX: the output (within-item offsets < 2^31)
   __shared__ const float2* s_ptr[GIN_MAX];
   __shared__ float s_F[GM_MAX];  // per stage: product of its memory inputs' power-of-two scales
   __shared__ int s_e[GIN_MAX];
-  __shared__ int s_tab[PAIR_MAX][48];
-  __shared__ int s_out_hi[16];
+  __shared__ int s_tab[PAIR_MAX][TABW];
+  __shared__ int s_out_hi[1 << (GL_MAX - 1 - GTB)];
   __shared__ long long s_out_base;
-  __shared__ float s_red[TPB / 32];
+  __shared__ float s_red[GTPB / 32];
   const int t = threadIdx.x;
   // tables shared by every tile
-  for (int e = t; e < (GIN_MAX + 1) * GH_MAX; e += TPB) {
+  for (int e = t; e < (GIN_MAX + 1) * GH_MAX; e += GTPB) {
     const int j = e / GH_MAX, i = e - j * GH_MAX;
     long long v = 0;
     if (i < P.n_h) v = (j < P.n_gin) ? P.gin[j].hstride[i] : (j == GIN_MAX ? P.out_hstride[i] : 0ll);
@@ -558,27 +619,28 @@ __global__ void __launch_bounds__(TPB, 4) k_group(const __grid_constant__ GParam
   for (int s = 0; s < P.n_st; ++s) {
     const GSt& S = P.st[s];
     const int nb = S.nbits;
-    for (int e = t; e < S.n_var * 48; e += TPB) {
-      const int j = e / 48, r = e - j * 48, part = r >> 4, v = r & 15;
+    for (int e = t; e < S.n_var * TABW; e += GTPB) {
+      const int j = e / TABW, r = e - j * TABW;
+      // r -> (first bit, value): bits 0-3, bits 4..GTB-1, bits GTB..
+      const int b0 = r < GT_MID ? 0 : (r < GT_HI ? 4 : GTB);
+      const int v = r - (r < GT_MID ? 0 : (r < GT_HI ? GT_MID : GT_HI));
       int a = 0;
-      for (int i = 0; i < 4; ++i) {
-        const int bit = part * 4 + i;
-        if (bit < nb && ((v >> i) & 1)) a += S.cstride[j][bit];
-      }
+      for (int i = 0; (v >> i) != 0; ++i)
+        if (b0 + i < nb && ((v >> i) & 1)) a += S.cstride[j][b0 + i];
       s_tab[S.q0 + j][r] = a;
     }
   }
   const GSt& SL = P.st[P.n_st - 1];
   const int nb_last = SL.nbits;
-  const int n_hi_last = nb_last > 8 ? (1 << (nb_last - 8)) : 1;
-  for (int it = t; it < n_hi_last; it += TPB) {
+  const int n_hi_last = nb_last > GTB ? (1 << (nb_last - GTB)) : 1;
+  for (int it = t; it < n_hi_last; it += GTPB) {
     int a = 0;
-    for (int i = 8; i < nb_last; ++i)
-      if ((it >> (i - 8)) & 1) a += P.out_cstride[i];
+    for (int i = GTB; i < nb_last; ++i)
+      if ((it >> (i - GTB)) & 1) a += P.out_cstride[i];
     s_out_hi[it] = a;
   }
   int out_lo = 0;
-  for (int i = 0; i < 8 && i < nb_last; ++i)
+  for (int i = 0; i < GTB && i < nb_last; ++i)
     if ((t >> i) & 1) out_lo += P.out_cstride[i];
   const int buf_elems = 1 << (GL_MAX - 1);
   long long cur_item = -1;
@@ -595,7 +657,7 @@ __global__ void __launch_bounds__(TPB, 4) k_group(const __grid_constant__ GParam
         __syncthreads();
         if (t == 0) {
           float b = 0.f;
-          for (int w = 0; w < TPB / 32; ++w) b = fmaxf(b, s_red[w]);
+          for (int w = 0; w < GTPB / 32; ++w) b = fmaxf(b, s_red[w]);
           if (b > 0.f) atomic_max_pos(&P.meta_m[(long long)P.out_meta * P.B + (P.out_dep ? cur_item : 0ll)], b);
         }
       }
@@ -629,7 +691,7 @@ __global__ void __launch_bounds__(TPB, 4) k_group(const __grid_constant__ GParam
       }
       s_F[t - P.n_gin] = f;
     }
-    if (t == TPB - 1) {
+    if (t == GTPB - 1) {
       long long b = P.out_dep ? item * P.out_istride : 0ll;
       for (int i = 0; i < P.n_h; ++i)
         if ((h >> i) & 1ll) b += s_hstr[GIN_MAX][i];
@@ -646,12 +708,18 @@ __global__ void __launch_bounds__(TPB, 4) k_group(const __grid_constant__ GParam
       const bool with_k = S.n_in > S.n_var;
       bool done = false;
       const float F = s_F[s];
-#define TNQ_PFK(n) done = with_k ? stage_pf_nhi<n, true>(S, t, prev, cur, P.out, last, s_ptr, F, s_tab + S.q0, s_out_hi, s_out_base, out_lo, &tmax) \
-                                 : stage_pf_nhi<n, false>(S, t, prev, cur, P.out, last, s_ptr, F, s_tab + S.q0, s_out_hi, s_out_base, out_lo, &tmax)
-      if (S.n_var == 1) TNQ_PFK(1);
-      else if (S.n_var == 2) TNQ_PFK(2);
-      else if (S.n_var == 3) TNQ_PFK(3);
+#define TNQ_PFK2(n, pdv) done = with_k ? stage_pf_nhi<n, true, pdv>(S, t, prev, cur, P.out, last, s_ptr, F, s_tab + S.q0, s_out_hi, s_out_base, out_lo, &tmax) \
+                                      : stage_pf_nhi<n, false, pdv>(S, t, prev, cur, P.out, last, s_ptr, F, s_tab + S.q0, s_out_hi, s_out_base, out_lo, &tmax)
+// (a previous-stage operand that is not dense takes the generic path)
+#define TNQ_PFK(n) { if (S.pd) { TNQ_PFK2(n, true); } else if (S.src[0] >= 0) { TNQ_PFK2(n, false); } }
+      switch (S.n_var) {
+        case 1: TNQ_PFK(1) break;
+        case 2: TNQ_PFK(2) break;
+        case 3: TNQ_PFK(3) break;
+        default: break;
+      }
 #undef TNQ_PFK
+#undef TNQ_PFK2
       if (!done) switch (S.n_var) {
 #define TNQ_STAGE(n) run_stage<n>(with_k, S, t, prev, cur, P.out, last, s_ptr, F, s_tab + S.q0, s_out_hi, s_out_base, out_lo, &tmax)
         case 0: TNQ_STAGE(0); break;
@@ -684,7 +752,7 @@ __global__ void __launch_bounds__(TPB, 4) k_group(const __grid_constant__ GParam
   __syncthreads();
   if (t == 0 && cur_item >= 0) {
     float b = 0.f;
-    for (int w = 0; w < TPB / 32; ++w) b = fmaxf(b, s_red[w]);
+    for (int w = 0; w < GTPB / 32; ++w) b = fmaxf(b, s_red[w]);
     if (b > 0.f) atomic_max_pos(&P.meta_m[(long long)P.out_meta * P.B + (P.out_dep ? cur_item : 0ll)], b);
   }
 }
@@ -1044,6 +1112,9 @@ static GParams group_gparams(const tnq_plan& P, const Layout& L, const FusedGrou
     std::stable_partition(ins.begin(), ins.end(), varies);
     S.n_var = 0;
     for (int tid : ins) S.n_var += varies(tid) ? 1 : 0;
+    // the previous stage's buffer first among the varying inputs
+    const int prev_tid = s > 0 ? prog.buckets[g.buckets[s - 1]].output : -1;
+    std::stable_partition(ins.begin(), ins.begin() + S.n_var, [&](int tid) { return tid == prev_tid; });
     S.q0 = G.n_pairs;
     G.n_pairs += S.n_var;
     if (G.n_pairs > PAIR_MAX) return G;
@@ -1072,6 +1143,12 @@ static GParams group_gparams(const tnq_plan& P, const Layout& L, const FusedGrou
         S.ustride[j] = 1 << pu;
       }
     }
+  }
+  for (int s = 0; s < G.n_st; ++s) {  // dense previous-stage operand (offset 2c, u at bit 0)
+    GSt& S = G.st[s];
+    bool d = S.n_var > 0 && S.src[0] < 0 && S.ustride[0] == 1;
+    for (int b = 0; d && b < S.nbits; ++b) d = S.cstride[0][b] == (2 << b);
+    S.pd = d ? 1 : 0;
   }
   const auto& last = sv[G.n_st - 1];
   for (size_t b = 0; b < last.size(); ++b) {
@@ -1431,7 +1508,7 @@ static tnq_status group_grid_size(int* out) {
   int dev = 0, sms = 0, per_sm = 0;
   CU(cudaGetDevice(&dev));
   CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_group, TPB, GROUP_SMEM_BYTES));
+  CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_group, GTPB, GROUP_SMEM_BYTES));
   *out = std::max(1, sms * std::max(1, per_sm));
   return TNQ_OK;
 }
@@ -1545,7 +1622,7 @@ static void launch_step(const ExecConfig& C, int i, float2* arena, int* me, unsi
     g.meta_m = mm;
     const long long tiles = (g.out_dep ? (long long)g.B : 1ll) << g.n_h;
     const long long grid = std::min<long long>(tiles, (long long)C.group_grid);
-    k_group<<<(unsigned)grid, TPB, C.gsmem[st.second], s>>>(g, tiles);
+    k_group<<<(unsigned)grid, GTPB, C.gsmem[st.second], s>>>(g, tiles);
   }
 }
 
