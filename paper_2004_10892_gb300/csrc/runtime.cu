@@ -37,6 +37,7 @@ constexpr int GMAX = 52;  // index bits of one bucket launch (output bits + item
 static_assert(GB_SIDE >= GEMM_SIDE_MAX + 1 && GB_BITS >= GEMM_BITS_MAX, "GEMM limits of planner and kernels differ");
 constexpr int TPB = 256;  // threads per block of the bucket kernel
 constexpr int MAX_ITEM_BITS = 16;
+constexpr int HOIST_MAX_BITS = 24;  // largest early-bucket result (2^24 entries; see hoist_levels)
 
 // ---------------------------------------------------------------------------
 // device-side records
@@ -53,6 +54,18 @@ struct KParams {
   int B;                         // meta row length
   int* meta_e;
   unsigned* meta_m;
+};
+
+// One early bucket of a level launch (k_bucket_level): like KParams for an
+// item-invariant bucket, with arena byte offsets instead of pointers.
+struct HoistDev {
+  long long out;                  // arena byte offset of the result
+  long long in[KMAX];             // arena byte offsets of the inputs
+  long long stride[KMAX][HOIST_MAX_BITS];  // element stride of each output bit, per input
+  int in_meta[KMAX];              // meta row of input j, -1 for gate tensors (unit scale)
+  int nin, bits, sum, out_meta;   // inputs, output bits, 1: sum over bit 0 (Eq. 2), meta row of the result
+  int blk0;                       // first block of this bucket in its level's launch
+  int pad;
 };
 
 struct LeafDev {
@@ -299,6 +312,85 @@ __global__ void __launch_bounds__(TPB) k_bucket(const __grid_constant__ KParams 
       float b = 0.f;
       for (int w = 0; w < TPB / 32; ++w) b = fmaxf(b, sh_red[w]);
       if (b > 0.f && g0 < total) atomic_max_pos(&P.meta_m[(long long)P.out_meta * P.B + (g0 >> ob)], b);
+    }
+  }
+}
+
+// K1 for the early buckets of one level (see hoist_levels): every bucket of
+// the level in one launch, 256 entries per block; block b works on the bucket
+// whose blk0 is the largest not above b. Item-invariant: one meta row each.
+__global__ void __launch_bounds__(256) k_bucket_level(const HoistDev* __restrict__ hd, int n, char* arena,
+                                                     int* meta_e, unsigned* meta_m, int B) {
+  __shared__ int s_b;
+  __shared__ long long s_str[KMAX][HOIST_MAX_BITS];
+  __shared__ const float2* s_in[KMAX];
+  __shared__ float s_f[KMAX];
+  __shared__ float s_red[8];
+  const int t = threadIdx.x;
+  if (t == 0) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (hd[mid].blk0 <= (int)blockIdx.x) lo = mid;
+      else hi = mid - 1;
+    }
+    s_b = lo;
+  }
+  __syncthreads();
+  const HoistDev& H = hd[s_b];
+  const int nin = H.nin, bits = H.bits;
+  for (int e = t; e < nin * bits; e += 256) s_str[e / bits][e % bits] = H.stride[e / bits][e % bits];
+  if (t < nin) {
+    s_in[t] = reinterpret_cast<const float2*>(arena + H.in[t]);
+    if (H.in_meta[t] < 0) {
+      s_f[t] = 1.f;
+    } else {
+      int m;
+      s_f[t] = scale_of_max(meta_m[(long long)H.in_meta[t] * B], &m);
+    }
+  }
+  __syncthreads();
+  const long long g = (long long)(blockIdx.x - H.blk0) * 256 + t;
+  float mx = 0.f;
+  if (g < (1ll << bits)) {
+    float2 a0 = make_float2(1.f, 0.f), a1 = make_float2(1.f, 0.f);
+    for (int j = 0; j < nin; ++j) {
+      long long idx = 0;
+      for (int i = 0; i < bits; ++i)
+        if ((g >> i) & 1ll) idx += s_str[j][i];
+      const float f = s_f[j];
+      if (H.sum) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(s_in[j] + idx));
+        const float2 x0 = make_float2(v.x * f, v.y * f), x1 = make_float2(v.z * f, v.w * f);
+        a0 = j ? cmul(a0, x0) : x0;
+        a1 = j ? cmul(a1, x1) : x1;
+      } else {
+        const float2 v = __ldg(s_in[j] + idx);
+        const float2 x = make_float2(v.x * f, v.y * f);
+        a0 = j ? cmul(a0, x) : x;
+      }
+    }
+    const float2 r = H.sum ? make_float2(a0.x + a1.x, a0.y + a1.y) : a0;
+    reinterpret_cast<float2*>(arena + H.out)[g] = r;
+    mx = fmaxf(fabsf(r.x), fabsf(r.y));
+  }
+  for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  if ((t & 31) == 0) s_red[t >> 5] = mx;
+  __syncthreads();
+  if (t == 0) {
+    float b = 0.f;
+    for (int w = 0; w < 8; ++w) b = fmaxf(b, s_red[w]);
+    if (b > 0.f) atomic_max_pos(&meta_m[(long long)H.out_meta * B], b);
+    if ((int)blockIdx.x == H.blk0) {
+      int e = 0;
+      for (int j = 0; j < nin; ++j) {
+        if (H.in_meta[j] < 0) continue;
+        const long long row = (long long)H.in_meta[j] * B;
+        int m;
+        scale_of_max(meta_m[row], &m);
+        e += meta_e[row] + m;
+      }
+      meta_e[(long long)H.out_meta * B] = e;
     }
   }
 }
@@ -825,6 +917,7 @@ struct Layout {
   int mode = 0, B = 1, item_bits = 0;
   std::vector<long long> off;   // element offset per tensor
   std::vector<char> dep;        // item-dependent per tensor
+  std::vector<int> hoist;       // per bucket: level (>= 1) of an early bucket (see hoist_levels), else 0
   long long arena_elems = 0;
   long long gemm_off = 0;        // element offset of the GEMM operand scratch inside the arena
   size_t hdr_off = 0, bits_off = 0, scalar_off = 0, res_off = 0, part_off = 0, meta_e_off = 0, meta_m_off = 0,
@@ -857,6 +950,42 @@ GemmShape gemm_shape(const tnq_plan& P, const FusedGroup& g, int items) {
   return s;
 }
 
+// Early buckets: a single (unfused) bucket whose result does not depend on
+// the item and whose inputs are gate tensors or results of early buckets
+// depends on nothing the batch computes otherwise. These run first, before
+// every other step, one launch per level (level = 1 + the highest level among
+// the producers of its inputs). Their results are given a lifetime from the
+// start of the batch, so no other tensor shares their memory meanwhile.
+std::vector<int> hoist_levels(const Program& prog, const std::vector<char>& dep) {
+  const int nb = (int)prog.buckets.size();
+  std::vector<int> lv(nb, 0);
+  for (int b = 0; b < nb; ++b) {
+    if (!prog.group_of.empty() && prog.group_of[b] >= 0) continue;
+    const PBucket& B = prog.buckets[b];
+    if (dep[B.output] || prog.tensors[B.output].rank() > HOIST_MAX_BITS || B.k > KMAX || B.k < 1) continue;
+    int l = 0;
+    bool ok = true;
+    for (int t : B.inputs) {
+      const int p = prog.tensors[t].producer;
+      if (p < 0) continue;  // gate tensor, written by the leaf kernel
+      if (lv[p] == 0) { ok = false; break; }
+      l = std::max(l, lv[p]);
+    }
+    if (ok) lv[b] = l + 1;
+  }
+  return lv;
+}
+
+// Lifetimes in bucket steps (a fused group's tensors live at its last bucket;
+// the results inside a group are never stored), early-bucket results from
+// the start of the batch.
+Liveness layout_liveness(const Program& prog, const std::vector<int>& hoist) {
+  Liveness LV = tensor_liveness(prog);
+  for (size_t b = 0; b < prog.buckets.size(); ++b)
+    if (hoist[b]) LV.lo[prog.buckets[b].output] = -1;
+  return LV;
+}
+
 Layout make_layout(const tnq_plan& P, int mode, int B) {
   const Program& prog = P.prog;
   Layout L;
@@ -867,9 +996,8 @@ Layout make_layout(const tnq_plan& P, int mode, int B) {
   L.off.assign(T, 0);
   L.dep.assign(T, 0);
   for (int t = 0; t < T; ++t) L.dep[t] = tensor_dep(prog.tensors[t], mode);
-  // lifetimes in bucket steps (a fused group's tensors live at its last bucket;
-  // the results inside a group are never stored)
-  const Liveness LV = tensor_liveness(prog);
+  L.hoist = hoist_levels(prog, L.dep);
+  const Liveness LV = layout_liveness(prog, L.hoist);
   const std::vector<int>& lo = LV.lo;
   const std::vector<int>& hi = LV.hi;
   std::vector<long long> size(T);
@@ -948,6 +1076,11 @@ struct ExecConfig {
   std::vector<double> step_flops;    // algorithmic flops of each step (all items; cost model of Section IV)
   std::vector<std::vector<int>> step_deps;  // earlier steps each step must wait for (concurrent launches)
   std::vector<int> step_stream;      // side stream of each step in a captured batch
+  std::vector<int> step_hoist;       // per step: level of an early bucket (runs in its level's launch), else 0
+  std::vector<HoistDev> hoist_dev;   // early buckets in level order (host copy)
+  std::vector<int> hoist_first;      // per level: first entry in hoist_dev (one past the last level at the end)
+  std::vector<int> hoist_blocks;     // per level: blocks of its launch
+  HoistDev* d_hoist = nullptr;
   void* ws = nullptr;                // workspace the graph was captured for
   cudaGraphExec_t exec = nullptr;
 };
@@ -963,6 +1096,7 @@ struct DeviceState {
       cudaFree(c->d_scalars);
       cudaFree(c->d_inout);
       cudaFree(c->d_finals);
+      cudaFree(c->d_hoist);
       delete c;
     }
   }
@@ -1315,6 +1449,10 @@ static bool build_steps(const tnq_plan& P, const Layout& L, ExecConfig& C) {
   C.ge.clear();
   C.step_bytes.clear();
   C.step_flops.clear();
+  C.step_hoist.clear();
+  C.hoist_dev.clear();
+  C.hoist_first.clear();
+  C.hoist_blocks.clear();
   auto tbytes = [&](int t) { return std::ldexp(8.0, prog.tensors[t].rank()) * (L.dep[t] ? L.B : 1); };
   auto bflops = [&](int bi) {
     const PBucket& b = prog.buckets[bi];
@@ -1329,6 +1467,7 @@ static bool build_steps(const tnq_plan& P, const Layout& L, ExecConfig& C) {
       if (!ok) { set_error("bucket too large for one launch"); return false; }
       C.steps.push_back({0, (int)C.kp.size()});
       C.step_group.push_back(-1);
+      C.step_hoist.push_back(L.hoist[bi]);
       C.kp.push_back(k);
       C.kshape.push_back({prog.buckets[bi].k, k.G > 8 ? 12 : 8});
       double by = tbytes(prog.buckets[bi].output);
@@ -1341,6 +1480,7 @@ static bool build_steps(const tnq_plan& P, const Layout& L, ExecConfig& C) {
       if (!gemm_params(P, L, prog.groups[gi], G, E)) return false;
       C.steps.push_back({2, (int)C.gb.size()});
       C.step_group.push_back(gi);
+      C.step_hoist.push_back(0);
       C.gb.push_back(G);
       C.ge.push_back(E);
       double by = tbytes(prog.groups[gi].output);
@@ -1356,6 +1496,7 @@ static bool build_steps(const tnq_plan& P, const Layout& L, ExecConfig& C) {
       if (!ok) { set_error("fused group does not fit one launch"); return false; }
       C.steps.push_back({1, (int)C.gp.size()});
       C.step_group.push_back(gi);
+      C.step_hoist.push_back(0);
       C.gp.push_back(g);
       C.gsmem.push_back(smem);
       double by = tbytes(prog.groups[gi].output);
@@ -1366,6 +1507,34 @@ static bool build_steps(const tnq_plan& P, const Layout& L, ExecConfig& C) {
       C.step_flops.push_back(fl);
     }
   }
+  // early buckets, level by level (program order within a level)
+  int levels = 0;
+  for (int h : C.step_hoist) levels = std::max(levels, h);
+  for (int l = 1; l <= levels; ++l) {
+    C.hoist_first.push_back((int)C.hoist_dev.size());
+    int blocks = 0;
+    for (size_t i = 0; i < C.steps.size(); ++i) {
+      if (C.step_hoist[i] != l) continue;
+      const KParams& k = C.kp[C.steps[i].second];
+      HoistDev h;
+      std::memset(&h, 0, sizeof(h));
+      h.out = (long long)reinterpret_cast<size_t>(k.out);
+      h.nin = C.kshape[C.steps[i].second].first;
+      h.bits = k.G;
+      h.sum = k.sum;
+      h.out_meta = k.out_meta;
+      h.blk0 = blocks;
+      for (int j = 0; j < h.nin; ++j) {
+        h.in[j] = (long long)reinterpret_cast<size_t>(k.in[j]);
+        h.in_meta[j] = k.in_meta[j];
+        for (int b = 0; b < k.G; ++b) h.stride[j][b] = k.stride[j][b];
+      }
+      blocks += (int)(((1ll << k.G) + 255) >> 8);
+      C.hoist_dev.push_back(h);
+    }
+    C.hoist_blocks.push_back(blocks);
+  }
+  C.hoist_first.push_back((int)C.hoist_dev.size());
   step_dependencies(P, L, C);
   return true;
 }
@@ -1380,8 +1549,22 @@ static std::string validate_config(const tnq_plan& P, int mode, int B) {
   C.L = L;
   if (!build_steps(P, L, C)) return std::string("build_steps failed: ") + tnq_last_error();
   const Program& prog = P.prog;
-  const Liveness LV = tensor_liveness(prog);
+  const Liveness LV = layout_liveness(prog, L.hoist);
   auto alloc = [&](int t) { return ((long long)1 << prog.tensors[t].rank()) * (L.dep[t] ? B : 1); };
+  for (size_t i = 0; i < C.steps.size(); ++i) {  // early buckets: item-invariant, inputs ready before their level
+    if (!C.step_hoist[i]) continue;
+    const KParams& k = C.kp[C.steps[i].second];
+    if (k.G != k.out_bits || k.G > HOIST_MAX_BITS) return "early bucket shape";
+    for (int j = 0; j < C.kshape[C.steps[i].second].first; ++j)
+      if (k.in_dep[j]) return "early bucket reads an item-dependent tensor";
+  }
+  for (size_t bi = 0; bi < prog.buckets.size(); ++bi) {
+    if (!L.hoist[bi]) continue;
+    for (int t : prog.buckets[bi].inputs) {
+      const int p = prog.tensors[t].producer;
+      if (p >= 0 && (!L.hoist[p] || L.hoist[p] >= L.hoist[bi])) return "early bucket input not ready";
+    }
+  }
   auto off_of = [&](const void* p) { return (long long)((size_t)p / 8); };
   int single = 0;
   for (size_t bi = 0; bi < prog.buckets.size(); ++bi) {
@@ -1558,6 +1741,16 @@ static tnq_status build_config(const tnq_plan& P, int mode, int B, ExecConfig** 
     delete C;
     return TNQ_EUNSUPPORTED;
   }
+  if ((e = up((void**)&C->d_hoist, C->hoist_dev.data(), C->hoist_dev.size() * sizeof(HoistDev))) != cudaSuccess) {
+    set_error(std::string("uploading plan tables: ") + cudaGetErrorString(e));
+    cudaFree(C->d_leaves);
+    cudaFree(C->d_scalars);
+    cudaFree(C->d_inout);
+    cudaFree(C->d_finals);
+    cudaFree(C->d_hoist);
+    delete C;
+    return TNQ_ECUDA;
+  }
   *out = C;
   return TNQ_OK;
 }
@@ -1656,8 +1849,14 @@ static void enqueue_batch(const tnq_plan& P, ExecConfig& C, char* ws, cudaStream
   }
   k_scalar_init<<<(B + 127) / 128, 128, 0, s>>>(C.d_scalars, C.n_scalars, C.d_inout, C.n_inout, hdr, bits, scal, B);
   int* status = reinterpret_cast<int*>(ws + L.status_off);
+  // early buckets first, one launch per level; their steps launch nothing below
+  for (size_t l = 0; l + 1 < C.hoist_first.size(); ++l)
+    k_bucket_level<<<(unsigned)C.hoist_blocks[l], 256, 0, s>>>(C.d_hoist + C.hoist_first[l],
+                                                                 C.hoist_first[l + 1] - C.hoist_first[l],
+                                                                 reinterpret_cast<char*>(arena), me, mm, B);
   if (!side) {
-    for (size_t i = 0; i < C.steps.size(); ++i) launch_step(C, (int)i, arena, me, mm, status, s);
+    for (size_t i = 0; i < C.steps.size(); ++i)
+      if (!C.step_hoist[i]) launch_step(C, (int)i, arena, me, mm, status, s);
   } else {
     cudaEventRecord(side->fork, s);
     for (int k = 0; k < N_SIDE_STREAMS; ++k) cudaStreamWaitEvent(side->st[k], side->fork, 0);
@@ -1665,7 +1864,7 @@ static void enqueue_batch(const tnq_plan& P, ExecConfig& C, char* ws, cudaStream
       const int k = C.step_stream[i];
       for (int j : C.step_deps[i])
         if (C.step_stream[j] != k) cudaStreamWaitEvent(side->st[k], side->done[j], 0);
-      launch_step(C, (int)i, arena, me, mm, status, side->st[k]);
+      if (!C.step_hoist[i]) launch_step(C, (int)i, arena, me, mm, status, side->st[k]);
       cudaEventRecord(side->done[i], side->st[k]);
     }
     for (int k = 0; k < N_SIDE_STREAMS; ++k) {
@@ -2159,9 +2358,17 @@ int tnq_internal_launches_per_batch(const tnq_plan* plan) {
   if (!plan) return 0;
   int n = 0;
   const auto& prog = plan->prog;
-  for (size_t b = 0; b < prog.buckets.size(); ++b)
-    n += (prog.group_of.empty() || prog.group_of[b] < 0 || prog.groups[prog.group_of[b]].buckets.back() == (int)b);
-  return n + 4;
+  std::vector<char> dep(prog.tensors.size());
+  for (size_t t = 0; t < dep.size(); ++t) dep[t] = tensor_dep(prog.tensors[t], 0);
+  const std::vector<int> hoist = hoist_levels(prog, dep);  // single-bitstring calls
+  int levels = 0;
+  for (size_t b = 0; b < prog.buckets.size(); ++b) {
+    levels = std::max(levels, hoist[b]);
+    const int gi = prog.group_of.empty() ? -1 : prog.group_of[b];
+    if (gi < 0) n += !hoist[b];
+    else if (prog.groups[gi].buckets.back() == (int)b) n += prog.groups[gi].gemm ? 3 : 1;  // GEMM: 2 packs + MMA
+  }
+  return n + levels + 4;  // + leaf, scalar, final and slice-sum kernels
 }
 
 size_t tnq_plan_workspace_bytes(const tnq_plan* plan, uint32_t batch) {
@@ -2392,6 +2599,9 @@ tnq_status tnq_contract_sliced_noalloc(const tnq_plan* plan, const uint8_t* bits
   std::vector<FinalDev> finals;
   for (int t : prog.finals) finals.push_back(FinalDev{C.L.off[t], t, (int)C.L.dep[t]});
   if (!build_steps(*plan, C.L, C)) return TNQ_EUNSUPPORTED;
+  // the early buckets run as ordinary steps here (no level table in the scratch)
+  std::fill(C.step_hoist.begin(), C.step_hoist.end(), 0);
+  C.hoist_first.clear();
   char* base = reinterpret_cast<char*>(scratch);
   size_t o = 0;
   C.d_leaves = reinterpret_cast<LeafDev*>(base + o);
