@@ -409,6 +409,8 @@ constexpr int GTPB = 1 << GTB;      // threads per k_group block
 constexpr int GT_MID = 16;          // table entries of bits 4..GTB-1 start here
 constexpr int GT_HI = GT_MID + (1 << (GTB - 4));  // ... and of bits GTB..GL_MAX-2 here
 constexpr int TABW = GT_HI + (1 << (GL_MAX - 1 - GTB));
+static_assert(GTB >= 6, "the stage-buffer swizzle assumes >= 64 threads per k_group block");
+constexpr int TAIL_MIN = 2, TAIL_MAX = 4;  // stages after the first that group_tail runs in registers
 constexpr int GH_MAX = 32;  // tile bits (output variables outside the block; a bag of 2^40 entries has < 32)
 constexpr int PAIR_MAX = GIN_MAX + GM_MAX - 1;  // varying (stage, operand) pairs: at most every input of every stage
 constexpr int GROUP_SMEM_BYTES = (1 << (GL_MAX - 1)) * 3 / 2 * (int)sizeof(float2);  // regions A + B
@@ -441,9 +443,20 @@ struct GParams {
   int out_cstride[GL_MAX];
   int n_st, n_gin, n_h, out_meta, out_dep, B;
   int n_pairs;
+  int tail;                    // > 0: stages 1..tail run in registers (group_tail) after stage 0
   int* meta_e;
   unsigned* meta_m;
 };
+
+// Stage buffers in shared memory are stored swizzled: complex entry o sits at
+// swz(o), which keeps (u = 0, u = 1) pairs together and permutes the 16-byte
+// pairs within each group of 8 (pair p at p ^ ((p >> 3) & 7)). Threads that
+// read the pairs of consecutive subtrees (group_tail) then hit distinct banks;
+// for entries t + GTPB it the swizzle is swz(t) + GTPB it (GTPB >= 64).
+__device__ __forceinline__ int swz(int o) {
+  const int p = o >> 1;
+  return ((p ^ ((p >> 3) & 7)) << 1) | (o & 1);
+}
 
 // One stage of a fused group. Inputs n_var.. do not vary over the block's
 // local bits: their (u=0, u=1) pairs, times the stage's power-of-two scales,
@@ -478,6 +491,10 @@ __device__ __forceinline__ void group_stage(const GSt& S, int t, const float2* p
     ptr[j] = src < 0 ? prev : s_ptr[src];
     lo[j] = tab[j][t & 15] + tab[j][GT_MID + (t >> 4)];
   }
+  // operand j's pair at local offset o (the previous stage's buffer is swizzled)
+  auto at = [&](int j, int o) -> float4 {
+    return *reinterpret_cast<const float4*>(ptr[j] + (S.src[j] < 0 ? swz(o) : o));
+  };
 #pragma unroll 2
   for (int it = 0; it < n_hi; ++it) {
     const int c = t + (it << GTB);
@@ -485,19 +502,19 @@ __device__ __forceinline__ void group_stage(const GSt& S, int t, const float2* p
       float2 p0 = k0, p1 = k1;
       constexpr int J0 = K ? 0 : 1;
       if (!K) {
-        const float4 v = *reinterpret_cast<const float4*>(ptr[0] + lo[0] + tab[0][GT_HI + it]);
+        const float4 v = at(0, lo[0] + tab[0][GT_HI + it]);
         p0 = make_float2(v.x, v.y);
         p1 = make_float2(v.z, v.w);
       }
 #pragma unroll
       for (int j = J0; j < NV - 1; ++j) {
-        const float4 v = *reinterpret_cast<const float4*>(ptr[j] + lo[j] + tab[j][GT_HI + it]);
+        const float4 v = at(j, lo[j] + tab[j][GT_HI + it]);
         p0 = cmul(p0, make_float2(v.x, v.y));
         p1 = cmul(p1, make_float2(v.z, v.w));
       }
       float2 r;
       if (NV >= 1 && (K || NV >= 2)) {
-        const float4 v = *reinterpret_cast<const float4*>(ptr[NV - 1] + lo[NV - 1] + tab[NV - 1][GT_HI + it]);
+        const float4 v = at(NV - 1, lo[NV - 1] + tab[NV - 1][GT_HI + it]);
         float rx = p0.x * v.x;
         rx = fmaf(-p0.y, v.y, rx);
         rx = fmaf(p1.x, v.z, rx);
@@ -515,7 +532,7 @@ __device__ __forceinline__ void group_stage(const GSt& S, int t, const float2* p
         out[out_base + out_lo + s_out_hi[it]] = r;
         *tmax = fmaxf(*tmax, fmaxf(fabsf(r.x), fabsf(r.y)));
       } else {
-        cur[c] = r;
+        cur[swz(c)] = r;
       }
     }
   }
@@ -562,7 +579,7 @@ __device__ __forceinline__ void stage_pf(const GSt& S, int t, const float2* prev
 #pragma unroll
   for (int j = 0; j < NV; ++j) {
     if (PD && j == 0) {
-      base[0] = reinterpret_cast<const float4*>(prev) + t;
+      base[0] = reinterpret_cast<const float4*>(prev) + (t ^ ((t >> 3) & 7));  // swizzled pair t
 #pragma unroll
       for (int u = 0; u < U; ++u) ti[0][u] = u * GTPB;
     } else {
@@ -636,7 +653,7 @@ __device__ __forceinline__ void stage_pf(const GSt& S, int t, const float2* prev
           dst[oh + so[u]] = r;
           *tmax = fmaxf(*tmax, fmaxf(fabsf(r.x), fabsf(r.y)));
         } else {
-          cur[t + (it0 + u) * GTPB] = r;
+          cur[swz(t) + (it0 + u) * GTPB] = r;
         }
       }
     }
@@ -686,6 +703,81 @@ __device__ __forceinline__ void run_stage(bool with_k, const GSt& S, int t, cons
   else
     group_stage<(NV > 0 ? NV : 1), false>(S, t, prev, cur, out, last, s_ptr, F, tab, s_out_hi, out_base, out_lo,
                                           tmax);
+}
+
+// Stages 1..M of a group in registers. Every one of them reads the previous
+// stage densely (operand 0, entry c at 2c: the pair over u_s) and has at most
+// one other varying operand; so the last stage's entry cm depends on the
+// previous stages only through the 2^M stage-0 entries cm 2^M .. cm 2^M +
+// 2^M - 1, a binary tree: stage s entry cm 2^(M-s) + k is the sum over u of
+// stage s-1 entries 2k + u (relative to the subtree) times the stage's other
+// operands. A thread evaluates whole subtrees: one read of its stage-0 pairs,
+// no barrier and no shared-memory stage between. K pairs as in stage_pf.
+template <int M>
+__device__ __forceinline__ void group_tail(const GParams& P, int t, const float2* buf, const float2* const* s_ptr,
+                                           const float* s_F, const int (*s_tab)[TABW], const int* s_out_hi,
+                                           long long out_base, int out_lo, float* tmax) {
+  float2 K0[M], K1[M];
+  const float2* op[M];
+  int row[M];
+  bool two[M];
+#pragma unroll
+  for (int s = 0; s < M; ++s) {
+    const GSt& S = P.st[s + 1];
+    float2 k0 = make_float2(s_F[s + 1], 0.f), k1 = k0;
+    for (int j = S.n_var; j < S.n_in; ++j) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(s_ptr[S.src[j]]));
+      k0 = cmul(k0, make_float2(v.x, v.y));
+      k1 = cmul(k1, make_float2(v.z, v.w));
+    }
+    K0[s] = k0;
+    K1[s] = k1;
+    two[s] = S.n_var > 1;
+    op[s] = two[s] ? s_ptr[S.src[1]] : nullptr;
+    row[s] = S.q0 + 1;
+  }
+  const int nb_last = P.st[M].nbits;
+  const int n_fin = nb_last > GTB ? 1 << (nb_last - GTB) : 1;
+  const float4* b4 = reinterpret_cast<const float4*>(buf);
+  float2* dst = P.out + out_base + out_lo;
+  for (int i = 0; i < n_fin; ++i) {
+    const int cm = t + GTPB * i;
+    if (nb_last < GTB && cm >= (1 << nb_last)) break;
+    float2 x[1 << M];
+#pragma unroll
+    for (int q = 0; q < (1 << (M - 1)); ++q) {
+      const int p = (cm << (M - 1)) + q;
+      const float4 v = b4[p ^ ((p >> 3) & 7)];
+      x[2 * q] = make_float2(v.x, v.y);
+      x[2 * q + 1] = make_float2(v.z, v.w);
+    }
+#pragma unroll
+    for (int s = 0; s < M; ++s) {
+#pragma unroll
+      for (int k = 0; k < (1 << (M - 1 - s)); ++k) {
+        float2 a0 = x[2 * k], a1 = x[2 * k + 1];
+        if (two[s]) {
+          const int c = (cm << (M - 1 - s)) + k;
+          const int* tr = s_tab[row[s]];
+          const int off = tr[c & 15] + tr[GT_MID + ((c >> 4) & ((1 << (GTB - 4)) - 1))] + tr[GT_HI + (c >> GTB)];
+          const float4 w = __ldg(reinterpret_cast<const float4*>(op[s] + off));
+          a0 = cmul(a0, make_float2(w.x, w.y));
+          a1 = cmul(a1, make_float2(w.z, w.w));
+        }
+        float rx = K0[s].x * a0.x;  // K0 a0 + K1 a1
+        rx = fmaf(-K0[s].y, a0.y, rx);
+        rx = fmaf(K1[s].x, a1.x, rx);
+        rx = fmaf(-K1[s].y, a1.y, rx);
+        float ry = K0[s].x * a0.y;
+        ry = fmaf(K0[s].y, a0.x, ry);
+        ry = fmaf(K1[s].x, a1.y, ry);
+        ry = fmaf(K1[s].y, a1.x, ry);
+        x[k] = make_float2(rx, ry);
+      }
+    }
+    dst[s_out_hi[i]] = x[0];
+    *tmax = fmaxf(*tmax, fmaxf(fabsf(x[0].x), fabsf(x[0].y)));
+  }
 }
 
 // Persistent fused-group kernel: every block builds the stage tables once,
@@ -794,7 +886,8 @@ __global__ void __launch_bounds__(GTPB, 4) k_group(const __grid_constant__ GPara
     // least one bit fewer than the stage before, so B needs half of A
     float2* prev = g_stage + buf_elems;
     float2* cur = g_stage;
-    for (int s = 0; s < P.n_st; ++s) {
+    const int n_run = P.tail ? 1 : P.n_st;  // stages run in shared memory
+    for (int s = 0; s < n_run; ++s) {
       const GSt& S = P.st[s];
       const bool last = (s == P.n_st - 1);
       const bool with_k = S.n_in > S.n_var;
@@ -829,6 +922,13 @@ __global__ void __launch_bounds__(GTPB, 4) k_group(const __grid_constant__ GPara
       float2* tmp = prev;
       prev = cur;
       cur = tmp;
+    }
+    switch (P.tail) {  // stage 0's buffer is now prev
+      case 1: group_tail<1>(P, t, prev, s_ptr, s_F, s_tab, s_out_hi, s_out_base, out_lo, &tmax); break;
+      case 2: group_tail<2>(P, t, prev, s_ptr, s_F, s_tab, s_out_hi, s_out_base, out_lo, &tmax); break;
+      case 3: group_tail<3>(P, t, prev, s_ptr, s_F, s_tab, s_out_hi, s_out_base, out_lo, &tmax); break;
+      case 4: group_tail<4>(P, t, prev, s_ptr, s_F, s_tab, s_out_hi, s_out_base, out_lo, &tmax); break;
+      default: break;
     }
     if (h == 0 && t == 0) {
       int e = 0;
@@ -1284,6 +1384,19 @@ static GParams group_gparams(const tnq_plan& P, const Layout& L, const FusedGrou
     for (int b = 0; d && b < S.nbits; ++b) d = S.cstride[0][b] == (2 << b);
     S.pd = d ? 1 : 0;
   }
+  // stages 1.. in registers (group_tail) when each reads the previous one
+  // densely, has at most one other varying operand (from memory) and one bit
+  // fewer than the stage before
+  {
+    bool ok = G.n_st - 1 >= TAIL_MIN && G.n_st - 1 <= TAIL_MAX;
+    for (int s = 1; ok && s < G.n_st; ++s) {
+      const GSt& S = G.st[s];
+      ok = S.pd && S.n_var >= 1 && S.n_var <= 2 && (S.n_var < 2 || S.src[1] >= 0) &&
+           S.nbits == G.st[s - 1].nbits - 1;
+      for (int j = S.n_var; ok && j < S.n_in; ++j) ok = S.src[j] >= 0;
+    }
+    G.tail = ok ? G.n_st - 1 : 0;
+  }
   const auto& last = sv[G.n_st - 1];
   for (size_t b = 0; b < last.size(); ++b) {
     const int p = index_in(o.vars, last[b]);
@@ -1291,7 +1404,8 @@ static GParams group_gparams(const tnq_plan& P, const Layout& L, const FusedGrou
     G.out_cstride[b] = 1 << p;
   }
   if (last.size() + g.tile_vars.size() != o.vars.size()) return G;
-  *smem = GROUP_SMEM_BYTES;
+  // with the register tail only stage 0's buffer (region A) is used
+  *smem = G.tail ? (int)sizeof(float2) << G.st[0].nbits : GROUP_SMEM_BYTES;
   (void)maxbits;
   *ok = true;
   return G;
