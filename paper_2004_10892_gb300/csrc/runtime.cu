@@ -693,6 +693,23 @@ __device__ __forceinline__ bool stage_pf_nhi(const GSt& S, int t, const float2* 
 #undef TNQ_PF
 }
 
+// Stage 0 of a chain with a register tail: operands from memory, never the
+// group's last stage.
+template <int NV, bool K>
+__device__ __forceinline__ void stage0_pf(const GSt& S, int t, float2* cur, const float2* const* s_ptr, float F,
+                                          const int (*tab)[TABW]) {
+#define TNQ_PF0(n) stage_pf<NV, K, n, false, false>(S, t, nullptr, cur, nullptr, s_ptr, F, tab, nullptr, 0, 0, nullptr)
+  switch (S.nbits - GTB) {
+    case 5: TNQ_PF0(32); break;
+    case 4: TNQ_PF0(16); break;
+    case 3: TNQ_PF0(8); break;
+    case 2: TNQ_PF0(4); break;
+    case 1: TNQ_PF0(2); break;
+    default: TNQ_PF0(1); break;
+  }
+#undef TNQ_PF0
+}
+
 template <int NV>
 __device__ __forceinline__ void run_stage(bool with_k, const GSt& S, int t, const float2* prev, float2* cur,
                                           float2* out, bool last, const float2* const* s_ptr, float F,
@@ -781,8 +798,11 @@ __device__ __forceinline__ void group_tail(const GParams& P, int t, const float2
 }
 
 // Persistent fused-group kernel: every block builds the stage tables once,
+// (TK: chains with a register tail -- stage 0 in shared memory, then
+// group_tail; fewer code paths, so five blocks fit per SM)
 // then loops over tiles (item, H assignment) tile = blockIdx.x + k*gridDim.x.
-__global__ void __launch_bounds__(GTPB, 4) k_group(const __grid_constant__ GParams P, long long n_tiles) {
+template <bool TK>
+__global__ void __launch_bounds__(GTPB, TK ? 5 : 4) k_group(const __grid_constant__ GParams P, long long n_tiles) {
   extern __shared__ float2 g_stage[];  // stage regions A (2^(GL_MAX-1) entries) and B (half of A)
   __shared__ int s_hstr[GIN_MAX + 1][GH_MAX];  // row GIN_MAX: the output (within-item offsets < 2^31)
   __shared__ const float2* s_ptr[GIN_MAX];
@@ -886,7 +906,26 @@ __global__ void __launch_bounds__(GTPB, 4) k_group(const __grid_constant__ GPara
     // least one bit fewer than the stage before, so B needs half of A
     float2* prev = g_stage + buf_elems;
     float2* cur = g_stage;
-    const int n_run = P.tail ? 1 : P.n_st;  // stages run in shared memory
+    if constexpr (TK) {
+      const GSt& S = P.st[0];
+      const bool with_k = S.n_in > S.n_var;
+      const float F = s_F[0];
+      switch (S.n_var * 2 + (with_k ? 1 : 0)) {
+        case 2: stage0_pf<1, false>(S, t, cur, s_ptr, F, s_tab + S.q0); break;
+        case 3: stage0_pf<1, true>(S, t, cur, s_ptr, F, s_tab + S.q0); break;
+        case 4: stage0_pf<2, false>(S, t, cur, s_ptr, F, s_tab + S.q0); break;
+        case 5: stage0_pf<2, true>(S, t, cur, s_ptr, F, s_tab + S.q0); break;
+        case 6: stage0_pf<3, false>(S, t, cur, s_ptr, F, s_tab + S.q0); break;
+        default: stage0_pf<3, true>(S, t, cur, s_ptr, F, s_tab + S.q0); break;
+      }
+      __syncthreads();
+      switch (P.tail) {  // stage 0's buffer is region A
+        case 2: group_tail<2>(P, t, cur, s_ptr, s_F, s_tab, s_out_hi, s_out_base, out_lo, &tmax); break;
+        case 3: group_tail<3>(P, t, cur, s_ptr, s_F, s_tab, s_out_hi, s_out_base, out_lo, &tmax); break;
+        default: group_tail<4>(P, t, cur, s_ptr, s_F, s_tab, s_out_hi, s_out_base, out_lo, &tmax); break;
+      }
+    }
+    const int n_run = TK ? 0 : P.n_st;  // stages run in shared memory
     for (int s = 0; s < n_run; ++s) {
       const GSt& S = P.st[s];
       const bool last = (s == P.n_st - 1);
@@ -922,13 +961,6 @@ __global__ void __launch_bounds__(GTPB, 4) k_group(const __grid_constant__ GPara
       float2* tmp = prev;
       prev = cur;
       cur = tmp;
-    }
-    switch (P.tail) {  // stage 0's buffer is now prev
-      case 1: group_tail<1>(P, t, prev, s_ptr, s_F, s_tab, s_out_hi, s_out_base, out_lo, &tmax); break;
-      case 2: group_tail<2>(P, t, prev, s_ptr, s_F, s_tab, s_out_hi, s_out_base, out_lo, &tmax); break;
-      case 3: group_tail<3>(P, t, prev, s_ptr, s_F, s_tab, s_out_hi, s_out_base, out_lo, &tmax); break;
-      case 4: group_tail<4>(P, t, prev, s_ptr, s_F, s_tab, s_out_hi, s_out_base, out_lo, &tmax); break;
-      default: break;
     }
     if (h == 0 && t == 0) {
       int e = 0;
@@ -1167,6 +1199,7 @@ struct ExecConfig {
   std::vector<std::pair<int, int>> kshape;  // (n_in, LT) per single-bucket step
   std::vector<GParams> gp;           // per fused-group step
   std::vector<int> gsmem;            // dynamic shared memory bytes per fused-group step
+  std::vector<int> ggrid;            // persistent blocks per fused-group step (SMs x resident blocks at its gsmem)
   int group_grid = 152 * 4;          // persistent blocks of k_group (SMs x resident blocks)
   std::vector<GemmBucketArgs> gb;    // per GEMM step (pointers are arena offsets)
   std::vector<GemmEpilogue> ge;
@@ -1388,7 +1421,9 @@ static GParams group_gparams(const tnq_plan& P, const Layout& L, const FusedGrou
   // densely, has at most one other varying operand (from memory) and one bit
   // fewer than the stage before
   {
-    bool ok = G.n_st - 1 >= TAIL_MIN && G.n_st - 1 <= TAIL_MAX;
+    bool ok = G.n_st - 1 >= TAIL_MIN && G.n_st - 1 <= TAIL_MAX && G.st[0].n_var >= 1 && G.st[0].n_var <= 3 &&
+              G.st[0].nbits > 0;
+    for (int j = 0; ok && j < G.st[0].n_in; ++j) ok = G.st[0].src[j] >= 0;
     for (int s = 1; ok && s < G.n_st; ++s) {
       const GSt& S = G.st[s];
       ok = S.pd && S.n_var >= 1 && S.n_var <= 2 && (S.n_var < 2 || S.src[1] >= 0) &&
@@ -1798,14 +1833,18 @@ static std::string validate_config(const tnq_plan& P, int mode, int B) {
 }
 
 static cudaError_t allow_group_smem() {
-  return cudaFuncSetAttribute(k_group, cudaFuncAttributeMaxDynamicSharedMemorySize, GROUP_SMEM_BYTES);
+  const cudaError_t e = cudaFuncSetAttribute(k_group<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             GROUP_SMEM_BYTES);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_group<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, GROUP_SMEM_BYTES);
 }
 
-static tnq_status group_grid_size(int* out) {
+static tnq_status group_grid_size(int* out, int smem = GROUP_SMEM_BYTES, bool tail = false) {
   int dev = 0, sms = 0, per_sm = 0;
   CU(cudaGetDevice(&dev));
   CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_group, GTPB, GROUP_SMEM_BYTES));
+  if (tail) CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_group<true>, GTPB, smem));
+  else CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_group<false>, GTPB, smem));
   *out = std::max(1, sms * std::max(1, per_sm));
   return TNQ_OK;
 }
@@ -1854,6 +1893,18 @@ static tnq_status build_config(const tnq_plan& P, int mode, int B, ExecConfig** 
     cudaFree(C->d_finals);
     delete C;
     return TNQ_EUNSUPPORTED;
+  }
+  for (size_t i = 0; i < C->gsmem.size(); ++i) {  // chains with a register tail: more blocks may fit
+    int g = 0;
+    if ((gst = group_grid_size(&g, C->gsmem[i], C->gp[i].tail > 0)) != TNQ_OK) {
+      cudaFree(C->d_leaves);
+      cudaFree(C->d_scalars);
+      cudaFree(C->d_inout);
+      cudaFree(C->d_finals);
+      delete C;
+      return gst;
+    }
+    C->ggrid.push_back(g);
   }
   if ((e = up((void**)&C->d_hoist, C->hoist_dev.data(), C->hoist_dev.size() * sizeof(HoistDev))) != cudaSuccess) {
     set_error(std::string("uploading plan tables: ") + cudaGetErrorString(e));
@@ -1928,8 +1979,10 @@ static void launch_step(const ExecConfig& C, int i, float2* arena, int* me, unsi
     g.meta_e = me;
     g.meta_m = mm;
     const long long tiles = (g.out_dep ? (long long)g.B : 1ll) << g.n_h;
-    const long long grid = std::min<long long>(tiles, (long long)C.group_grid);
-    k_group<<<(unsigned)grid, GTPB, C.gsmem[st.second], s>>>(g, tiles);
+    const long long grid =
+        std::min<long long>(tiles, (long long)(C.ggrid.empty() ? C.group_grid : C.ggrid[st.second]));
+    if (g.tail) k_group<true><<<(unsigned)grid, GTPB, C.gsmem[st.second], s>>>(g, tiles);
+    else k_group<false><<<(unsigned)grid, GTPB, C.gsmem[st.second], s>>>(g, tiles);
   }
 }
 
