@@ -516,9 +516,14 @@ __global__ void k_gemm_pack(const GemmBucketArgs g, int side) {
     }
   }
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const long long r = i % rows;
-    const int kc = (int)((i / rows) % kch);
-    const long long bi = i / (rows * kch);
+    // 8 consecutive threads: the 8 rows of one core matrix (one 128-byte
+    // store each); then the next K chunks of the same rows (contiguous reads
+    // when K is the operand's lowest dimension)
+    const long long q = i >> 3;
+    const int kc = (int)(q % kch);
+    const long long r8 = rows >> 3;
+    const long long r = ((q / kch) % r8) * 8 + (i & 7);
+    const long long bi = q / (kch * r8);
     const long long item = bi >> g.ns, sidx = bi & ((1ll << g.ns) - 1);
     const int k0 = kc * CH;
     float re[CH], im[CH];
