@@ -102,8 +102,8 @@ class ClockSampler:
 # bytes_one_slice x B / k_group launches per batch (traffic scales with the
 # slices of a batch; item-invariant operands are read once per batch, so this
 # slightly overstates it).
-MEASURED_TRAFFIC = {"k_group": {"source_sha1": "1a6dc9893f59ebe531c0a4a5ef191c1096dfdf67",
-                                "bytes_one_slice": 105188352.0, "launches": 12,
+MEASURED_TRAFFIC = {"k_group": {"source_sha1": "f5f103d8ceefaef549520d9a5103b75d02250fbc",
+                                "bytes_one_slice": 104181248.0, "launches": 12,
                                 "capture": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:k_group "
                                            "on a one-slice batch of the tuned default plan (12 launches)"}}
 
