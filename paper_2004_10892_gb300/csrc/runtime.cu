@@ -2211,6 +2211,21 @@ int tnq_internal_step_kinds(const tnq_plan* plan, int mode, uint32_t batch, int3
   return 0;
 }
 
+// Internal hook (not in include/tnq.h; host only): for every fused-chain step
+// of configuration (mode, batch), in program order, the number of its later
+// stages that run as register subtrees (0: all stages in shared memory).
+int tnq_internal_group_tails(const tnq_plan* plan, int mode, uint32_t batch, int32_t* tails, int cap,
+                             int32_t* out_n) {
+  if (!plan || !out_n) return 1;
+  ExecConfig C;
+  C.L = make_layout(*plan, mode, (int)batch);
+  if (!build_steps(*plan, C.L, C)) return 1;
+  *out_n = (int32_t)C.gp.size();
+  if ((int)C.gp.size() > cap) return 1;
+  for (size_t i = 0; i < C.gp.size(); ++i) tails[i] = C.gp[i].tail;
+  return 0;
+}
+
 // Internal hook (not in include/tnq.h; host only): the concurrency structure of
 // configuration (mode, batch) for checking it on the host. Per step: its side
 // stream, the tensor it writes, up to 16 tensors it reads (-1 past the end) and

@@ -271,3 +271,29 @@ def test_early_buckets_of_the_7x7_plan(tnq_lib):
     per_step = len(steps) + 2 * steps.count(2) + 4  # GEMM steps launch two packs and the MMA
     launches = L.tnq_internal_launches_per_batch(plan.handle)
     assert 0 < launches < per_step - 100, (launches, per_step)
+
+
+def test_parity_plans_cover_every_register_tail(tnq_lib):
+    """Host-only: the fused-chain plans of the GPU parity tests (small grids at
+    fuse_min_rank 1/4/8, the 6x6 plans) contain chains whose later stages run as
+    register subtrees of every depth (2, 3, 4) and chains that stay in shared
+    memory, so the parity tests exercise both kernel instantiations."""
+    L = tnq_lib.lib()
+    f = L.tnq_internal_group_tails
+    P = ctypes.POINTER
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32, P(ctypes.c_int32), ctypes.c_int, P(ctypes.c_int32)]
+    seen = set()
+    plans = []
+    for seed, (rows, cols, cyc, p) in enumerate([(4, 4, 16, 2), (5, 5, 20, 3), (4, 5, 24, 4)]):
+        for fuse in (1, 4, 8):
+            plans.append(tnq_lib.Plan(I.random_grid_circuit(rows, cols, cyc, 20 + seed), min_p=p, max_p=p,
+                                      fuse_min_rank=fuse))
+    plans.append(tnq_lib.Plan(I.random_grid_circuit(6, 6, 24, 0), max_bag_log2=24, min_p=5, max_p=5))
+    buf = (ctypes.c_int32 * 256)()
+    n = ctypes.c_int32()
+    for plan in plans:
+        for mode in (0, 1):
+            assert f(plan.handle, mode, 8, buf, 256, ctypes.byref(n)) == 0
+            seen.update(buf[i] for i in range(n.value))
+    assert {0, 2, 3, 4} <= seen, seen
+    assert seen <= {0, 2, 3, 4}, seen  # depth 1 is not used (shared-memory stage instead)
