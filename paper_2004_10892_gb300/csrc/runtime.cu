@@ -728,8 +728,9 @@ __device__ __forceinline__ void run_stage(bool with_k, const GSt& S, int t, cons
 // previous stages only through the 2^M stage-0 entries cm 2^M .. cm 2^M +
 // 2^M - 1, a binary tree: stage s entry cm 2^(M-s) + k is the sum over u of
 // stage s-1 entries 2k + u (relative to the subtree) times the stage's other
-// operands. A thread evaluates whole subtrees: one read of its stage-0 pairs,
-// no barrier and no shared-memory stage between. K pairs as in stage_pf.
+// operands (each stage one elimination step of Eq. 2). A thread evaluates
+// whole subtrees: one read of its stage-0 pairs, no barrier and no
+// shared-memory stage between. K pairs as in stage_pf.
 template <int M>
 __device__ __forceinline__ void group_tail(const GParams& P, int t, const float2* buf, const float2* const* s_ptr,
                                            const float* s_F, const int (*s_tab)[TABW], const int* s_out_hi,
