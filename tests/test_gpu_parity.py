@@ -204,6 +204,30 @@ def test_7x7_full_size_sampled_slices(cuda, tnq_lib, oracle_lib):
     assert abs(per.sum() - amp) <= 1e-12 * np.abs(per).sum()
 
 
+@pytest.mark.slow
+def test_7x7_bench_configuration_sampled_slices(cuda, tnq_lib, oracle_lib):
+    """The benchmark's own configuration at full size: 7x7 depth 1+32+1, order
+    recomputed after every deletion, best of 32 randomised greedy orders (p = 5),
+    GEMM-shaped chains in 3xBF16, autotuned, all 32 slices in one batch. Two
+    slices against the oracle; the slice sum equals the amplitude."""
+    import torch
+
+    circ = I.random_grid_circuit(7, 7, 32, 0)
+    bits = I.random_bitstring(49, 0)
+    plan = tnq_lib.Plan(circ, max_bag_log2=28, max_p=40, precision=1, gemm_min_k_log2=4, reorder_every=1,
+                        order_trials=32, fuse_min_rank=12)
+    inf = plan.info()
+    assert inf["max_bag"] <= 28 and inf["n_gemm_buckets"] > 0
+    n_sl = inf["n_slices"]
+    ws = torch.empty(plan.workspace_bytes(n_sl), dtype=torch.uint8, device="cuda")
+    plan.autotune(bits, workspace=ws, max_batch=n_sl)
+    amp, per = tnq_lib.contract_sliced(plan, bits, 0, n_sl, workspace=ws, max_batch=n_sl, per_slice=True)
+    for s in (0, n_sl - 1):
+        r = oracle_lib.contract(circ, bits, order=plan.order(), mu=plan.sliced(), slices=(s, s + 1))
+        assert abs(per[s] - r) / abs(r) < SPLIT_TOL, (s, per[s], r)
+    assert abs(per.sum() - amp) <= 1e-12 * np.abs(per).sum()
+
+
 @pytest.mark.parametrize("fuse", [1, 4, 8])
 def test_fused_chains_match_oracle(cuda, tnq_lib, oracle_lib, fuse):
     """Chains fused into one kernel (down to tiny chains) give the oracle's slices."""
