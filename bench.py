@@ -53,32 +53,53 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
+        self.samples = []  # (host time, csv line)
+        self.t0 = self.t1 = None  # the timed region, set by the caller
+
+    def _read(self):
+        for line in self.proc.stdout:
+            if line.strip():
+                self.samples.append((time.perf_counter(), line))
 
     def __enter__(self):
+        import threading
+
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
+            return self
+        self.reader = threading.Thread(target=self._read, daemon=True)
+        self.reader.start()
+        t = time.perf_counter()
+        while not self.samples and time.perf_counter() - t < 3.0:  # sampling runs before timing starts
+            time.sleep(0.02)
         return self
 
     def __exit__(self, *exc):
-        self.lines = []
         if self.proc:
+            time.sleep(0.25)  # one more sample after the region
             self.proc.terminate()
             try:
-                out, _ = self.proc.communicate(timeout=5)
+                self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
-                out, _ = self.proc.communicate()
-            self.lines = [l for l in out.splitlines() if l.strip()]
+            self.reader.join(timeout=5)
         return False
 
     def summary(self):
+        """Median SM clock and throttle reasons of the samples taken inside the
+        timed region (the nearest ones if the region was shorter than a sample)."""
+        inside = [l for t, l in self.samples if self.t0 is not None and self.t0 <= t <= self.t1]
+        lines = inside
+        if not lines and self.samples and self.t0 is not None:
+            mid = 0.5 * (self.t0 + self.t1)
+            lines = [min(self.samples, key=lambda x: abs(x[0] - mid))[1]]
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for l in getattr(self, "lines", []):
+        for l in lines:
             f = [x.strip() for x in l.split(",")]
             if len(f) < 9:
                 continue
@@ -91,7 +112,7 @@ class ClockSampler:
                 if v.lower() == "active":
                     reasons.add(name)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "samples_in_timed_region": len(inside)}
 
 
 # ncu DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of every
@@ -255,7 +276,8 @@ def run_reference(args, cfg_name):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 60, about 1 s of GPU time; 5 oracle slices for --impl reference)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="tnq", choices=["tnq", "reference"])
     ap.add_argument("--config", default="7x7_d1+32+1", choices=sorted(CONFIGS))
@@ -282,6 +304,8 @@ def main():
     ap.add_argument("--tune-batch", type=int, default=16, help="slices per batch while autotuning")
     ap.add_argument("--tune-gb", type=int, default=48, help="workspace GiB while autotuning")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 5 if args.impl == "reference" else 60
 
     if args.impl == "reference":
         run_reference(args, args.config)
@@ -351,12 +375,14 @@ def main():
         if world > 1:
             dist.barrier()
         t0 = time.perf_counter()
+        clk.t0 = t0
         e0.record(stream)
         for _ in range(args.steps):
             amp = tnq.contract_sliced(plan, bits, workspace=ws, max_batch=B, stream=stream)
         e1.record(stream)
         torch.cuda.synchronize()
-        t_wall = time.perf_counter() - t0
+        clk.t1 = time.perf_counter()
+        t_wall = clk.t1 - t0
         if world > 1:
             dist.barrier()
     t_dev = e0.elapsed_time(e1) / 1e3
