@@ -116,8 +116,10 @@ typedef struct {
   int32_t reorder_every;  /* > 0: recompute the greedy order (opts->ordering) of the reduced graph after every
                              this many deletions (Algorithm 2's optional recomputation step); 0 (default): never */
   int32_t order_trials;   /* > 1: also plan from this many - 1 greedy orders with seeded random ties (seeded by
-                             opts->seed) and keep the plan with the lowest 2^p * sum over steps 2^bag; 0 or 1
-                             (default): the deterministic greedy order only */
+                             opts->seed) and keep the plan with the lowest 2^p * sum over steps 2^bag (the
+                             earliest of equals); 0 or 1 (default): the deterministic greedy order only. The
+                             trials run on host threads (at most the hardware threads; the environment
+                             variable TNQ_PLAN_THREADS lowers the cap); the plan does not depend on it */
 } tnq_plan_opts;
 
 typedef struct {

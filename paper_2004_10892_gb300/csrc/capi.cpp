@@ -1,12 +1,17 @@
 // capi.cpp -- host-side C-ABI entry points: errors, planning, plan queries and
 // the graph-level algorithms (Algorithms 1, 2, 4 and the Section III scores).
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
+#include <cstdlib>
+#include <exception>
 #include <iterator>
 #include <cmath>
 #include <cstring>
 #include <new>
 #include <string>
+#include <thread>
+#include <vector>
 
 #include "../../include/tnq.h"
 #include "plan.hpp"
@@ -95,38 +100,66 @@ tnq_status tnq_plan_from_circuit(int32_t n_qubits, const tnq_gate* gates, size_t
     P->graph = network_graph(P->net);
     // order_trials > 1: also try greedy orders with seeded random ties and keep
     // the trial whose sliced plan has the lowest cost 2^p * sum over steps 2^bag
-    // (bag limit met first); trial 0 is the deterministic order
+    // (bag limit met first; the earliest trial among equals); trial 0 is the
+    // deterministic order. Trials are independent and run on host threads
+    // (TNQ_PLAN_THREADS caps their number); the choice does not depend on it.
     const int trials = std::max(1, o.order_trials);
-    double best_cost = 0;
-    bool best_fits = false;
-    for (int trial = 0; trial < trials; ++trial) {
+    struct Trial {
+      std::vector<int> ord, mu, order;
+      int tau = 0;
+      double cost = 0;
+      bool fits = false;
+    };
+    std::vector<Trial> tr(trials);
+    auto run_trial = [&](int trial) {
       uint64_t rs = (o.seed ^ 0x9E3779B97F4A7C15ull) + (uint64_t)trial;
-      std::vector<int> ord = greedy_order(P->graph, o.ordering, trial ? &rs : nullptr);
-      DeletionResult R = greedy_deletion(P->graph, ord, o.slicer, o.min_p, o.max_p, o.max_bag_log2, o.seed,
+      Trial& T = tr[trial];
+      T.ord = greedy_order(P->graph, o.ordering, trial ? &rs : nullptr);
+      DeletionResult R = greedy_deletion(P->graph, T.ord, o.slicer, o.min_p, o.max_p, o.max_bag_log2, o.seed,
                                          o.td_rebuild != 0,
                                          o.slicer == TNQ_SLICER_LEARNED ? &learned_propose : nullptr, nullptr,
                                          o.reorder_every, o.ordering);
       Graph reduced = P->graph;
       for (int v : R.mu) delete_vertex(reduced, v);
       std::vector<int> bags;
-      const int tau = treewidth_of_order(reduced, R.reduced_order, &bags);
-      double cost = 0;
+      T.tau = treewidth_of_order(reduced, R.reduced_order, &bags);
       int max_bag = 0;
       for (int b : bags) {
-        cost += std::ldexp(1.0, b);
+        T.cost += std::ldexp(1.0, b);
         max_bag = std::max(max_bag, b);
       }
-      cost = std::ldexp(cost, (int)R.mu.size());
-      const bool fits = o.max_bag_log2 <= 0 || max_bag <= o.max_bag_log2;
-      if (trial == 0 || (fits && !best_fits) || (fits == best_fits && cost < best_cost)) {
-        best_cost = cost;
-        best_fits = fits;
-        P->order_full = ord;
-        P->mu = R.mu;
-        P->order = R.reduced_order;
-        P->tau = tau;
-      }
+      T.cost = std::ldexp(T.cost, (int)R.mu.size());
+      T.fits = o.max_bag_log2 <= 0 || max_bag <= o.max_bag_log2;
+      T.mu = std::move(R.mu);
+      T.order = std::move(R.reduced_order);
+    };
+    int nth = std::min(trials, std::max(1, (int)std::thread::hardware_concurrency()));
+    if (const char* e = std::getenv("TNQ_PLAN_THREADS")) nth = std::max(1, std::min(nth, std::atoi(e)));
+    if (nth <= 1) {
+      for (int t = 0; t < trials; ++t) run_trial(t);
+    } else {
+      std::atomic<int> next(0);
+      std::vector<std::exception_ptr> err(nth);
+      std::vector<std::thread> pool;
+      for (int w = 0; w < nth; ++w)
+        pool.emplace_back([&, w] {
+          try {
+            for (int t; (t = next.fetch_add(1)) < trials;) run_trial(t);
+          } catch (...) {
+            err[w] = std::current_exception();
+          }
+        });
+      for (auto& th : pool) th.join();
+      for (auto& e : err)
+        if (e) std::rethrow_exception(e);
     }
+    int best = 0;
+    for (int t = 1; t < trials; ++t)
+      if ((tr[t].fits && !tr[best].fits) || (tr[t].fits == tr[best].fits && tr[t].cost < tr[best].cost)) best = t;
+    P->order_full = std::move(tr[best].ord);
+    P->mu = std::move(tr[best].mu);
+    P->order = std::move(tr[best].order);
+    P->tau = tr[best].tau;
     P->tau_full = treewidth_of_order(P->graph, P->order_full);
     P->prog = compile_program(P->net, P->order, P->mu);
     if (o.precision != TNQ_PREC_C64)

@@ -370,3 +370,17 @@ def test_order_trials(tnq_lib):
     b = tnq_lib.Plan(circ, max_bag_log2=16, max_p=30, order_trials=8, seed=3)
     assert a.order() == b.order() and a.sliced() == b.sliced()
     assert a.info()["max_bag"] <= 16 and a.info()["p"] <= one.info()["p"] + 1
+
+
+def test_order_trials_do_not_depend_on_threads(tnq_lib, monkeypatch):
+    """The randomised greedy orders are tried on host threads; the chosen plan
+    is the same with one thread (the earliest of equally cheap trials wins)."""
+    cases = [(I.random_grid_circuit(6, 6, 24, 2), dict(max_bag_log2=16, max_p=30, order_trials=16, seed=5)),
+             (I.random_grid_circuit(7, 7, 32, 0), dict(max_bag_log2=28, max_p=40, reorder_every=1, order_trials=12))]
+    for circ, kw in cases:
+        monkeypatch.delenv("TNQ_PLAN_THREADS", raising=False)
+        a = tnq_lib.Plan(circ, **kw)
+        monkeypatch.setenv("TNQ_PLAN_THREADS", "1")
+        b = tnq_lib.Plan(circ, **kw)
+        assert a.order() == b.order() and a.sliced() == b.sliced()
+        assert a.info()["total_flops"] == b.info()["total_flops"]
