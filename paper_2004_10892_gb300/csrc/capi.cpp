@@ -138,17 +138,26 @@ tnq_status tnq_plan_from_circuit(int32_t n_qubits, const tnq_gate* gates, size_t
     if (nth <= 1) {
       for (int t = 0; t < trials; ++t) run_trial(t);
     } else {
+      // nth - 1 helper threads and this one take trials from a shared counter
+      // (if a helper cannot be started, the others still run every trial)
       std::atomic<int> next(0);
       std::vector<std::exception_ptr> err(nth);
+      auto work = [&](int w) {
+        try {
+          for (int t; (t = next.fetch_add(1)) < trials;) run_trial(t);
+        } catch (...) {
+          err[w] = std::current_exception();
+        }
+      };
       std::vector<std::thread> pool;
-      for (int w = 0; w < nth; ++w)
-        pool.emplace_back([&, w] {
-          try {
-            for (int t; (t = next.fetch_add(1)) < trials;) run_trial(t);
-          } catch (...) {
-            err[w] = std::current_exception();
-          }
-        });
+      for (int w = 1; w < nth; ++w) {
+        try {
+          pool.emplace_back(work, w);
+        } catch (const std::exception&) {
+          break;
+        }
+      }
+      work(0);
       for (auto& th : pool) th.join();
       for (auto& e : err)
         if (e) std::rethrow_exception(e);
