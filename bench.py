@@ -5,8 +5,9 @@ One step = one amplitude <x|C|0^49>: all 2^p slices (p chosen so every slice's
 largest bucket has at most 2^28 entries) contracted through the C-ABI call
 tnq_contract_sliced and summed in FP64. The JSON line reports
 slice-contractions/s (the metric), time per amplitude, the relative error of
-one slice against the FP64 oracle, the roofline of the fused bucket kernel,
-and the oracle's own speed on the host cores.
+the amplitude (every slice recomputed by the FP64 oracle) and of its worst
+slice, the roofline of the fused bucket kernel, and the oracle's own speed on
+the host cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Under torchrun every rank contracts its own bitstring's amplitude (weak
@@ -147,6 +148,16 @@ def fp32_peak_tflops(peaks):
     return 152 * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
 
 
+def measured_fp32_peak(L, stream):
+    """FP32 FMA peak measured on this device (tnq_internal_fp32_peak: an FMA
+    loop on every SM, best of 5 launches timed with CUDA events), TFLOP/s."""
+    out = ctypes.c_double()
+    L.tnq_internal_fp32_peak.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]
+    if L.tnq_internal_fp32_peak(5, ctypes.c_void_p(stream.cuda_stream), ctypes.byref(out)) != 0:
+        return None
+    return out.value
+
+
 def launch_roofline(L, plan, bits, ws, B, n_sl, stream, peaks, info):
     """Times every launch of one batch with CUDA events on the launching stream
     and returns the roofline of the kernel with the largest share of time."""
@@ -179,7 +190,11 @@ def launch_roofline(L, plan, bits, ws, B, n_sl, stream, peaks, info):
     t_gem = sum(ms[i] for i in gem)
     tot = t_grp + t_one + t_gem
     hbm = peaks["hbm_gbs"]
-    fp32 = fp32_peak_tflops(peaks)
+    fp32_meas = measured_fp32_peak(L, stream)
+    fp32 = fp32_meas if fp32_meas else fp32_peak_tflops(peaks)
+    fp32_src = ("measured: FFMA loop on every SM (tnq_internal_fp32_peak), best of 5 CUDA-event-timed launches; "
+                f"derived 152 SMs x 128 lanes x 2 x max clock = {fp32_peak_tflops(peaks):.1f}") if fp32_meas else \
+        "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"
     one_gbs = sum(by[i] for i in one) / (t_one / 1e3) / 1e9 if t_one > 0 else None
     grp_tfs = sum(fl[i] for i in grp) / (t_grp / 1e3) / 1e12 if t_grp > 0 else None
     k_bucket = {"kernel": "k_bucket", "bound": "hbm", "achieved": one_gbs, "peak": hbm, "unit": "GB/s",
@@ -198,7 +213,7 @@ def launch_roofline(L, plan, bits, ws, B, n_sl, stream, peaks, info):
                "frac": grp_tfs / fp32 if grp_tfs else None, "launches": len(grp), "time_share": t_grp / tot,
                "flops_per_launch": sum(fl[i] for i in grp) / max(len(grp), 1),
                "ms_per_launch": t_grp / max(len(grp), 1),
-               "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}
+               "peak_source": fp32_src}
     dom, other = (k_group, k_bucket) if t_grp >= t_one else (k_bucket, k_group)
     out = dict(dom)
     out["traffic"] = None
@@ -227,13 +242,39 @@ def launch_roofline(L, plan, bits, ws, B, n_sl, stream, peaks, info):
     return out
 
 
-def oracle_slice(circ, bits, plan, s):
-    """FP64 oracle value and time of slice s of the plan (test infrastructure, CPU)."""
+def rel_err(a, ref, n):
+    """Relative error with the Porter-Thomas floor: |a - ref| / |ref| when
+    |ref|^2 >= 2^-n / 10, else |a - ref| / 2^(-n/2)."""
+    floor = 2.0 ** (-n / 2)
+    den = abs(ref) if abs(ref) ** 2 >= floor ** 2 / 10 else floor
+    return abs(a - ref) / den
+
+
+def oracle_check(circ, bits, plan, gpu_amp, gpu_per, n_check, cpu_budget_s=20.0):
+    """FP64 oracle values of slices 0..n_check-1 of the plan (test
+    infrastructure, CPU), one call per slice so the first ones also time the
+    CPU baseline; returns the amplitude's error (when every slice is checked),
+    the largest per-slice error and the baseline sample."""
     from oracle import oracle
 
-    t0 = time.perf_counter()
-    v = oracle.contract(circ, bits, order=plan.order(), mu=plan.sliced(), slices=(s, s + 1))
-    return v, time.perf_counter() - t0, oracle.num_threads()
+    ref = []
+    t_sample, n_sample = 0.0, 0
+    for s in range(n_check):
+        t0 = time.perf_counter()
+        ref.append(oracle.contract(circ, bits, order=plan.order(), mu=plan.sliced(), slices=(s, s + 1)))
+        dt = time.perf_counter() - t0
+        if t_sample < cpu_budget_s:
+            t_sample += dt
+            n_sample += 1
+    n_sl = len(gpu_per)
+    slice_err = max(abs(gpu_per[s] - ref[s]) / abs(ref[s]) if ref[s] != 0 else abs(gpu_per[s])
+                    for s in range(n_check))
+    amp_ref = sum(ref) if n_check == n_sl else None
+    return {"amp_ref": amp_ref,
+            "amp_err": rel_err(gpu_amp, amp_ref, circ.n_qubits) if amp_ref is not None else None,
+            "slice_err_max": slice_err, "n_checked": n_check,
+            "cpu_value": n_sample / t_sample, "cpu_slices": n_sample, "cpu_s": t_sample,
+            "cores": oracle.num_threads()}
 
 
 def run_reference(args, cfg_name):
@@ -282,7 +323,10 @@ def main():
     ap.add_argument("--impl", default="tnq", choices=["tnq", "reference"])
     ap.add_argument("--config", default="7x7_d1+32+1", choices=sorted(CONFIGS))
     ap.add_argument("--max-batch", type=int, default=256, help="slices contracted at once")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true",
+                    help="skip the FP64 oracle (CPU baseline and the amplitude's error)")
+    ap.add_argument("--oracle-slices", type=int, default=0,
+                    help="slices checked against the FP64 oracle (0: all, which gives the amplitude's error)")
     ap.add_argument("--no-profile", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--precision", default="bf16x3", choices=["c64", "bf16x3", "tf32x3"],
@@ -403,15 +447,19 @@ def main():
         roof = launch_roofline(L, plan, bits, ws, B, n_sl, stream, peaks, info)
 
     cpu = None
-    err = None
+    chk = None
     if rank == 0 and not args.no_cpu_baseline:
-        # one slice in FP64 on the host cores: the CPU baseline and the error check
-        ref, t_cpu, cores = oracle_slice(circ, bits, plan, 0)
-        per = tnq.contract_sliced(plan, bits, 0, 1, workspace=ws, max_batch=1, stream=stream)
-        err = abs(per - ref) / abs(ref) if ref != 0 else abs(per)
-        cpu = {"value": 1.0 / t_cpu, "unit": "slices/s", "cores": cores, "kind": "oracle",
-               "sample": "slice 0 of the same 7x7 amplitude (FP64 bucket elimination, OpenMP over entries)"
-               if args.config.startswith("7x7") else f"slice 0 of {args.config}"}
+        # every slice of the timed amplitude in FP64 on the host cores (the
+        # parity check of the headline number); the first ~20 s of it also
+        # time the CPU baseline
+        amp_chk, per = tnq.contract_sliced(plan, bits, 0, n_sl, workspace=ws, max_batch=B, stream=stream,
+                                           per_slice=True)
+        n_check = n_sl if args.oracle_slices <= 0 else min(args.oracle_slices, n_sl)
+        chk = oracle_check(circ, bits, plan, amp_chk, per, n_check)
+        chk["same_as_timed"] = amp_chk == amp
+        cpu = {"value": chk["cpu_value"], "unit": "slices/s", "cores": chk["cores"], "kind": "oracle",
+               "sample": f"slices 0..{chk['cpu_slices'] - 1} of the same amplitude ({chk['cpu_s']:.1f} s; FP64 "
+                         f"bucket elimination, OpenMP over output entries)"}
 
     if rank == 0:
         h2d = 8 + n_batches * (64 + 8 * ((circ.n_qubits + 31) // 32) * (B + 1))
@@ -432,7 +480,14 @@ def main():
                        "form": "plain per-slice" if args.plain else "batched, fused, autotuned",
                        "reorder_every": args.reorder_every, "order_trials": args.order_trials},
             "time_per_amplitude_s": t_dev / args.steps,
-            "rel_err_vs_fp64": err,
+            "rel_err_vs_fp64": chk["amp_err"] if chk else None,
+            "rel_err_vs_fp64_detail": {
+                "amplitude": chk["amp_err"], "max_slice": chk["slice_err_max"],
+                "slices_checked": chk["n_checked"], "oracle_amplitude": [chk["amp_ref"].real, chk["amp_ref"].imag]
+                if chk["amp_ref"] is not None else None,
+                "rule": "|a - a_fp64| / |a_fp64| if |a_fp64|^2 >= 2^-n/10 else / 2^(-n/2); the amplitude is the "
+                        "FP64 sum of every slice (Eq. 5), checked from the same batch configuration as the timed "
+                        "steps"} if chk else None,
             "amplitude": [amp.real, amp.imag],
             "e2e": {"value": e2e_value, "unit": "slices/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,

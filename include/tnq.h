@@ -164,6 +164,11 @@ void tnq_plan_opts_default(tnq_plan_opts* opts);
 tnq_status tnq_plan_from_circuit(int32_t n_qubits, const tnq_gate* gates, size_t n_gates,
                                  const tnq_plan_opts* opts, tnq_plan** out_plan);
 void tnq_plan_destroy(tnq_plan* plan);
+/* Size and cost of the plan (Section IV: a slice needs memory M = O(2^tau)
+ * and P = O(2^(tau+1)) operations; the whole amplitude 2^p times that):
+ * tau_full and tau from Algorithm 1 before and after slicing, and the exact
+ * per-slice flops and bytes of the compiled bucket program (every bucket of
+ * Eq. 2 counted with its real bag size). TNQ_EINVAL on NULL arguments. */
 tnq_status tnq_plan_info_get(const tnq_plan* plan, tnq_plan_info* out);
 
 /* Reduced elimination order pi~ as variables (qubit[i], segment[i]), i <
@@ -227,7 +232,10 @@ tnq_status tnq_plan_fused_chains(const tnq_plan* plan, int32_t* last_bucket, siz
  * plan's cached device configurations. */
 tnq_status tnq_plan_keep_chains(tnq_plan* plan, const int32_t* last_bucket, size_t n);
 
-/* tnq_amplitudes_batch: amplitudes of many bitstrings of many plans.
+/* tnq_amplitudes_batch: amplitudes of many bitstrings of many plans; each
+ * amplitude is Eq. 5 for its bitstring (the sum over the plan's 2^p slices of
+ * Eq. 4). The plan does not depend on the bitstring (output wires are fixed
+ * variables, Section II.A), so (bitstring, slice) pairs batch like slices.
  * Plan i has bitstrings bits_offset[i] .. bits_offset[i+1]-1 (bits_offset has
  * n_plans+1 entries, bits_offset[0] = 0); bitstring b occupies
  * bits[b*n_qubits(plan) ...] -- the bytes of all bitstrings packed back to
@@ -239,20 +247,23 @@ tnq_status tnq_amplitudes_batch(const tnq_plan* const* plans, size_t n_plans,
                                 double* out_amps);
 
 /* tnq_contract_sliced_noalloc: the same partial sum as tnq_contract_sliced
- * for callers that cannot allocate device memory (a host whose own pool
- * allocator already holds the memory it may use, code running while another
- * thread keeps a stream capture open, or a loop that cannot afford
- * cudaMalloc's implicit synchronisation). The paper has no counterpart: this
- * is a deployment variant. Instead of a caller workspace it uses one static
- * 64 MiB device array (held by every GPU that loads the library until the
- * process exits) for the plan tables and the intermediate tensors; it
- * allocates no device memory. As many slices run at once as fit in it.
+ * for callers that cannot allocate device memory: a host whose own pool
+ * allocator already holds all the device memory it is allowed to use, or a
+ * latency-bound loop that cannot afford cudaMalloc's implicit device
+ * synchronisation. The paper has no counterpart: this is a deployment
+ * variant. Instead of a caller workspace it uses one static 64 MiB device
+ * array (held by every GPU that loads the library until the process exits)
+ * for the plan tables and the intermediate tensors; it allocates no device
+ * memory. As many slices run at once as fit in it, with the same kernels and
+ * launch shapes as tnq_contract_sliced.
  *  - The first call on each device looks up the array's device address with
- *    that device current; make that first call before any stream capture.
+ *    that device current, and the first call of a plan at a batch size builds
+ *    its host-side launch tables (cached with the plan, freed by
+ *    tnq_plan_destroy); make those first calls before any stream capture.
  *  - Every call shares the one array per device: calls that overlap on the
  *    GPU (other streams, other threads) race and give wrong results. The
- *    call clears what must start at zero and synchronises `stream` before it
- *    returns.
+ *    call uploads its tables again, clears what must start at zero and
+ *    synchronises `stream` before it returns.
  *  - TNQ_ENOMEM (with the byte counts in tnq_last_error) if one slice of the
  *    plan needs more than the 64 MiB.
  * Arguments, results and other errors as tnq_contract_sliced. */

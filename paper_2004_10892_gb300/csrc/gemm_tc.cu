@@ -613,11 +613,18 @@ __global__ void k_gemm_pack(const GemmBucketArgs g, int side) {
 
 }  // namespace
 
+// SMs of the current device (one query per call; the attribute is cached by the runtime).
+static int device_sms() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      sms <= 0)
+    sms = 1;
+  return sms;
+}
+
 void gemm_tc_launch(int kind, const GemmArgs& args, void* stream) {
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  int dev = 0, sms = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-    sms = 148;
+  const int sms = device_sms();
   const long long tiles = (long long)args.batch * args.row_tiles_a * args.row_tiles_b;
   const unsigned grid = (unsigned)std::max<long long>(1, std::min<long long>(tiles, sms));  // one block per SM
   if (kind == GEMM_BF16) {
@@ -635,8 +642,9 @@ void gemm_bucket_launch(const GemmBucketArgs& g, const GemmEpilogue& ep, int* st
   const long long batch = (long long)g.items << g.ns;
   const int ch = 16 / esize;  // K values per thread of k_gemm_pack
   const long long na = batch * g.m_pad * (g.k_pad / ch), nb = batch * g.n_pad * (g.k_pad / ch);
-  const int blocks_a = (int)std::min<long long>((na + 255) / 256, 152 * 16);
-  const int blocks_b = (int)std::min<long long>((nb + 255) / 256, 152 * 16);
+  const long long cap = 16ll * device_sms();  // grid-stride pack: 16 blocks of 256 threads per SM
+  const int blocks_a = (int)std::max<long long>(1, std::min<long long>((na + 255) / 256, cap));
+  const int blocks_b = (int)std::max<long long>(1, std::min<long long>((nb + 255) / 256, cap));
   if (g.kind == GEMM_BF16) {
     k_gemm_pack<GEMM_BF16><<<blocks_a, 256, 0, s>>>(g, 0);
     k_gemm_pack<GEMM_BF16><<<blocks_b, 256, 0, s>>>(g, 1);

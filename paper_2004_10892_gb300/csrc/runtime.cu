@@ -21,6 +21,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -1219,10 +1220,23 @@ struct ExecConfig {
   cudaGraphExec_t exec = nullptr;
 };
 
+// Host-side configuration of the allocation-free entry point for one batch
+// size: its device pointers point into the library's static scratch, so it
+// owns no device memory; the host tables are uploaded again on every call.
+struct NoallocConfig {
+  ExecConfig C;
+  std::vector<LeafDev> leaves, scalars;
+  std::vector<FinalDev> finals;
+  size_t tables = 0;  // bytes of plan tables at the front of the scratch
+};
+
 struct DeviceState {
   int device = -1;
   std::map<std::pair<int, int>, ExecConfig*> configs;  // (mode, B)
+  std::map<int, NoallocConfig*> noalloc;               // B
+  std::map<uint64_t, int> noalloc_batch;               // batch cap -> largest B that fits the scratch
   ~DeviceState() {
+    for (auto& kv : noalloc) delete kv.second;
     for (auto& kv : configs) {
       ExecConfig* c = kv.second;
       if (c->exec) cudaGraphExecDestroy(c->exec);
@@ -2366,7 +2380,61 @@ static void reset_device_state(const tnq_plan& P) {
 }
 }  // namespace tnq
 
+// FP32 FMA throughput probe: every thread runs 8 independent FMA chains of
+// 16 x iters steps (x = x a + b, bounded for |a| < 1), so the FMA pipes of
+// every SM stay busy; the result only feeds a store that never happens for
+// these inputs, which keeps the loop.
+__global__ void __launch_bounds__(256) k_ffma_peak(float a, float b, int iters, float* out) {
+  float x[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) x[i] = threadIdx.x * 1e-3f + (float)i;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+#pragma unroll
+      for (int i = 0; i < 8; ++i) x[i] = fmaf(x[i], a, b);
+  }
+  float sum = 0.f;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) sum += x[i];
+  if (sum == -1.2345e30f) out[0] = sum;
+}
+
 extern "C" {
+
+// Internal measurement hook (not in include/tnq.h): measured FP32 FMA peak of
+// the current device in TFLOP/s (2 flops per FMA), the best of `reps` timed
+// launches of k_ffma_peak on `stream` (SMs x 8 blocks of 256 threads). The
+// roofline of the fused chain kernel, whose arithmetic is FP32 FMA/FMUL,
+// divides by it.
+int tnq_internal_fp32_peak(int reps, void* stream, double* out_tflops) {
+  if (!out_tflops || reps < 1) return 1;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 1;
+  const int blocks = sms * 8, iters = 4096;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return 1;
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return 1; }
+  float best = 0.f;
+  k_ffma_peak<<<blocks, 256, 0, s>>>(0.999f, 1e-3f, iters, nullptr);  // warm-up
+  for (int r = 0; r < reps; ++r) {
+    cudaEventRecord(e0, s);
+    k_ffma_peak<<<blocks, 256, 0, s>>>(0.999f, 1e-3f, iters, nullptr);
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms > 0.f && (best == 0.f || ms < best)) best = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (cudaGetLastError() != cudaSuccess || best <= 0.f) return 1;
+  const double flops = 2.0 * 8 * 16 * (double)iters * 256.0 * blocks;
+  *out_tflops = flops / (best * 1e-3) / 1e12;
+  return 0;
+}
 
 int tnq_internal_profile(const tnq_plan* plan, const uint8_t* bits, uint64_t s0, uint64_t s1, void* workspace,
                          size_t ws_bytes, uint32_t max_batch, void* stream, int cap, float* ms, double* bytes,
@@ -2692,10 +2760,9 @@ tnq_status tnq_amplitudes_batch(const tnq_plan* const* plans, size_t n_plans, co
 // Allocation-free variant of tnq_contract_sliced.
 //
 // Some callers cannot call cudaMalloc: a host whose own pool allocator has
-// already reserved the device memory it is allowed to use, code that runs
-// while another thread of the process holds a stream capture open (where
-// cudaMalloc is not allowed), or a latency-bound loop in which cudaMalloc's
-// implicit device synchronisation would stall other streams. For them this
+// already reserved the device memory it is allowed to use, or a latency-bound
+// loop in which cudaMalloc's implicit device synchronisation would stall
+// other streams. For them this
 // entry point takes its scratch (plan tables and intermediate tensors) from one
 // fixed-size array in device global memory that the library declares at file
 // scope; every GPU that loads the library holds that array until the process
@@ -2731,6 +2798,97 @@ static tnq_status noalloc_scratch_address(void** out) {
   return TNQ_OK;
 }
 
+// Bytes of plan tables (leaf, scalar, wire, final and early-bucket records)
+// at the front of the scratch for batch B.
+static size_t noalloc_table_bytes(const tnq_plan& P, int B) {
+  ExecConfig C;
+  C.L = make_layout(P, 0, B);
+  const size_t hoist = build_steps(P, C.L, C) ? C.hoist_dev.size() : 0;
+  return align_up(P.prog.leaves.size() * sizeof(LeafDev), 256) +
+         align_up(P.prog.scalar_leaves.size() * sizeof(LeafDev), 256) +
+         align_up(P.net.inout_qubits.size() * sizeof(int), 256) + align_up(P.prog.finals.size() * sizeof(FinalDev), 256) +
+         align_up(hoist * sizeof(HoistDev), 256);
+}
+
+// Host-side configuration of the allocation-free path for batch B, built once
+// per (plan, B) on the plan's device and cached with its other configurations:
+// the same steps, launch shapes and early-bucket levels as the workspace path,
+// with the plan tables at the front of the static scratch and the workspace
+// after them. Nothing in it owns device memory. Caller holds no lock.
+static tnq_status get_noalloc_config(const tnq_plan& P, uint64_t cap, char* scratch, NoallocConfig** out) {
+  int dev;
+  CU(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(P.dev_mu);
+  if (P.dev && P.dev->device != dev) {
+    set_error("plan already bound to another CUDA device");
+    return TNQ_EINVAL;
+  }
+  if (!P.dev) {
+    P.dev = new DeviceState();
+    P.dev->device = dev;
+  }
+  const Program& prog = P.prog;
+  // largest power-of-two batch (<= cap) whose tables and workspace fit
+  int B = 0;
+  auto cb = P.dev->noalloc_batch.find(cap);
+  if (cb != P.dev->noalloc_batch.end()) {
+    B = cb->second;
+  } else {
+    for (uint64_t b = 1; b <= cap; b <<= 1) {
+      if (noalloc_table_bytes(P, (int)b) + make_layout(P, 0, (int)b).total > NOALLOC_SCRATCH_BYTES) break;
+      B = (int)b;
+    }
+    if (B > 0) P.dev->noalloc_batch[cap] = B;
+  }
+  if (B == 0) {
+    set_error("plan needs " + std::to_string(noalloc_table_bytes(P, 1) + make_layout(P, 0, 1).total) +
+              " bytes of scratch for one slice; the static scratch of tnq_contract_sliced_noalloc holds " +
+              std::to_string(NOALLOC_SCRATCH_BYTES) + " bytes");
+    return TNQ_ENOMEM;
+  }
+  auto it = P.dev->noalloc.find(B);
+  if (it != P.dev->noalloc.end()) {
+    *out = it->second;
+    return TNQ_OK;
+  }
+  CU(allow_group_smem());
+  int ggrid = 0;
+  tnq_status st = group_grid_size(&ggrid);
+  if (st != TNQ_OK) return st;
+  std::unique_ptr<NoallocConfig> NC(new NoallocConfig());
+  ExecConfig& C = NC->C;
+  C.group_grid = ggrid;
+  C.L = make_layout(P, 0, B);
+  for (int t : prog.leaves) NC->leaves.push_back(make_leafdev(P, &prog.tensors[t], prog.tensors[t].leaf_gate, &C.L, t));
+  for (int g : prog.scalar_leaves) NC->scalars.push_back(make_leafdev(P, nullptr, g, nullptr, -1));
+  for (int t : prog.finals) NC->finals.push_back(FinalDev{C.L.off[t], t, (int)C.L.dep[t]});
+  if (!build_steps(P, C.L, C)) return TNQ_EUNSUPPORTED;
+  for (size_t i = 0; i < C.gsmem.size(); ++i) {  // per-chain persistent grids, as build_config sizes them
+    int g = 0;
+    if ((st = group_grid_size(&g, C.gsmem[i], C.gp[i].tail > 0)) != TNQ_OK) return st;
+    C.ggrid.push_back(g);
+  }
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    char* p = scratch + o;
+    o = align_up(o + bytes, 256);
+    return p;
+  };
+  C.d_leaves = reinterpret_cast<LeafDev*>(take(NC->leaves.size() * sizeof(LeafDev)));
+  C.d_scalars = reinterpret_cast<LeafDev*>(take(NC->scalars.size() * sizeof(LeafDev)));
+  C.d_inout = reinterpret_cast<int*>(take(P.net.inout_qubits.size() * sizeof(int)));
+  C.d_finals = reinterpret_cast<FinalDev*>(take(NC->finals.size() * sizeof(FinalDev)));
+  C.d_hoist = reinterpret_cast<HoistDev*>(take(C.hoist_dev.size() * sizeof(HoistDev)));
+  NC->tables = o;
+  C.n_leaves = (int)NC->leaves.size();
+  C.n_scalars = (int)NC->scalars.size();
+  C.n_inout = (int)P.net.inout_qubits.size();
+  C.n_finals = (int)NC->finals.size();
+  *out = NC.get();
+  P.dev->noalloc[B] = NC.release();
+  return TNQ_OK;
+}
+
 }  // namespace tnq
 
 extern "C" {
@@ -2748,63 +2906,24 @@ tnq_status tnq_contract_sliced_noalloc(const tnq_plan* plan, const uint8_t* bits
   if (st != TNQ_OK) return st;
   void* scratch = nullptr;
   if ((st = noalloc_scratch_address(&scratch)) != TNQ_OK) return st;
-  CU(allow_group_smem());
-  int ggrid = 0;
-  if ((st = group_grid_size(&ggrid)) != TNQ_OK) return st;
-
-  // Host copies of the plan tables; they go to the front of the scratch.
-  const Program& prog = plan->prog;
   const uint64_t n_items = slice_end - slice_begin;
   uint64_t cap = 1;
   while (cap < n_items && cap < (1ull << MAX_ITEM_BITS)) cap <<= 1;
-  int B = 0;
-  size_t tables = 0;
-  for (uint64_t b = 1; b <= cap; b <<= 1) {
-    const size_t t = align_up((prog.leaves.size() + prog.scalar_leaves.size()) * sizeof(LeafDev), 256) +
-                     align_up(plan->net.inout_qubits.size() * sizeof(int), 256) +
-                     align_up(prog.finals.size() * sizeof(FinalDev), 256);
-    if (t + layout_bytes(*plan, 0, (int)b) > NOALLOC_SCRATCH_BYTES) break;
-    B = (int)b;
-    tables = t;
-  }
-  if (B == 0) {
-    set_error("plan needs " + std::to_string(layout_bytes(*plan, 0, 1)) +
-              " bytes of scratch for one slice; the static scratch of tnq_contract_sliced_noalloc holds " +
-              std::to_string(NOALLOC_SCRATCH_BYTES) + " bytes");
-    return TNQ_ENOMEM;
-  }
-  ExecConfig C;  // pointers into the scratch; nothing here is freed
-  C.group_grid = ggrid;
-  C.L = make_layout(*plan, 0, B);
-  std::vector<LeafDev> leaves, scalars;
-  for (int t : prog.leaves) leaves.push_back(make_leafdev(*plan, &prog.tensors[t], prog.tensors[t].leaf_gate, &C.L, t));
-  for (int g : prog.scalar_leaves) scalars.push_back(make_leafdev(*plan, nullptr, g, nullptr, -1));
-  std::vector<FinalDev> finals;
-  for (int t : prog.finals) finals.push_back(FinalDev{C.L.off[t], t, (int)C.L.dep[t]});
-  if (!build_steps(*plan, C.L, C)) return TNQ_EUNSUPPORTED;
-  // the early buckets run as ordinary steps here (no level table in the scratch)
-  std::fill(C.step_hoist.begin(), C.step_hoist.end(), 0);
-  C.hoist_first.clear();
-  char* base = reinterpret_cast<char*>(scratch);
-  size_t o = 0;
-  C.d_leaves = reinterpret_cast<LeafDev*>(base + o);
-  o += leaves.size() * sizeof(LeafDev);
-  C.d_scalars = reinterpret_cast<LeafDev*>(base + o);
-  o = align_up(o + scalars.size() * sizeof(LeafDev), 256);
-  C.d_inout = reinterpret_cast<int*>(base + o);
-  o = align_up(o + plan->net.inout_qubits.size() * sizeof(int), 256);
-  C.d_finals = reinterpret_cast<FinalDev*>(base + o);
-  o = align_up(o + finals.size() * sizeof(FinalDev), 256);
-  C.n_leaves = (int)leaves.size();
-  C.n_scalars = (int)scalars.size();
-  C.n_inout = (int)plan->net.inout_qubits.size();
-  C.n_finals = (int)finals.size();
-  char* ws = base + tables;
+  NoallocConfig* NC = nullptr;
+  if ((st = get_noalloc_config(*plan, cap, reinterpret_cast<char*>(scratch), &NC)) != TNQ_OK) return st;
+  ExecConfig& C = NC->C;
+  const int B = C.L.B;
+  char* ws = reinterpret_cast<char*>(scratch) + NC->tables;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  if (!leaves.empty()) CU(cudaMemcpyAsync(C.d_leaves, leaves.data(), leaves.size() * sizeof(LeafDev), cudaMemcpyHostToDevice, s));
-  if (!scalars.empty()) CU(cudaMemcpyAsync(C.d_scalars, scalars.data(), scalars.size() * sizeof(LeafDev), cudaMemcpyHostToDevice, s));
-  if (C.n_inout) CU(cudaMemcpyAsync(C.d_inout, plan->net.inout_qubits.data(), C.n_inout * sizeof(int), cudaMemcpyHostToDevice, s));
-  if (!finals.empty()) CU(cudaMemcpyAsync(C.d_finals, finals.data(), finals.size() * sizeof(FinalDev), cudaMemcpyHostToDevice, s));
+  // every call shares the scratch: the plan tables go up again each time
+  auto put = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
+    return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s) : cudaSuccess;
+  };
+  CU(put(C.d_leaves, NC->leaves.data(), NC->leaves.size() * sizeof(LeafDev)));
+  CU(put(C.d_scalars, NC->scalars.data(), NC->scalars.size() * sizeof(LeafDev)));
+  CU(put(C.d_inout, plan->net.inout_qubits.data(), (size_t)C.n_inout * sizeof(int)));
+  CU(put(C.d_finals, NC->finals.data(), NC->finals.size() * sizeof(FinalDev)));
+  CU(put(C.d_hoist, C.hoist_dev.data(), C.hoist_dev.size() * sizeof(HoistDev)));
   std::vector<unsigned> words((size_t)C.L.n_words * C.L.n_rows, 0u);
   pack_bits(bits, plan->net.n_qubits, words);
   CU(cudaMemcpyAsync(ws + C.L.bits_off, words.data(), words.size() * 4, cudaMemcpyHostToDevice, s));
@@ -2812,6 +2931,7 @@ tnq_status tnq_contract_sliced_noalloc(const tnq_plan* plan, const uint8_t* bits
   std::vector<double> res(2 * (size_t)B), part(2);
   int dev_status = 0;
   double sre = 0, sim = 0;
+  std::lock_guard<std::mutex> lk(plan->dev_mu);  // one launch sequence per plan at a time
   for (uint64_t b0 = slice_begin; b0 < slice_end; b0 += B) {
     BatchHdr h;
     std::memset(&h, 0, sizeof(h));

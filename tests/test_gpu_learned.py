@@ -51,8 +51,8 @@ def test_gpu_gradients_match_oracle(cuda, LN, hidden):
 def test_training_and_planner_gain(cuda, tnq_lib, LN):
     """Train on 60 small circuits; the learned slicer is then compared with
     tree-trimming on held-out circuits at the same bag limit by exact total
-    flops. The gain is reported; the learned planner must not be worse on
-    average by more than a few percent of a doubling."""
+    flops. The learned planner must need fewer total flops on average (a
+    negative mean log2 ratio)."""
     from paper_2004_10892_gb300 import train_proposer as TP
 
     X, y = TP.build_dataset(TP.training_circuits(60, seed=77), max_steps=10)
@@ -67,4 +67,4 @@ def test_training_and_planner_gain(cuda, tnq_lib, LN):
         deltas.append(np.log2(ln.info()["total_flops"]) - np.log2(tt.info()["total_flops"]))
     mean = float(np.mean(deltas))
     print(f"learned vs tree-trimming: mean log2 total-flop ratio {mean:+.3f} over {len(deltas)} circuits {deltas}")
-    assert mean < 0.1
+    assert mean < 0.0, deltas
