@@ -345,6 +345,9 @@ def main():
     ap.add_argument("--tune-file", default=None,
                     help="JSON of the autotuner's kept chains: loaded instead of tuning if it exists, else written "
                          "after tuning (lets a profiler run reuse the decisions of a plain run)")
+    ap.add_argument("--split-slices", action="store_true",
+                    help="under torchrun: every rank contracts its contiguous share of one amplitude's 2^p slices "
+                         "and the FP64 partial sums are all-reduced (strong scaling; Eq. 5)")
     ap.add_argument("--tune-batch", type=int, default=16, help="slices per batch while autotuning")
     ap.add_argument("--tune-gb", type=int, default=48, help="workspace GiB while autotuning")
     args = ap.parse_args()
@@ -370,7 +373,7 @@ def main():
     native_build.build()
     rows, cols, cyc, mb, pmin, pmax = CONFIGS[args.config]
     circ = inputs.random_grid_circuit(rows, cols, cyc, 0)
-    bits = inputs.random_bitstring(circ.n_qubits, rank)
+    bits = inputs.random_bitstring(circ.n_qubits, 0 if args.split_slices else rank)
     t_plan = time.perf_counter()
     prec = {"c64": 0, "bf16x3": 1, "tf32x3": 2}[args.precision]
     if args.plain:
@@ -401,15 +404,26 @@ def main():
                 json.dump({"kept_chains": plan.fused_chains()}, f)
     t_tune = time.perf_counter() - t_tune
     info = plan.info()
-    B = min(args.max_batch, n_sl)
+    my_b, my_e = 0, n_sl
+    if args.split_slices:
+        from paper_2004_10892_gb300.shard import sharded_amplitude, slice_range
+
+        my_b, my_e = slice_range(n_sl, rank, world)
+    B = min(args.max_batch, max(my_e - my_b, 1))
     free, _ = torch.cuda.mem_get_info()
     while B > 1 and plan.workspace_bytes(B) > 0.8 * free:
         B //= 2
     ws = torch.empty(plan.workspace_bytes(B), dtype=torch.uint8, device="cuda")
 
+    def one_step():
+        if args.split_slices:  # this rank's share of the slices, then one FP64 all-reduce (Eq. 5)
+            return sharded_amplitude(lambda b, e: tnq.contract_sliced(plan, bits, b, e, workspace=ws, max_batch=B,
+                                                                      stream=stream), n_sl)
+        return tnq.contract_sliced(plan, bits, workspace=ws, max_batch=B, stream=stream)
+
     # warm-up (also captures the CUDA graph)
     for _ in range(args.warmup):
-        amp = tnq.contract_sliced(plan, bits, workspace=ws, max_batch=B, stream=stream)
+        amp = one_step()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -422,7 +436,7 @@ def main():
         clk.t0 = t0
         e0.record(stream)
         for _ in range(args.steps):
-            amp = tnq.contract_sliced(plan, bits, workspace=ws, max_batch=B, stream=stream)
+            amp = one_step()
         e1.record(stream)
         torch.cuda.synchronize()
         clk.t1 = time.perf_counter()
@@ -434,10 +448,10 @@ def main():
         tt = torch.tensor([t_dev, t_wall], device="cuda", dtype=torch.float64)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_dev, t_wall = float(tt[0]), float(tt[1])
-    total_slices = args.steps * n_sl * world
+    total_slices = args.steps * n_sl * (1 if args.split_slices else world)
     value = total_slices / t_dev
     e2e_value = total_slices / t_wall
-    n_batches = (n_sl + B - 1) // B
+    n_batches = (my_e - my_b + B - 1) // B
     launches = args.steps * n_batches * L.tnq_internal_launches_per_batch(plan.handle)
 
     # live per-launch timing of one batch (CUDA events on the launching stream)
@@ -467,10 +481,12 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": "slices/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
+            "scaling": "strong" if args.split_slices else "weak", "vs_baseline": None,
             "dtype": {"c64": "c64", "bf16x3": "c64+3xbf16", "tf32x3": "c64+3xtf32"}[args.precision],
             "data": "synthetic",
-            "config": {"workload": f"grid {args.config} random circuit (seed 0), one amplitude per step per GPU",
+            "config": {"workload": f"grid {args.config} random circuit (seed 0), " +
+                       ("one amplitude per step, its slices split across the GPUs" if args.split_slices
+                        else "one amplitude per step per GPU"),
                        "n_qubits": circ.n_qubits, "p": info["p"], "n_slices": n_sl, "tau_full": info["tau_full"],
                        "tau": info["tau"], "max_bag": info["max_bag"], "batch": B,
                        "flops_per_slice": info["flops_per_slice"], "bytes_per_slice": info["bytes_per_slice"],

@@ -205,3 +205,103 @@ def batched_serving_workload(n_circuits: int = 64, bitstrings_per_circuit: int =
         bits = [random_bitstring(circ.n_qubits, (seed + i) * 1000 + j) for j in range(bitstrings_per_circuit)]
         out.append((circ, bits))
     return out
+
+
+# ---- general tensor networks (indices of any dimension L) --------------------
+@dataclass
+class TensorNetwork:
+    """A closed tensor network: dims[i] = number of values of index i; tensors
+    are (indices, complex128 array of shape (dims[i] for i in indices)), numpy
+    C order (the first listed index varies slowest)."""
+
+    dims: list
+    tensors: list
+    name: str = ""
+
+
+def _normal_pair(rng: SplitMix64):
+    """Two independent standard normal deviates (Box-Muller on two uniforms)."""
+    import math
+
+    u1 = 1.0 - rng.unit()  # (0, 1]
+    u2 = rng.unit()
+    r = math.sqrt(-2.0 * math.log(u1))
+    return r * math.cos(2 * math.pi * u2), r * math.sin(2 * math.pi * u2)
+
+
+def random_complex_array(shape, rng: SplitMix64, scale: float = 1.0, bias: complex = 0j):
+    """Entries bias + scale * z with z complex normal of unit variance (re, im
+    each of variance 1/2), drawn in C order."""
+    import numpy as np
+
+    n = 1
+    for d in shape:
+        n *= int(d)
+    out = np.empty(n, dtype=np.complex128)
+    for k in range(n):
+        a, b = _normal_pair(rng)
+        out[k] = bias + scale * complex(a, b) * 0.7071067811865476
+    return out.reshape(tuple(int(d) for d in shape))
+
+
+def random_lattice_network(rows: int, cols: int, L, seed: int, periodic: bool = False) -> TensorNetwork:
+    """A closed rows x cols lattice network: one index per nearest-neighbour bond
+    (dimension L, or drawn from the tuple L per bond), one tensor per site over
+    its bonds, complex normal entries scaled by prod over its legs of
+    dim^-1/4 (so that the value's typical magnitude is 1). `periodic` adds the
+    wrap-around bonds (a torus)."""
+    rng = SplitMix64(seed ^ 0x1A771CE5)
+    dims_choice = tuple(L) if isinstance(L, (tuple, list)) else (int(L),)
+    bonds = []
+    for r in range(rows):
+        for c in range(cols):
+            if c + 1 < cols or (periodic and cols > 2):
+                bonds.append(((r, c), (r, (c + 1) % cols)))
+            if r + 1 < rows or (periodic and rows > 2):
+                bonds.append(((r, c), ((r + 1) % rows, c)))
+    dims = [dims_choice[rng.below(len(dims_choice))] for _ in bonds]
+    legs = {(r, c): [] for r in range(rows) for c in range(cols)}
+    for i, (a, b) in enumerate(bonds):
+        legs[a].append(i)
+        legs[b].append(i)
+    tensors = []
+    for r in range(rows):
+        for c in range(cols):
+            idx = tuple(legs[(r, c)])
+            scale = 1.0
+            for i in idx:
+                scale *= dims[i] ** -0.25
+            tensors.append((idx, random_complex_array([dims[i] for i in idx], rng, scale)))
+    return TensorNetwork(dims, tensors, f"lattice{rows}x{cols}_L{'-'.join(map(str, dims_choice))}_s{seed}")
+
+
+def random_ring_network(n: int, L: int, seed: int) -> TensorNetwork:
+    """n matrices M_k[i_k, i_{k+1 mod n}] around a ring (index k of dimension L):
+    its value is trace(M_0 M_1 ... M_{n-1})."""
+    rng = SplitMix64(seed ^ 0x21A6)
+    dims = [int(L)] * n
+    tensors = [((k, (k + 1) % n), random_complex_array([L, L], rng, L ** -0.5)) for k in range(n)]
+    return TensorNetwork(dims, tensors, f"ring{n}_L{L}_s{seed}")
+
+
+def random_small_network(n_indices: int, n_tensors: int, max_rank: int, dims, seed: int) -> TensorNetwork:
+    """Arbitrary seeded network for small checks: index dimensions drawn from
+    `dims`, each tensor over 0..max_rank distinct random indices (rank-0
+    scalars included); every index is then added to some tensor so that all
+    appear."""
+    rng = SplitMix64(seed ^ 0x5A11)
+    dl = [dims[rng.below(len(dims))] for _ in range(n_indices)]
+    idx_sets = []
+    for _ in range(n_tensors):
+        r = rng.below(max_rank + 1)
+        pool = list(range(n_indices))
+        pick = []
+        for _ in range(min(r, n_indices)):
+            pick.append(pool.pop(rng.below(len(pool))))
+        idx_sets.append(pick)
+    used = {i for s in idx_sets for i in s}
+    for i in range(n_indices):
+        if i not in used:
+            idx_sets[rng.below(n_tensors)].append(i)
+    tensors = [(tuple(s), random_complex_array([dl[i] for i in s], rng)) for s in idx_sets]
+    return TensorNetwork(dl, tensors, f"small_n{n_indices}_t{n_tensors}_s{seed}")
