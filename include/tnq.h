@@ -163,6 +163,35 @@ void tnq_plan_opts_default(tnq_plan_opts* opts);
  * unknown gate kind, n_qubits outside [1, 4096], or bad opts. */
 tnq_status tnq_plan_from_circuit(int32_t n_qubits, const tnq_gate* gates, size_t n_gates,
                                  const tnq_plan_opts* opts, tnq_plan** out_plan);
+/* tnq_plan_from_network: a general closed tensor network whose indices have
+ * any number of values L (Section II.A defines the network and its bucket
+ * elimination for any index dimension; Eq. 2's cost per bucket is then
+ * O(L^r)). Its value is the sum, over every assignment of values to all
+ * indices, of the product of the selected tensor entries; tnq_contract_sliced
+ * returns it (bits may be NULL: a general network has no qubits).
+ *  n_indices, dims: index i has dims[i] values, 1 <= dims[i] <= 2^16.
+ *  n_tensors >= 1; tensor t lists its indices at
+ *    tensor_indices[tensor_offsets[t] .. tensor_offsets[t+1]) (distinct ids in
+ *    [0, n_indices); tensor_offsets has n_tensors+1 entries, [0] = 0; rank 0
+ *    is a scalar). Every index must appear in some tensor.
+ *  tensor_data: complex128 as (re, im) doubles, tensors back to back, each in
+ *    row-major order over its index list (the first index varies slowest):
+ *    tensor t starts at the sum of the entry counts of tensors 0..t-1.
+ * Encoding: each index becomes ceil(log2 L) binary variables (its value's
+ * digits, digit 0 lowest); entries whose digits spell a value >= L are zero,
+ * so the value is unchanged, and the planner orders and slices these binary
+ * variables like circuit variables (a slice fixes digits: Eq. 4 on the
+ * values that carry them). tnq_plan_order / tnq_plan_sliced report variable
+ * (index, digit) in their (qubit, segment) arrays, and tnq_plan_info_get
+ * reports n_qubits = 0. A tensor may have at most 16 binary variables
+ * (2^16 entries after encoding). The library copies the data (stored in
+ * complex64, each tensor scaled by an exact power of two that the result
+ * undoes in FP64). TNQ_EINVAL on a bad index id, a repeated index in one
+ * tensor, an unused index, a non-finite entry, a too-large tensor or bad
+ * opts. */
+tnq_status tnq_plan_from_network(int32_t n_indices, const int32_t* dims, size_t n_tensors,
+                                 const int64_t* tensor_offsets, const int32_t* tensor_indices,
+                                 const double* tensor_data, const tnq_plan_opts* opts, tnq_plan** out_plan);
 void tnq_plan_destroy(tnq_plan* plan);
 /* Size and cost of the plan (Section IV: a slice needs memory M = O(2^tau)
  * and P = O(2^(tau+1)) operations; the whole amplitude 2^p times that):
@@ -191,7 +220,8 @@ size_t tnq_plan_workspace_bytes(const tnq_plan* plan, uint32_t batch);
 /* tnq_contract_sliced: sum over slices s in [slice_begin, slice_end) of the
  * sliced sub-contraction sigma_s (Eq. 4) of <bits|C|0^n>, i.e. the partial
  * sum of Eq. 5. [0, n_slices) gives the amplitude.
- *  bits: host, n_qubits bytes (0/1).
+ *  bits: host, n_qubits bytes (0/1); may be NULL for a general network
+ *    (tnq_plan_from_network), which has no qubits.
  *  workspace: device memory of ws_bytes >= tnq_plan_workspace_bytes(plan, 1);
  *    the call runs as many slices at once as the workspace holds (a power of
  *    two, at most max_batch if max_batch > 0).

@@ -69,6 +69,100 @@ void tnq_plan_opts_default(tnq_plan_opts* o) {
   o->leaf_absorb = 1;
 }
 
+static bool valid_opts(const tnq_plan_opts& o) {
+  return !(o.slicer < 0 || o.slicer > TNQ_SLICER_BETWEENNESS || o.min_p < 0 || o.max_p < o.min_p ||
+           o.max_p > 62 || o.max_bag_log2 < 0 || o.max_bag_log2 > 40 || o.precision < 0 ||
+           o.precision > TNQ_PREC_SPLIT_TF32 || o.ordering < 0 || o.ordering > TNQ_ORDER_MIN_DEGREE ||
+           o.fuse_min_rank < 0 || o.fuse_min_rank > 40 || o.leaf_absorb < 0 || o.leaf_absorb > 1 ||
+           o.reorder_every < 0 || o.order_trials < 0 || o.order_trials > 4096);
+}
+
+// Planning shared by circuits and general networks, once P->net is built:
+// the free-variable graph, greedy orders (order_trials of them), greedy
+// mu-treewidth deletion (Algorithm 2), and the compiled bucket program with
+// its GEMM chains, leaf absorption and fused chains.
+static void plan_network(tnq_plan* P, const tnq_plan_opts& o) {
+  P->graph = network_graph(P->net);
+  // order_trials > 1: also try greedy orders with seeded random ties and keep
+  // the trial whose sliced plan has the lowest cost 2^p * sum over steps 2^bag
+  // (bag limit met first; the earliest trial among equals); trial 0 is the
+  // deterministic order. Trials are independent and run on host threads
+  // (TNQ_PLAN_THREADS caps their number); the choice does not depend on it.
+  const int trials = std::max(1, o.order_trials);
+  struct Trial {
+    std::vector<int> ord, mu, order;
+    int tau = 0;
+    double cost = 0;
+    bool fits = false;
+  };
+  std::vector<Trial> tr(trials);
+  auto run_trial = [&](int trial) {
+    uint64_t rs = (o.seed ^ 0x9E3779B97F4A7C15ull) + (uint64_t)trial;
+    Trial& T = tr[trial];
+    T.ord = greedy_order(P->graph, o.ordering, trial ? &rs : nullptr);
+    DeletionResult R = greedy_deletion(P->graph, T.ord, o.slicer, o.min_p, o.max_p, o.max_bag_log2, o.seed,
+                                       o.td_rebuild != 0,
+                                       o.slicer == TNQ_SLICER_LEARNED ? &learned_propose : nullptr, nullptr,
+                                       o.reorder_every, o.ordering);
+    Graph reduced = P->graph;
+    for (int v : R.mu) delete_vertex(reduced, v);
+    std::vector<int> bags;
+    T.tau = treewidth_of_order(reduced, R.reduced_order, &bags);
+    int max_bag = 0;
+    for (int b : bags) {
+      T.cost += std::ldexp(1.0, b);
+      max_bag = std::max(max_bag, b);
+    }
+    T.cost = std::ldexp(T.cost, (int)R.mu.size());
+    T.fits = o.max_bag_log2 <= 0 || max_bag <= o.max_bag_log2;
+    T.mu = std::move(R.mu);
+    T.order = std::move(R.reduced_order);
+  };
+  int nth = std::min(trials, std::max(1, (int)std::thread::hardware_concurrency()));
+  if (const char* e = std::getenv("TNQ_PLAN_THREADS")) nth = std::max(1, std::min(nth, std::atoi(e)));
+  if (nth <= 1) {
+    for (int t = 0; t < trials; ++t) run_trial(t);
+  } else {
+    // nth - 1 helper threads and this one take trials from a shared counter
+    // (if a helper cannot be started, the others still run every trial)
+    std::atomic<int> next(0);
+    std::vector<std::exception_ptr> err(nth);
+    auto work = [&](int w) {
+      try {
+        for (int t; (t = next.fetch_add(1)) < trials;) run_trial(t);
+      } catch (...) {
+        err[w] = std::current_exception();
+      }
+    };
+    std::vector<std::thread> pool;
+    for (int w = 1; w < nth; ++w) {
+      try {
+        pool.emplace_back(work, w);
+      } catch (const std::exception&) {
+        break;
+      }
+    }
+    work(0);
+    for (auto& th : pool) th.join();
+    for (auto& e : err)
+      if (e) std::rethrow_exception(e);
+  }
+  int best = 0;
+  for (int t = 1; t < trials; ++t)
+    if ((tr[t].fits && !tr[best].fits) || (tr[t].fits == tr[best].fits && tr[t].cost < tr[best].cost)) best = t;
+  P->order_full = std::move(tr[best].ord);
+  P->mu = std::move(tr[best].mu);
+  P->order = std::move(tr[best].order);
+  P->tau = tr[best].tau;
+  P->tau_full = treewidth_of_order(P->graph, P->order_full);
+  P->prog = compile_program(P->net, P->order, P->mu);
+  if (o.precision != TNQ_PREC_C64)
+    find_gemm_chains(P->prog, P->order, o.gemm_min_k_log2 > 0 ? o.gemm_min_k_log2 : 4, 8);
+  if (o.leaf_absorb) absorb_leaves(P->prog);
+  fuse_chains(P->prog, P->order, o.fuse_min_rank);
+  P->amp_scale_log2 = -0.5 * P->net.n_sqrt2 + (double)P->net.leaf_exp;
+}
+
 tnq_status tnq_plan_from_circuit(int32_t n_qubits, const tnq_gate* gates, size_t n_gates,
                                  const tnq_plan_opts* opts, tnq_plan** out_plan) {
   if (!out_plan) { set_error("out_plan is NULL"); return TNQ_EINVAL; }
@@ -77,11 +171,7 @@ tnq_status tnq_plan_from_circuit(int32_t n_qubits, const tnq_gate* gates, size_t
   tnq_plan_opts o;
   tnq_plan_opts_default(&o);
   if (opts) o = *opts;
-  if (o.slicer < 0 || o.slicer > TNQ_SLICER_BETWEENNESS || o.min_p < 0 || o.max_p < o.min_p ||
-      o.max_p > 62 || o.max_bag_log2 < 0 || o.max_bag_log2 > 40 || o.precision < 0 ||
-      o.precision > TNQ_PREC_SPLIT_TF32 || o.ordering < 0 || o.ordering > TNQ_ORDER_MIN_DEGREE ||
-      o.fuse_min_rank < 0 || o.fuse_min_rank > 40 || o.leaf_absorb < 0 || o.leaf_absorb > 1 ||
-      o.reorder_every < 0 || o.order_trials < 0 || o.order_trials > 4096) {
+  if (!valid_opts(o)) {
     set_error("invalid plan options");
     return TNQ_EINVAL;
   }
@@ -97,85 +187,38 @@ tnq_status tnq_plan_from_circuit(int32_t n_qubits, const tnq_gate* gates, size_t
     }
     std::string err = build_network(n_qubits, gi.data(), n_gates, P->net);
     if (!err.empty()) { set_error(err); return TNQ_EINVAL; }
-    P->graph = network_graph(P->net);
-    // order_trials > 1: also try greedy orders with seeded random ties and keep
-    // the trial whose sliced plan has the lowest cost 2^p * sum over steps 2^bag
-    // (bag limit met first; the earliest trial among equals); trial 0 is the
-    // deterministic order. Trials are independent and run on host threads
-    // (TNQ_PLAN_THREADS caps their number); the choice does not depend on it.
-    const int trials = std::max(1, o.order_trials);
-    struct Trial {
-      std::vector<int> ord, mu, order;
-      int tau = 0;
-      double cost = 0;
-      bool fits = false;
-    };
-    std::vector<Trial> tr(trials);
-    auto run_trial = [&](int trial) {
-      uint64_t rs = (o.seed ^ 0x9E3779B97F4A7C15ull) + (uint64_t)trial;
-      Trial& T = tr[trial];
-      T.ord = greedy_order(P->graph, o.ordering, trial ? &rs : nullptr);
-      DeletionResult R = greedy_deletion(P->graph, T.ord, o.slicer, o.min_p, o.max_p, o.max_bag_log2, o.seed,
-                                         o.td_rebuild != 0,
-                                         o.slicer == TNQ_SLICER_LEARNED ? &learned_propose : nullptr, nullptr,
-                                         o.reorder_every, o.ordering);
-      Graph reduced = P->graph;
-      for (int v : R.mu) delete_vertex(reduced, v);
-      std::vector<int> bags;
-      T.tau = treewidth_of_order(reduced, R.reduced_order, &bags);
-      int max_bag = 0;
-      for (int b : bags) {
-        T.cost += std::ldexp(1.0, b);
-        max_bag = std::max(max_bag, b);
-      }
-      T.cost = std::ldexp(T.cost, (int)R.mu.size());
-      T.fits = o.max_bag_log2 <= 0 || max_bag <= o.max_bag_log2;
-      T.mu = std::move(R.mu);
-      T.order = std::move(R.reduced_order);
-    };
-    int nth = std::min(trials, std::max(1, (int)std::thread::hardware_concurrency()));
-    if (const char* e = std::getenv("TNQ_PLAN_THREADS")) nth = std::max(1, std::min(nth, std::atoi(e)));
-    if (nth <= 1) {
-      for (int t = 0; t < trials; ++t) run_trial(t);
-    } else {
-      // nth - 1 helper threads and this one take trials from a shared counter
-      // (if a helper cannot be started, the others still run every trial)
-      std::atomic<int> next(0);
-      std::vector<std::exception_ptr> err(nth);
-      auto work = [&](int w) {
-        try {
-          for (int t; (t = next.fetch_add(1)) < trials;) run_trial(t);
-        } catch (...) {
-          err[w] = std::current_exception();
-        }
-      };
-      std::vector<std::thread> pool;
-      for (int w = 1; w < nth; ++w) {
-        try {
-          pool.emplace_back(work, w);
-        } catch (const std::exception&) {
-          break;
-        }
-      }
-      work(0);
-      for (auto& th : pool) th.join();
-      for (auto& e : err)
-        if (e) std::rethrow_exception(e);
-    }
-    int best = 0;
-    for (int t = 1; t < trials; ++t)
-      if ((tr[t].fits && !tr[best].fits) || (tr[t].fits == tr[best].fits && tr[t].cost < tr[best].cost)) best = t;
-    P->order_full = std::move(tr[best].ord);
-    P->mu = std::move(tr[best].mu);
-    P->order = std::move(tr[best].order);
-    P->tau = tr[best].tau;
-    P->tau_full = treewidth_of_order(P->graph, P->order_full);
-    P->prog = compile_program(P->net, P->order, P->mu);
-    if (o.precision != TNQ_PREC_C64)
-      find_gemm_chains(P->prog, P->order, o.gemm_min_k_log2 > 0 ? o.gemm_min_k_log2 : 4, 8);
-    if (o.leaf_absorb) absorb_leaves(P->prog);
-    fuse_chains(P->prog, P->order, o.fuse_min_rank);
-    P->amp_scale_log2 = -0.5 * P->net.n_sqrt2;
+    plan_network(P.get(), o);
+    *out_plan = P.release();
+    return TNQ_OK;
+  })
+}
+
+tnq_status tnq_plan_from_network(int32_t n_indices, const int32_t* dims, size_t n_tensors,
+                                 const int64_t* tensor_offsets, const int32_t* tensor_indices,
+                                 const double* tensor_data, const tnq_plan_opts* opts, tnq_plan** out_plan) {
+  if (!out_plan) { set_error("out_plan is NULL"); return TNQ_EINVAL; }
+  *out_plan = nullptr;
+  if ((n_indices > 0 && !dims) || (n_tensors > 0 && (!tensor_offsets || !tensor_data)) ||
+      (n_tensors > 0 && tensor_offsets[n_tensors] > 0 && !tensor_indices)) {
+    set_error("NULL argument");
+    return TNQ_EINVAL;
+  }
+  if (n_tensors == 0) { set_error("a network needs at least one tensor"); return TNQ_EINVAL; }
+  if (tensor_offsets[0] != 0) { set_error("tensor_offsets[0] must be 0"); return TNQ_EINVAL; }
+  tnq_plan_opts o;
+  tnq_plan_opts_default(&o);
+  if (opts) o = *opts;
+  if (!valid_opts(o)) {
+    set_error("invalid plan options");
+    return TNQ_EINVAL;
+  }
+  TNQ_TRY({
+    std::unique_ptr<tnq_plan> P(new tnq_plan());
+    P->opts = o;
+    std::string err = build_general_network(n_indices, dims, n_tensors, tensor_offsets, tensor_indices,
+                                            tensor_data, P->net);
+    if (!err.empty()) { set_error(err); return TNQ_EINVAL; }
+    plan_network(P.get(), o);
     *out_plan = P.release();
     return TNQ_OK;
   })

@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <iterator>
 
 namespace tnq {
@@ -113,12 +114,94 @@ std::string build_network(int n_qubits, const GateIn* gates, size_t n_gates, Net
   return "";
 }
 
+std::string build_general_network(int n_indices, const int32_t* dims, size_t n_tensors, const int64_t* off,
+                                  const int32_t* idx, const double* data, Network& net) {
+  if (n_indices < 0 || n_indices > (1 << 24)) return "n_indices must be in [0, 2^24]";
+  if (n_tensors > ((size_t)1 << 24)) return "too many tensors";
+  net = Network();
+  net.general = true;
+  net.index_dim.assign(dims, dims + n_indices);
+  std::vector<int> first(n_indices + 1, 0);  // first binary variable of each index
+  for (int i = 0; i < n_indices; ++i) {
+    if (dims[i] < 1 || dims[i] > (1 << LEAF_VMAX)) return "index " + std::to_string(i) + ": dimension outside [1, 2^16]";
+    int b = 0;
+    while ((1 << b) < dims[i]) ++b;
+    first[i + 1] = first[i] + b;
+    for (int j = 0; j < b; ++j) {
+      Var v;
+      v.q = i;
+      v.seg = j;
+      v.kind = VAR_FREE;
+      net.vars.push_back(v);
+    }
+  }
+  std::vector<char> used(n_indices, 0);
+  size_t data_pos = 0;
+  for (size_t t = 0; t < n_tensors; ++t) {
+    if (off[t + 1] < off[t] || off[t] < 0) return "tensor " + std::to_string(t) + ": bad index offsets";
+    const int rank = (int)(off[t + 1] - off[t]);
+    const int32_t* ti = idx + off[t];
+    GateTensor g;
+    g.var.clear();
+    size_t entries = 1;
+    for (int k = 0; k < rank; ++k) {
+      const int i = ti[k];
+      if (i < 0 || i >= n_indices) return "tensor " + std::to_string(t) + ": index id out of range";
+      for (int k2 = 0; k2 < k; ++k2)
+        if (ti[k2] == i) return "tensor " + std::to_string(t) + ": index " + std::to_string(i) + " listed twice";
+      used[i] = 1;
+      entries *= (size_t)dims[i];
+      for (int v = first[i]; v < first[i + 1]; ++v) g.var.push_back(v);
+    }
+    g.nv = (int)g.var.size();
+    if (g.nv > LEAF_VMAX) return "tensor " + std::to_string(t) + ": more than 2^16 entries after binary encoding";
+    g.val.assign(std::max<size_t>(4, (size_t)1 << g.nv), std::complex<float>(0.f, 0.f));
+    // largest |entry| -> exponent e with max / 2^e in [0.5, 1)
+    double mx = 0;
+    for (size_t e = 0; e < entries; ++e) {
+      const double re = data[2 * (data_pos + e)], im = data[2 * (data_pos + e) + 1];
+      if (!std::isfinite(re) || !std::isfinite(im)) return "tensor " + std::to_string(t) + ": non-finite entry";
+      mx = std::max(mx, std::max(std::fabs(re), std::fabs(im)));
+    }
+    int ex = 0;
+    if (mx > 0) std::frexp(mx, &ex);
+    net.leaf_exp += ex;
+    // entry of binary assignment a: the digits of each index spell its value x_k
+    for (size_t a = 0; a < ((size_t)1 << g.nv); ++a) {
+      size_t row = 0, bitpos = 0;
+      bool pad = false;
+      for (int k = 0; k < rank; ++k) {
+        const int i = ti[k];
+        const int nb = first[i + 1] - first[i];
+        const size_t x = (a >> bitpos) & (((size_t)1 << nb) - 1);
+        bitpos += nb;
+        if (x >= (size_t)dims[i]) pad = true;
+        row = row * (size_t)dims[i] + x;
+      }
+      if (pad) continue;
+      const double re = std::ldexp(data[2 * (data_pos + row)], -ex), im = std::ldexp(data[2 * (data_pos + row) + 1], -ex);
+      g.val[a] = std::complex<float>((float)re, (float)im);
+    }
+    data_pos += entries;
+    net.tensors.push_back(g);
+  }
+  for (int i = 0; i < n_indices; ++i)
+    if (!used[i]) return "index " + std::to_string(i) + " appears in no tensor";
+  for (size_t i = 0; i < net.vars.size(); ++i) {
+    net.vars[i].free_id = (int)net.free_vars.size();
+    net.free_vars.push_back((int)i);
+  }
+  return "";
+}
+
 Graph network_graph(const Network& net) {
   Graph g((int)net.free_vars.size());
   for (const auto& t : net.tensors) {
-    if (t.nv < 2) continue;
-    int a = net.vars[t.var[0]].free_id, b = net.vars[t.var[1]].free_id;
-    if (a >= 0 && b >= 0) g.add_edge(a, b);
+    for (int x = 0; x < t.nv; ++x)
+      for (int y = x + 1; y < t.nv; ++y) {
+        int a = net.vars[t.var[x]].free_id, b = net.vars[t.var[y]].free_id;
+        if (a >= 0 && b >= 0) g.add_edge(a, b);
+      }
   }
   return g;
 }
@@ -154,10 +237,13 @@ Program compile_program(const Network& net, const std::vector<int>& order, const
       P.scalar_leaves.push_back((int)gi);
       continue;
     }
-    for (int e = 0; e < 4; ++e) {
-      const float m = std::abs(gt.val[e]);
-      if (m != 0.f && (m < 0.0625f || m > 16.f)) t.wide_range = true;
-    }
+    // (a general network's tensors are stored with their largest |entry| in
+    // [0.5, 1), so none is wide-range)
+    if (!net.general)
+      for (int e = 0; e < 4; ++e) {
+        const float m = std::abs(gt.val[e]);
+        if (m != 0.f && (m < 0.0625f || m > 16.f)) t.wide_range = true;
+      }
     std::sort(t.vars.begin(), t.vars.end(), by_pos);
     t.vars.erase(std::unique(t.vars.begin(), t.vars.end()), t.vars.end());
     P.tensors.push_back(t);
@@ -294,6 +380,65 @@ static std::vector<int> bag_of(const Program& P, const PBucket& b) {
   return u;
 }
 
+// Tile shape of a fused chain: the local variables L are the chain's
+// eliminated ones plus n_local - |elim| of its output variables; the others
+// are tile variables. The earliest `keep_low` output variables are always
+// local, so the output is written in runs of 2^keep_low consecutive entries.
+// The rest are chosen greedily (ties to the earliest position) to minimise
+// sum_j 2^|vars_j & L| over the chain's external inputs j: the entries of its
+// operands one tile touches, i.e. what a block reads from L2 per tile (an
+// input holding no local variable becomes a per-block constant). With
+// keep_low >= the number of output variables this is the earliest-position
+// choice. TNQ_GROUP_TILE_LOW (environment, read once) overrides keep_low.
+static int group_tile_low() {
+  static const int v = [] {
+    const char* e = std::getenv("TNQ_GROUP_TILE_LOW");
+    return e ? std::atoi(e) : 3;
+  }();
+  return v;
+}
+
+static void choose_tile(const Program& P, FusedGroup& g, const std::vector<int>& outv, int n_local) {
+  const int keep_low = group_tile_low();
+  std::vector<char> local(outv.size(), 0);
+  int n = (int)g.local_vars.size();
+  for (size_t i = 0; i < outv.size() && n < n_local && (int)i < keep_low; ++i, ++n) local[i] = 1;
+  // per external input: which output variables it holds, and its local count so far
+  std::vector<std::vector<char>> holds;
+  std::vector<int> cnt;
+  for (int t : g.ext_inputs) {
+    const auto& tv = P.tensors[t].vars;
+    std::vector<char> h(outv.size(), 0);
+    int c = 0;
+    for (size_t i = 0; i < outv.size(); ++i) {
+      h[i] = std::find(tv.begin(), tv.end(), outv[i]) != tv.end();
+      if (h[i] && local[i]) ++c;
+    }
+    for (int u : g.local_vars) c += std::find(tv.begin(), tv.end(), u) != tv.end();
+    holds.push_back(h);
+    cnt.push_back(c);
+  }
+  for (; n < n_local; ++n) {
+    int best = -1;
+    double best_cost = 0;
+    for (size_t i = 0; i < outv.size(); ++i) {
+      if (local[i]) continue;
+      double cost = 0;
+      for (size_t j = 0; j < holds.size(); ++j) cost += std::ldexp(1.0, cnt[j] + (holds[j][i] ? 1 : 0));
+      if (best < 0 || cost < best_cost) {
+        best = (int)i;
+        best_cost = cost;
+      }
+    }
+    if (best < 0) break;
+    local[best] = 1;
+    for (size_t j = 0; j < holds.size(); ++j) cnt[j] += holds[j][best];
+  }
+  for (size_t i = 0; i < outv.size(); ++i)
+    if (local[i]) g.local_vars.push_back(outv[i]);
+    else g.tile_vars.push_back(outv[i]);
+}
+
 void fuse_chains(Program& P, const std::vector<int>& order, int min_rank) {
   const int nb = (int)P.buckets.size();
   if (P.bytes_unfused == 0) P.bytes_unfused = P.bytes_per_slice;
@@ -354,9 +499,7 @@ void fuse_chains(Program& P, const std::vector<int>& order, int min_rank) {
     std::sort(U2.begin(), U2.end(), by_pos);
     const int n_local = std::min<int>(GL_MAX, (int)U2.size());
     g.local_vars = elim;
-    for (int v : outv)
-      if ((int)g.local_vars.size() < n_local) g.local_vars.push_back(v);
-      else g.tile_vars.push_back(v);
+    choose_tile(P, g, outv, n_local);
     std::sort(g.local_vars.begin(), g.local_vars.end(), by_pos);
     const int gi = (int)P.groups.size();
     for (int b : chain) P.group_of[b] = gi;

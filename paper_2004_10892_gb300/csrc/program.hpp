@@ -29,15 +29,23 @@ struct Var {
   int free_id = -1;  // index among free variables
 };
 
-// A gate tensor over one or two network variables; entry (a, b) at a + 2b.
-// Non-diagonal gates with a 1/sqrt2 prefactor (H, X^1/2, Y^1/2) are stored
-// multiplied by sqrt2; the plan keeps the count of such factors and applies
-// 2^(-count/2) to the amplitude in FP64.
+// A network tensor over nv two-valued network variables: entry index
+// sum_x a_x 2^x for values a_x of var[x]. Circuit gates have nv <= 2 (entry
+// (a, b) at a + 2b; val always holds 4 entries); a general network's tensor
+// has its indices' binary digits as variables and 2^nv entries. Non-diagonal
+// gates with a 1/sqrt2 prefactor (H, X^1/2, Y^1/2) are stored multiplied by
+// sqrt2; the plan keeps the count of such factors and applies 2^(-count/2) to
+// the amplitude in FP64. A general tensor is stored divided by 2^e (its
+// largest |entry| in [0.5, 1)); the plan applies 2^(sum of e) in FP64.
 struct GateTensor {
   int nv = 0;
-  int var[2] = {-1, -1};
-  std::complex<float> val[4];
+  std::vector<int> var;
+  std::vector<std::complex<float>> val;
+  GateTensor() : var(2, -1), val(4) {}
 };
+
+// Most binary variables one tensor of a general network may have (2^16 entries).
+constexpr int LEAF_VMAX = 16;
 
 struct Network {
   int n_qubits = 0;
@@ -45,7 +53,12 @@ struct Network {
   std::vector<GateTensor> tensors;
   std::vector<int> free_vars;  // network var id of each free variable
   int n_sqrt2 = 0;             // number of 1/sqrt2 factors taken out of gate values
+  long long leaf_exp = 0;      // general networks: sum of the exponents taken out of the tensors
   std::vector<int> inout_qubits;  // qubits whose input segment is also the output
+  // General network (tnq_plan_from_network): no qubits or wires; variable
+  // (q, seg) is binary digit seg of index q, whose dimension is index_dim[q].
+  bool general = false;
+  std::vector<int> index_dim;
 };
 
 struct GateIn {
@@ -55,6 +68,16 @@ struct GateIn {
 
 // Returns an empty string on success, else an error message.
 std::string build_network(int n_qubits, const GateIn* gates, size_t n_gates, Network& out);
+
+// General closed network (Section II.A for indices of any dimension L): index
+// i has dims[i] values and becomes ceil(log2 dims[i]) binary variables (its
+// digits); tensor t lists its indices at idx[off[t] .. off[t+1]) and its
+// entries, complex128 (re, im) pairs in row-major order over that list (the
+// first index varies slowest), at data[2 * data_off[t] ...], where data_off
+// is the running sum of the tensors' entry counts. Entries whose digits spell
+// a value >= dims[i] are zero. Returns an empty string on success.
+std::string build_general_network(int n_indices, const int32_t* dims, size_t n_tensors, const int64_t* off,
+                                  const int32_t* idx, const double* data, Network& out);
 
 // Free-variable graph of the network (vertices = free ids).
 Graph network_graph(const Network& net);

@@ -70,14 +70,21 @@ struct HoistDev {
 };
 
 struct LeafDev {
-  float2 val[4];      // gate entries, (a, b) at a + 2b
-  int nv;             // gate variables (1 or 2)
-  int vkind[2];       // 0 free, 1 fixed to 0 (input wire), 2 output bit, 3 sliced
-  int varg[2];        // free: bit in the leaf; output: qubit; sliced: j
+  float2 val[4];      // entries when nv <= 2: (a, b) at a + 2b
+  long long tab;      // nv > 2 (general networks): element offset of the 2^nv entries in the leaf value table
+  long long off;      // element offset in the arena
+  int nv;             // tensor variables (binary; entry index sum_x a_x 2^x)
   int n_free;         // leaf rank
   int dep;            // item-dependent in this configuration
-  long long off;      // element offset in the arena
+  int pad;
+  signed char vkind[LEAF_VMAX];  // 0 free, 1 fixed to 0 (input wire), 2 output bit, 3 sliced
+  short varg[LEAF_VMAX];         // free: bit in the leaf; output: qubit; sliced: j
 };
+
+// Entry a of a leaf: inline for gates, from the value table for general tensors.
+__device__ __forceinline__ float2 leaf_entry(const LeafDev& L, const float2* __restrict__ vals, int a) {
+  return L.nv <= 2 ? L.val[a] : vals[L.tab + a];
+}
 
 struct FinalDev {
   long long off;
@@ -117,7 +124,8 @@ __device__ __forceinline__ int bit_of(const unsigned* bits, int n_words, int bro
 // K5: restrict every gate tensor to the item's fixed values (input 0, output
 // bits, sliced values: Eq. 4).
 __global__ void k_leaf_init(const LeafDev* __restrict__ leaves, int n_leaves, const BatchHdr* __restrict__ hdr_p,
-                            const unsigned* __restrict__ bits, float2* __restrict__ arena, int B) {
+                            const unsigned* __restrict__ bits, const float2* __restrict__ vals,
+                            float2* __restrict__ arena, int B) {
   const BatchHdr h = *hdr_p;
   long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)n_leaves * B) return;
@@ -129,17 +137,19 @@ __global__ void k_leaf_init(const LeafDev* __restrict__ leaves, int n_leaves, co
   bool valid;
   item_decode(h, item, &slice, &brow, &valid);
   float2* out = arena + L.off + (L.dep ? ((long long)item << L.n_free) : 0ll);
+  // the fixed variables' part of the entry index is the same for every entry
+  int a_fixed = 0;
+  for (int x = 0; x < L.nv; ++x) {
+    int a = 0;
+    if (L.vkind[x] == 2) a = bit_of(bits, h.n_words, brow, L.varg[x]);
+    else if (L.vkind[x] == 3) a = (int)((slice >> L.varg[x]) & 1ull);
+    a_fixed |= a << x;
+  }
   for (int e = 0; e < (1 << L.n_free); ++e) {
-    int a[2] = {0, 0};
-    for (int x = 0; x < L.nv; ++x) {
-      switch (L.vkind[x]) {
-        case 0: a[x] = (e >> L.varg[x]) & 1; break;
-        case 1: a[x] = 0; break;
-        case 2: a[x] = bit_of(bits, h.n_words, brow, L.varg[x]); break;
-        default: a[x] = (int)((slice >> L.varg[x]) & 1ull); break;
-      }
-    }
-    out[e] = L.val[a[0] + 2 * a[1]];
+    int a = a_fixed;
+    for (int x = 0; x < L.nv; ++x)
+      if (L.vkind[x] == 0) a |= ((e >> L.varg[x]) & 1) << x;
+    out[e] = leaf_entry(L, vals, a);
   }
 }
 
@@ -147,7 +157,7 @@ __global__ void k_leaf_init(const LeafDev* __restrict__ leaves, int n_leaves, co
 // without a non-diagonal gate, per item (FP64).
 __global__ void k_scalar_init(const LeafDev* __restrict__ sl, int n_sl, const int* __restrict__ inout_q, int n_inout,
                               const BatchHdr* __restrict__ hdr_p, const unsigned* __restrict__ bits,
-                              double2* __restrict__ item_scalar, int B) {
+                              const float2* __restrict__ vals, double2* __restrict__ item_scalar, int B) {
   const BatchHdr h = *hdr_p;
   int item = blockIdx.x * blockDim.x + threadIdx.x;
   if (item >= B) return;
@@ -157,13 +167,13 @@ __global__ void k_scalar_init(const LeafDev* __restrict__ sl, int n_sl, const in
   item_decode(h, item, &slice, &brow, &valid);
   double re = 1.0, im = 0.0;
   for (int i = 0; i < n_sl; ++i) {
-    const LeafDev L = sl[i];
-    int a[2] = {0, 0};
+    const LeafDev& L = sl[i];
+    int a = 0;
     for (int x = 0; x < L.nv; ++x) {
-      if (L.vkind[x] == 2) a[x] = bit_of(bits, h.n_words, brow, L.varg[x]);
-      else if (L.vkind[x] == 3) a[x] = (int)((slice >> L.varg[x]) & 1ull);
+      if (L.vkind[x] == 2) a |= bit_of(bits, h.n_words, brow, L.varg[x]) << x;
+      else if (L.vkind[x] == 3) a |= (int)((slice >> L.varg[x]) & 1ull) << x;
     }
-    const float2 v = L.val[a[0] + 2 * a[1]];
+    const float2 v = leaf_entry(L, vals, a);
     const double nr = re * v.x - im * v.y, ni = re * v.y + im * v.x;
     re = nr;
     im = ni;
@@ -1216,6 +1226,8 @@ struct ExecConfig {
   std::vector<int> hoist_first;      // per level: first entry in hoist_dev (one past the last level at the end)
   std::vector<int> hoist_blocks;     // per level: blocks of its launch
   HoistDev* d_hoist = nullptr;
+  std::vector<float2> vals;          // leaf value table: entries of general-network tensors with > 2 variables
+  float2* d_vals = nullptr;
   void* ws = nullptr;                // workspace the graph was captured for
   cudaGraphExec_t exec = nullptr;
 };
@@ -1245,6 +1257,7 @@ struct DeviceState {
       cudaFree(c->d_inout);
       cudaFree(c->d_finals);
       cudaFree(c->d_hoist);
+      cudaFree(c->d_vals);
       delete c;
     }
   }
@@ -1252,11 +1265,20 @@ struct DeviceState {
 
 void destroy_device_state(DeviceState* s) { delete s; }
 
-static LeafDev make_leafdev(const tnq_plan& P, const PTensor* pt, int gate, const Layout* L, int tid) {
+// Leaf record of network tensor `gate`; general tensors with more than two
+// variables append their entries to `vals` (the configuration's leaf value table).
+static LeafDev make_leafdev(const tnq_plan& P, const PTensor* pt, int gate, const Layout* L, int tid,
+                            std::vector<float2>* vals) {
   const GateTensor& gt = P.net.tensors[gate];
   LeafDev d;
   std::memset(&d, 0, sizeof(d));
-  for (int i = 0; i < 4; ++i) d.val[i] = make_float2(gt.val[i].real(), gt.val[i].imag());
+  if (gt.nv <= 2) {
+    for (int i = 0; i < 4; ++i) d.val[i] = make_float2(gt.val[i].real(), gt.val[i].imag());
+    d.tab = -1;
+  } else {
+    d.tab = (long long)vals->size();
+    for (int i = 0; i < (1 << gt.nv); ++i) vals->push_back(make_float2(gt.val[i].real(), gt.val[i].imag()));
+  }
   d.nv = gt.nv;
   d.n_free = pt ? pt->rank() : 0;
   std::vector<int> mu_index(P.net.free_vars.size(), -1);
@@ -1870,12 +1892,23 @@ static tnq_status build_config(const tnq_plan& P, int mode, int B, ExecConfig** 
   tnq_status gst = group_grid_size(&ggrid);
   if (gst != TNQ_OK) return gst;
   ExecConfig* C = new ExecConfig();
+  auto fail = [&](tnq_status st) {
+    cudaFree(C->d_leaves);
+    cudaFree(C->d_scalars);
+    cudaFree(C->d_inout);
+    cudaFree(C->d_finals);
+    cudaFree(C->d_hoist);
+    cudaFree(C->d_vals);
+    delete C;
+    return st;
+  };
   C->group_grid = ggrid;
   C->L = make_layout(P, mode, B);
   const Program& prog = P.prog;
   std::vector<LeafDev> leaves, scalars;
-  for (int t : prog.leaves) leaves.push_back(make_leafdev(P, &prog.tensors[t], prog.tensors[t].leaf_gate, &C->L, t));
-  for (int g : prog.scalar_leaves) scalars.push_back(make_leafdev(P, nullptr, g, nullptr, -1));
+  for (int t : prog.leaves)
+    leaves.push_back(make_leafdev(P, &prog.tensors[t], prog.tensors[t].leaf_gate, &C->L, t, &C->vals));
+  for (int g : prog.scalar_leaves) scalars.push_back(make_leafdev(P, nullptr, g, nullptr, -1, &C->vals));
   std::vector<FinalDev> finals;
   for (int t : prog.finals) finals.push_back(FinalDev{C->L.off[t], t, (int)C->L.dep[t]});
   C->n_leaves = (int)leaves.size();
@@ -1892,44 +1925,20 @@ static tnq_status build_config(const tnq_plan& P, int mode, int B, ExecConfig** 
       (e = up((void**)&C->d_scalars, scalars.data(), scalars.size() * sizeof(LeafDev))) != cudaSuccess ||
       (e = up((void**)&C->d_inout, P.net.inout_qubits.data(), P.net.inout_qubits.size() * sizeof(int))) !=
           cudaSuccess ||
-      (e = up((void**)&C->d_finals, finals.data(), finals.size() * sizeof(FinalDev))) != cudaSuccess) {
+      (e = up((void**)&C->d_finals, finals.data(), finals.size() * sizeof(FinalDev))) != cudaSuccess ||
+      (e = up((void**)&C->d_vals, C->vals.data(), C->vals.size() * sizeof(float2))) != cudaSuccess) {
     set_error(std::string("uploading plan tables: ") + cudaGetErrorString(e));
-    cudaFree(C->d_leaves);
-    cudaFree(C->d_scalars);
-    cudaFree(C->d_inout);
-    cudaFree(C->d_finals);
-    delete C;
-    return TNQ_ECUDA;
+    return fail(TNQ_ECUDA);
   }
-  if (!build_steps(P, C->L, *C)) {
-    cudaFree(C->d_leaves);
-    cudaFree(C->d_scalars);
-    cudaFree(C->d_inout);
-    cudaFree(C->d_finals);
-    delete C;
-    return TNQ_EUNSUPPORTED;
-  }
+  if (!build_steps(P, C->L, *C)) return fail(TNQ_EUNSUPPORTED);
   for (size_t i = 0; i < C->gsmem.size(); ++i) {  // chains with a register tail: more blocks may fit
     int g = 0;
-    if ((gst = group_grid_size(&g, C->gsmem[i], C->gp[i].tail > 0)) != TNQ_OK) {
-      cudaFree(C->d_leaves);
-      cudaFree(C->d_scalars);
-      cudaFree(C->d_inout);
-      cudaFree(C->d_finals);
-      delete C;
-      return gst;
-    }
+    if ((gst = group_grid_size(&g, C->gsmem[i], C->gp[i].tail > 0)) != TNQ_OK) return fail(gst);
     C->ggrid.push_back(g);
   }
   if ((e = up((void**)&C->d_hoist, C->hoist_dev.data(), C->hoist_dev.size() * sizeof(HoistDev))) != cudaSuccess) {
     set_error(std::string("uploading plan tables: ") + cudaGetErrorString(e));
-    cudaFree(C->d_leaves);
-    cudaFree(C->d_scalars);
-    cudaFree(C->d_inout);
-    cudaFree(C->d_finals);
-    cudaFree(C->d_hoist);
-    delete C;
-    return TNQ_ECUDA;
+    return fail(TNQ_ECUDA);
   }
   *out = C;
   return TNQ_OK;
@@ -2027,9 +2036,10 @@ static void enqueue_batch(const tnq_plan& P, ExecConfig& C, char* ws, cudaStream
   cudaMemsetAsync(mm, 0, (size_t)T * B * 4, s);
   if (C.n_leaves) {
     long long n = (long long)C.n_leaves * B;
-    k_leaf_init<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(C.d_leaves, C.n_leaves, hdr, bits, arena, B);
+    k_leaf_init<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(C.d_leaves, C.n_leaves, hdr, bits, C.d_vals, arena, B);
   }
-  k_scalar_init<<<(B + 127) / 128, 128, 0, s>>>(C.d_scalars, C.n_scalars, C.d_inout, C.n_inout, hdr, bits, scal, B);
+  k_scalar_init<<<(B + 127) / 128, 128, 0, s>>>(C.d_scalars, C.n_scalars, C.d_inout, C.n_inout, hdr, bits, C.d_vals,
+                                                scal, B);
   int* status = reinterpret_cast<int*>(ws + L.status_off);
   // early buckets first, one launch per level; their steps launch nothing below
   for (size_t l = 0; l + 1 < C.hoist_first.size(); ++l)
@@ -2054,9 +2064,11 @@ static void enqueue_batch(const tnq_plan& P, ExecConfig& C, char* ws, cudaStream
       cudaStreamWaitEvent(s, side->join[k], 0);
     }
   }
-  const double sc = P.amp_scale_log2;  // = -n_sqrt2 / 2
-  const int n_sqrt2 = (int)std::lround(-2.0 * sc);
-  const int scale_exp = -(n_sqrt2 / 2), scale_half = n_sqrt2 & 1;
+  // amplitude scale 2^(-n_sqrt2 / 2 + leaf_exp): sqrt2 factors of the gates,
+  // power-of-two factors taken out of a general network's tensors
+  const int n_sqrt2 = P.net.n_sqrt2;
+  const long long le = std::max<long long>(-100000, std::min<long long>(100000, P.net.leaf_exp));
+  const int scale_exp = -(n_sqrt2 / 2) + (int)le, scale_half = n_sqrt2 & 1;
   k_finalize<<<(B + 127) / 128, 128, 0, s>>>(C.d_finals, C.n_finals, scal, arena, me, B, hdr, scale_exp, scale_half,
                                               res);
   k_slice_sum<<<(L.n_rows + 127) / 128, 128, 0, s>>>(res, B, hdr, part, L.n_rows);
@@ -2241,6 +2253,41 @@ int tnq_internal_group_tails(const tnq_plan* plan, int mode, uint32_t batch, int
   return 0;
 }
 
+// Internal hook (not in include/tnq.h; host only): a text description of every
+// fused-chain step of configuration (mode, batch): per stage its local bits,
+// and per operand its source and the local bits it holds (nonzero strides),
+// plus the tile bits each external input holds. For planning the tile shape.
+int tnq_internal_group_text(const tnq_plan* plan, int mode, uint32_t batch, char* buf, size_t cap) {
+  if (!plan || !buf || cap == 0) return 1;
+  ExecConfig C;
+  C.L = make_layout(*plan, mode, (int)batch);
+  if (!build_steps(*plan, C.L, C)) return 1;
+  std::string out;
+  for (size_t gi = 0; gi < C.gp.size(); ++gi) {
+    const GParams& G = C.gp[gi];
+    out += "group " + std::to_string(gi) + " stages " + std::to_string(G.n_st) + " tail " + std::to_string(G.tail) +
+           " n_h " + std::to_string(G.n_h) + " gin " + std::to_string(G.n_gin) + "\n";
+    for (int j = 0; j < G.n_gin; ++j) {
+      int nh = 0;
+      for (int i = 0; i < G.n_h; ++i) nh += G.gin[j].hstride[i] != 0;
+      out += "  gin " + std::to_string(j) + " tile bits held " + std::to_string(nh) + " dep " +
+             std::to_string(G.gin[j].dep) + "\n";
+    }
+    for (int st = 0; st < G.n_st; ++st) {
+      const GSt& S = G.st[st];
+      out += "  stage " + std::to_string(st) + " nbits " + std::to_string(S.nbits) + " n_in " + std::to_string(S.n_in) +
+             " n_var " + std::to_string(S.n_var) + " pd " + std::to_string(S.pd) + "\n";
+      for (int j = 0; j < S.n_in; ++j) {
+        out += "    in src " + std::to_string(S.src[j]) + " ustride " + std::to_string(S.ustride[j]) + " local:";
+        for (int b = 0; b < S.nbits; ++b) out += S.cstride[j][b] ? " " + std::to_string(S.cstride[j][b]) : " .";
+        out += "\n";
+      }
+    }
+  }
+  std::snprintf(buf, cap, "%s", out.c_str());
+  return out.size() + 1 > cap ? 2 : 0;
+}
+
 // Internal hook (not in include/tnq.h; host only): the concurrency structure of
 // configuration (mode, batch) for checking it on the host. Per step: its side
 // stream, the tensor it writes, up to 16 tensors it reads (-1 past the end) and
@@ -2308,7 +2355,7 @@ namespace tnq {
 static tnq_status profile_steps(const tnq_plan* plan, const uint8_t* bits, uint64_t s0, uint64_t s1, void* workspace,
                                 size_t ws_bytes, uint32_t max_batch, void* stream, std::vector<float>& ms,
                                 ExecConfig** cfg) {
-  if (!plan || !bits || !workspace || s1 <= s0 || s1 > (1ull << plan->mu.size())) {
+  if (!plan || (!bits && plan->net.n_qubits > 0) || !workspace || s1 <= s0 || s1 > (1ull << plan->mu.size())) {
     set_error("bad profile arguments");
     return TNQ_EINVAL;
   }
@@ -2348,7 +2395,7 @@ static tnq_status profile_steps(const tnq_plan* plan, const uint8_t* bits, uint6
   CU(cudaMemsetAsync(ws + L.status_off, 0, 4, s));
   if (C->n_leaves) {
     long long n = (long long)C->n_leaves * B;
-    k_leaf_init<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(C->d_leaves, C->n_leaves, hdr, bw, arena, B);
+    k_leaf_init<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(C->d_leaves, C->n_leaves, hdr, bw, C->d_vals, arena, B);
   }
   std::vector<cudaEvent_t> ev(2 * (size_t)nbk);
   for (auto& e : ev) CU(cudaEventCreate(&e));
@@ -2491,7 +2538,7 @@ static tnq_status profile_steps_min(const tnq_plan* plan, const uint8_t* bits, u
 
 tnq_status tnq_plan_autotune(tnq_plan* plan, const uint8_t* bits, void* workspace, size_t ws_bytes,
                              uint32_t max_batch, void* stream, int32_t* out_n_fused) {
-  if (!plan || !bits || !workspace) { set_error("NULL argument"); return TNQ_EINVAL; }
+  if (!plan || (!bits && plan->net.n_qubits > 0) || !workspace) { set_error("NULL argument"); return TNQ_EINVAL; }
   for (int q = 0; q < plan->net.n_qubits; ++q)
     if (bits[q] > 1) { set_error("bitstring bytes must be 0 or 1"); return TNQ_EINVAL; }
   Program& prog = plan->prog;
@@ -2632,7 +2679,7 @@ size_t tnq_plan_workspace_bytes(const tnq_plan* plan, uint32_t batch) {
 tnq_status tnq_contract_sliced(const tnq_plan* plan, const uint8_t* bits, uint64_t slice_begin, uint64_t slice_end,
                                void* workspace, size_t ws_bytes, uint32_t max_batch, void* stream, double* out_amp,
                                double* out_slice_amps) {
-  if (!plan || !bits || !out_amp) { set_error("NULL argument"); return TNQ_EINVAL; }
+  if (!plan || (!bits && plan->net.n_qubits > 0) || !out_amp) { set_error("NULL argument"); return TNQ_EINVAL; }
   const uint64_t n_slices = 1ull << plan->mu.size();
   if (slice_begin > slice_end || slice_end > n_slices) { set_error("slice range outside [0, n_slices)"); return TNQ_EINVAL; }
   for (int q = 0; q < plan->net.n_qubits; ++q)
@@ -2804,10 +2851,13 @@ static size_t noalloc_table_bytes(const tnq_plan& P, int B) {
   ExecConfig C;
   C.L = make_layout(P, 0, B);
   const size_t hoist = build_steps(P, C.L, C) ? C.hoist_dev.size() : 0;
+  size_t vals = 0;
+  for (const GateTensor& g : P.net.tensors)
+    if (g.nv > 2) vals += (size_t)1 << g.nv;
   return align_up(P.prog.leaves.size() * sizeof(LeafDev), 256) +
          align_up(P.prog.scalar_leaves.size() * sizeof(LeafDev), 256) +
          align_up(P.net.inout_qubits.size() * sizeof(int), 256) + align_up(P.prog.finals.size() * sizeof(FinalDev), 256) +
-         align_up(hoist * sizeof(HoistDev), 256);
+         align_up(hoist * sizeof(HoistDev), 256) + align_up(vals * sizeof(float2), 256);
 }
 
 // Host-side configuration of the allocation-free path for batch B, built once
@@ -2859,8 +2909,9 @@ static tnq_status get_noalloc_config(const tnq_plan& P, uint64_t cap, char* scra
   ExecConfig& C = NC->C;
   C.group_grid = ggrid;
   C.L = make_layout(P, 0, B);
-  for (int t : prog.leaves) NC->leaves.push_back(make_leafdev(P, &prog.tensors[t], prog.tensors[t].leaf_gate, &C.L, t));
-  for (int g : prog.scalar_leaves) NC->scalars.push_back(make_leafdev(P, nullptr, g, nullptr, -1));
+  for (int t : prog.leaves)
+    NC->leaves.push_back(make_leafdev(P, &prog.tensors[t], prog.tensors[t].leaf_gate, &C.L, t, &C.vals));
+  for (int g : prog.scalar_leaves) NC->scalars.push_back(make_leafdev(P, nullptr, g, nullptr, -1, &C.vals));
   for (int t : prog.finals) NC->finals.push_back(FinalDev{C.L.off[t], t, (int)C.L.dep[t]});
   if (!build_steps(P, C.L, C)) return TNQ_EUNSUPPORTED;
   for (size_t i = 0; i < C.gsmem.size(); ++i) {  // per-chain persistent grids, as build_config sizes them
@@ -2879,6 +2930,7 @@ static tnq_status get_noalloc_config(const tnq_plan& P, uint64_t cap, char* scra
   C.d_inout = reinterpret_cast<int*>(take(P.net.inout_qubits.size() * sizeof(int)));
   C.d_finals = reinterpret_cast<FinalDev*>(take(NC->finals.size() * sizeof(FinalDev)));
   C.d_hoist = reinterpret_cast<HoistDev*>(take(C.hoist_dev.size() * sizeof(HoistDev)));
+  C.d_vals = reinterpret_cast<float2*>(take(C.vals.size() * sizeof(float2)));
   NC->tables = o;
   C.n_leaves = (int)NC->leaves.size();
   C.n_scalars = (int)NC->scalars.size();
@@ -2895,7 +2947,7 @@ extern "C" {
 
 tnq_status tnq_contract_sliced_noalloc(const tnq_plan* plan, const uint8_t* bits, uint64_t slice_begin,
                                        uint64_t slice_end, void* stream, double* out_amp, double* out_slice_amps) {
-  if (!plan || !bits || !out_amp) { set_error("NULL argument"); return TNQ_EINVAL; }
+  if (!plan || (!bits && plan->net.n_qubits > 0) || !out_amp) { set_error("NULL argument"); return TNQ_EINVAL; }
   const uint64_t n_slices = 1ull << plan->mu.size();
   if (slice_begin > slice_end || slice_end > n_slices) { set_error("slice range outside [0, n_slices)"); return TNQ_EINVAL; }
   for (int q = 0; q < plan->net.n_qubits; ++q)
@@ -2924,6 +2976,7 @@ tnq_status tnq_contract_sliced_noalloc(const tnq_plan* plan, const uint8_t* bits
   CU(put(C.d_inout, plan->net.inout_qubits.data(), (size_t)C.n_inout * sizeof(int)));
   CU(put(C.d_finals, NC->finals.data(), NC->finals.size() * sizeof(FinalDev)));
   CU(put(C.d_hoist, C.hoist_dev.data(), C.hoist_dev.size() * sizeof(HoistDev)));
+  CU(put(C.d_vals, C.vals.data(), C.vals.size() * sizeof(float2)));
   std::vector<unsigned> words((size_t)C.L.n_words * C.L.n_rows, 0u);
   pack_bits(bits, plan->net.n_qubits, words);
   CU(cudaMemcpyAsync(ws + C.L.bits_off, words.data(), words.size() * 4, cudaMemcpyHostToDevice, s));

@@ -64,6 +64,8 @@ SIGNATURES = {
     "tnq_version": (ctypes.c_char_p, []),
     "tnq_plan_opts_default": (None, [_P(PlanOpts)]),
     "tnq_plan_from_circuit": (ctypes.c_int, [ctypes.c_int32, _P(Gate), ctypes.c_size_t, _P(PlanOpts), _P(_vp)]),
+    "tnq_plan_from_network": (ctypes.c_int, [ctypes.c_int32, _i32p, ctypes.c_size_t, _P(ctypes.c_int64), _i32p,
+                                             _f64p, _P(PlanOpts), _P(_vp)]),
     "tnq_plan_destroy": (None, [_vp]),
     "tnq_plan_info_get": (ctypes.c_int, [_vp, _P(PlanInfo)]),
     "tnq_plan_order": (ctypes.c_int, [_vp, _i32p, _i32p]),
@@ -158,6 +160,32 @@ class Plan:
         _check(lib().tnq_plan_from_circuit(circ.n_qubits, arr, len(circ.gates), ctypes.byref(o), ctypes.byref(h)))
         self.handle = h
 
+    @classmethod
+    def from_network(cls, dims, tensors, **opts):
+        """tnq_plan_from_network: a closed network with L-valued indices.
+        tensors: list of (index tuple, complex array of shape (dims[i] for i in
+        the tuple)); the arrays are passed in C order."""
+        self = cls.__new__(cls)
+        self.n_qubits = 0
+        o = default_opts(**opts)
+        d = np.ascontiguousarray(np.array(list(dims) or [1], dtype=np.int32))
+        offs = [0]
+        idx = []
+        data = []
+        for ind, arr in tensors:
+            idx.extend(int(i) for i in ind)
+            offs.append(len(idx))
+            data.append(np.ascontiguousarray(np.asarray(arr, dtype=np.complex128)).reshape(-1))
+        off = np.array(offs, dtype=np.int64)
+        ia = np.ascontiguousarray(np.array(idx or [0], dtype=np.int32))
+        da = np.ascontiguousarray(np.concatenate(data) if data else np.zeros(1, np.complex128)).view(np.float64)
+        h = _vp()
+        _check(lib().tnq_plan_from_network(len(dims), _ptr(d, ctypes.c_int32), len(tensors), _ptr(off, ctypes.c_int64),
+                                           _ptr(ia, ctypes.c_int32), _ptr(da, ctypes.c_double), ctypes.byref(o),
+                                           ctypes.byref(h)))
+        self.handle = h
+        return self
+
     def __del__(self):
         h = getattr(self, "handle", None)
         if h and _lib is not None:
@@ -222,6 +250,8 @@ class Plan:
 
 
 def _bits_array(bits, n):
+    if bits is None and n == 0:  # a general network has no qubits
+        return np.zeros(1, np.uint8)
     b = np.ascontiguousarray(np.asarray(bits, dtype=np.uint8))
     if b.size != n:
         raise ValueError(f"bitstring has {b.size} entries, plan has {n} qubits")
@@ -251,7 +281,7 @@ def default_workspace(plans, want_items: int, fraction: float = 0.5):
     return torch.empty(need, dtype=torch.uint8, device="cuda")
 
 
-def contract_sliced(plan: Plan, bits, slice_begin: int = 0, slice_end: int | None = None, workspace=None,
+def contract_sliced(plan: Plan, bits=None, slice_begin: int = 0, slice_end: int | None = None, workspace=None,
                     max_batch: int = 0, stream=None, per_slice: bool = False):
     """tnq_contract_sliced: FP64 partial sum over slices [begin, end) (Eq. 5).
 
@@ -279,7 +309,7 @@ def contract_sliced(plan: Plan, bits, slice_begin: int = 0, slice_end: int | Non
     return amp
 
 
-def contract_sliced_noalloc(plan: Plan, bits, slice_begin: int = 0, slice_end: int | None = None, stream=None,
+def contract_sliced_noalloc(plan: Plan, bits=None, slice_begin: int = 0, slice_end: int | None = None, stream=None,
                             per_slice: bool = False):
     """tnq_contract_sliced_noalloc: as contract_sliced, with the library's static
     device scratch instead of a workspace (no device allocation anywhere)."""
