@@ -782,17 +782,8 @@ __device__ __forceinline__ void group_tail(const GParams& P, int t, const float2
     }
 #pragma unroll
     for (int s = 0; s < M; ++s) {
-#pragma unroll
-      for (int k = 0; k < (1 << (M - 1 - s)); ++k) {
-        float2 a0 = x[2 * k], a1 = x[2 * k + 1];
-        if (two[s]) {
-          const int c = (cm << (M - 1 - s)) + k;
-          const int* tr = s_tab[row[s]];
-          const int off = tr[c & 15] + tr[GT_MID + ((c >> 4) & ((1 << (GTB - 4)) - 1))] + tr[GT_HI + (c >> GTB)];
-          const float4 w = __ldg(reinterpret_cast<const float4*>(op[s] + off));
-          a0 = cmul(a0, make_float2(w.x, w.y));
-          a1 = cmul(a1, make_float2(w.z, w.w));
-        }
+      const int NK = 1 << (M - 1 - s);  // this stage's entries in the subtree (a constant once unrolled)
+      auto combine = [&](int k, float2 a0, float2 a1) {
         float rx = K0[s].x * a0.x;  // K0 a0 + K1 a1
         rx = fmaf(-K0[s].y, a0.y, rx);
         rx = fmaf(K1[s].x, a1.x, rx);
@@ -802,6 +793,24 @@ __device__ __forceinline__ void group_tail(const GParams& P, int t, const float2
         ry = fmaf(K1[s].x, a1.y, ry);
         ry = fmaf(K1[s].y, a1.x, ry);
         x[k] = make_float2(rx, ry);
+      };
+      if (two[s]) {
+        // the operand's offsets are additive over the bits of the local index:
+        // entry c0 + k (k below 2^(M-1-s), the low bits of c0 zero) is at
+        // offset(c0) + offset(k), offset(k) from the bits 0-3 table
+        const int c0 = cm << (M - 1 - s);
+        const int* tr = s_tab[row[s]];
+        const float2* q =
+            op[s] + tr[c0 & 15] + tr[GT_MID + ((c0 >> 4) & ((1 << (GTB - 4)) - 1))] + tr[GT_HI + (c0 >> GTB)];
+        float4 w[1 << (M - 1)];
+#pragma unroll
+        for (int k = 0; k < NK; ++k) w[k] = __ldg(reinterpret_cast<const float4*>(q + tr[k]));
+#pragma unroll
+        for (int k = 0; k < NK; ++k)
+          combine(k, cmul(x[2 * k], make_float2(w[k].x, w[k].y)), cmul(x[2 * k + 1], make_float2(w[k].z, w[k].w)));
+      } else {
+#pragma unroll
+        for (int k = 0; k < NK; ++k) combine(k, x[2 * k], x[2 * k + 1]);
       }
     }
     dst[s_out_hi[i]] = x[0];
@@ -860,6 +869,7 @@ __global__ void __launch_bounds__(GTPB, TK ? 5 : 4) k_group(const __grid_constan
     if ((t >> i) & 1) out_lo += P.out_cstride[i];
   const int buf_elems = 1 << (GL_MAX - 1);
   long long cur_item = -1;
+  long long meta_item = -1;  // item whose exponents and scales s_e / s_F hold
   float tmax = 0.f;
   for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
     const long long item = tile >> P.n_h;
@@ -881,37 +891,46 @@ __global__ void __launch_bounds__(GTPB, TK ? 5 : 4) k_group(const __grid_constan
       cur_item = item;
     }
     __syncthreads();  // previous tile done with s_ptr / stage buffers
-    if (t < P.n_gin) {
-      const GIn& g = P.gin[t];
-      long long b = g.dep ? item * g.istride : 0ll;
-      for (int i = 0; i < P.n_h; ++i)
-        if ((h >> i) & 1ll) b += s_hstr[t][i];
-      s_ptr[t] = g.ptr + b;
-      if (g.meta < 0) {
-        s_e[t] = 0;
-      } else {
-        const long long row = (long long)g.meta * P.B + (g.dep ? item : 0ll);
-        int m;
-        scale_of_max(P.meta_m[row], &m);
-        s_e[t] = P.meta_e[row] + m;
+    // tile pointers: warp w takes inputs w, w + 4, ... (and the output, as
+    // input n_gin); lane i adds the stride of tile bit i when it is set
+    for (int j = t >> 5; j <= P.n_gin; j += GTPB / 32) {
+      const int lane = t & 31;
+      const int r = j < P.n_gin ? j : GIN_MAX;
+      const int v = __reduce_add_sync(0xffffffffu, (lane < P.n_h && ((h >> lane) & 1ll)) ? s_hstr[r][lane] : 0);
+      if (lane == 0) {
+        if (j < P.n_gin) {
+          const GIn& g = P.gin[j];
+          s_ptr[j] = g.ptr + (g.dep ? item * g.istride : 0ll) + v;
+        } else {
+          s_out_base = (P.out_dep ? item * P.out_istride : 0ll) + v;
+        }
       }
-    } else if (t < P.n_gin + P.n_st) {
-      const GSt& S = P.st[t - P.n_gin];
-      float f = 1.f;
-      for (int j = 0; j < S.n_in; ++j) {
-        if (S.src[j] < 0) continue;
-        const GIn& g = P.gin[S.src[j]];
-        if (g.meta < 0) continue;
-        int m;
-        f *= scale_of_max(P.meta_m[(long long)g.meta * P.B + (g.dep ? item : 0ll)], &m);
-      }
-      s_F[t - P.n_gin] = f;
     }
-    if (t == GTPB - 1) {
-      long long b = P.out_dep ? item * P.out_istride : 0ll;
-      for (int i = 0; i < P.n_h; ++i)
-        if ((h >> i) & 1ll) b += s_hstr[GIN_MAX][i];
-      s_out_base = b;
+    // exponents and power-of-two scales depend on the item only
+    if (item != meta_item) {
+      if (t < P.n_gin) {
+        const GIn& g = P.gin[t];
+        if (g.meta < 0) {
+          s_e[t] = 0;
+        } else {
+          const long long row = (long long)g.meta * P.B + (g.dep ? item : 0ll);
+          int m;
+          scale_of_max(P.meta_m[row], &m);
+          s_e[t] = P.meta_e[row] + m;
+        }
+      } else if (t < P.n_gin + P.n_st) {
+        const GSt& S = P.st[t - P.n_gin];
+        float f = 1.f;
+        for (int j = 0; j < S.n_in; ++j) {
+          if (S.src[j] < 0) continue;
+          const GIn& g = P.gin[S.src[j]];
+          if (g.meta < 0) continue;
+          int m;
+          f *= scale_of_max(P.meta_m[(long long)g.meta * P.B + (g.dep ? item : 0ll)], &m);
+        }
+        s_F[t - P.n_gin] = f;
+      }
+      meta_item = item;
     }
     __syncthreads();
     // stage s writes region A (even s) or B (odd s); every stage output has at
