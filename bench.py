@@ -314,6 +314,155 @@ def run_reference(args, cfg_name):
     print(json.dumps(line), flush=True)
 
 
+def run_batched(args):
+    """Batched serving workload: 64 seeded circuits on 5x5..7x7 grids at depths
+    1+16+1..1+32+1 (uneven sizes), 16 seeded bitstrings each; plans sliced to
+    bags <= 2^26 (order recomputed while slicing, split-precision GEMM chains,
+    each plan autotuned before timing). One step = one tnq_amplitudes_batch call
+    over all 1024 amplitudes (host bitstrings in, FP64 amplitudes out: every
+    plan's batches are enqueued on up to four streams with one synchronisation)."""
+    import numpy as np
+    import torch
+
+    from oracle import oracle
+    from paper_2004_10892_gb300 import build as native_build
+    from paper_2004_10892_gb300 import inputs, tnq
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        work = inputs.batched_serving_workload(n_circuits=64, bitstrings_per_circuit=16, seed=0)
+        oracle.build()
+        sample = [(c, b[0]) for c, b in work if c.n_qubits == 25][:args.steps + args.warmup]
+        t0 = None
+        for k, (c, b) in enumerate(sample):
+            if k == args.warmup:
+                t0 = time.perf_counter()
+            oracle.contract(c, b)
+        dt = time.perf_counter() - t0
+        n = len(sample) - args.warmup
+        v = n / dt
+        line = {"impl": "reference", "metric": "amplitudes/s, batched serving workload", "value": v,
+                "unit": "amplitudes/s", "n_gpus": args.gpus, "steps": n, "warmup": args.warmup,
+                "ms_per_step": 1e3 * dt / n, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "c128", "data": "synthetic",
+                "config": {"workload": "batched: the 5x5 circuits of the 64-circuit workload, one amplitude per step"},
+                "cpu_baseline": {"value": v, "unit": "amplitudes/s", "cores": oracle.num_threads(), "kind": "oracle",
+                                 "sample": "5x5 amplitudes of the batched workload (the smallest circuits)"},
+                "e2e": {"value": v, "unit": "amplitudes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+    torch.cuda.set_device(local)
+    native_build.build()
+    work = inputs.batched_serving_workload(n_circuits=64, bitstrings_per_circuit=16, seed=1000 * rank)
+    prec = {"c64": 0, "bf16x3": 1, "tf32x3": 2}[args.precision]
+    t_plan = time.perf_counter()
+    plans = [tnq.Plan(c, max_bag_log2=26, max_p=30, precision=prec, gemm_min_k_log2=args.gemm_min_k,
+                      reorder_every=args.reorder_every, fuse_min_rank=args.fuse_min_rank) for c, _ in work]
+    t_plan = time.perf_counter() - t_plan
+    stream = torch.cuda.current_stream()
+    free, _ = torch.cuda.mem_get_info()
+    ws = torch.empty(int(free * 0.6) // 256 * 256, dtype=torch.uint8, device="cuda")
+    t_tune = time.perf_counter()
+    tuned = {}
+    if args.tune_file and os.path.exists(args.tune_file):
+        tuned = json.load(open(args.tune_file))
+    if not args.no_autotune:
+        for i, ((c, bl), plan) in enumerate(zip(work, plans)):
+            key = str(i)
+            if key in tuned:
+                plan.set_tuning(*tuned[key]["tuning"])
+                plan.keep_chains(tuned[key]["kept_chains"])
+            else:
+                n_sl = plan.info()["n_slices"]
+                plan.autotune(bl[0], workspace=ws, max_batch=min(16, n_sl), stream=stream)
+                tuned[key] = {"tuning": list(plan.tuning()), "kept_chains": plan.fused_chains()}
+        if args.tune_file and rank == 0:
+            json.dump(tuned, open(args.tune_file, "w"))
+    t_tune = time.perf_counter() - t_tune
+    bitlists = [bl for _, bl in work]
+    n_amp = sum(len(b) for b in bitlists)
+    n_items = sum(len(b) << p.info()["p"] for p, b in zip(plans, bitlists))
+    for _ in range(args.warmup):
+        amps = tnq.amplitudes_batch(plans, bitlists, workspace=ws, stream=stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        clk.t0 = t0
+        e0.record(stream)
+        for _ in range(args.steps):
+            amps = tnq.amplitudes_batch(plans, bitlists, workspace=ws, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clk.t1 = time.perf_counter()
+    t_dev = e0.elapsed_time(e1) / 1e3
+    t_wall = clk.t1 - t0
+    # kernel launches per step: each plan's batches (the largest power-of-two batch whose workspace fits one
+    # of the call's four lanes, as tnq_amplitudes_batch picks it) x its launches per batch, + one accumulate each
+    region = ws.numel() * 7 // 8 // 4
+    launches = 0
+    for p, b in zip(plans, bitlists):
+        items = len(b) << p.info()["p"]
+        B = 1
+        while B < items and B < (1 << 16) and p.workspace_bytes(2 * B) <= region:
+            B *= 2
+        launches += -(-items // B) * (tnq.lib().tnq_internal_launches_per_batch(p.handle) + 1)
+    launches *= args.steps
+    # the plan with the most work: per-launch roofline of one of its batches
+    big = max(range(len(plans)), key=lambda i: plans[i].info()["total_flops"])
+    roof = None
+    if not args.no_profile:
+        nb = plans[big].info()["n_slices"]
+        roof = launch_roofline(tnq.lib(), plans[big], bitlists[big][0], ws, min(nb, 16), nb, stream, load_peaks(),
+                               plans[big].info())
+        if roof:
+            roof["note"] = f"one batch of the batch's largest plan (circuit {big}, {work[big][0].name})"
+    # oracle check of a sample: every 5x5 amplitude of the first 8 circuits of that size
+    errs, t_cpu, n_cpu = [], 0.0, 0
+    if not args.no_cpu_baseline:
+        for i, (c, bl) in enumerate(work):
+            if c.n_qubits != 25 or n_cpu >= 8:
+                continue
+            tt = time.perf_counter()
+            ref = oracle.contract(c, bl[0])
+            t_cpu += time.perf_counter() - tt
+            n_cpu += 1
+            errs.append(rel_err(amps[16 * i], ref, c.n_qubits))
+    line = {
+        "metric": "slice-contractions/s & amplitudes/s, batched serving workload (64 circuits x 16 bitstrings)",
+        "value": args.steps * n_items / t_dev, "unit": "slices/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": {"c64": "c64", "bf16x3": "c64+3xbf16", "tf32x3": "c64+3xtf32"}[args.precision], "data": "synthetic",
+        "config": {"workload": "batched: 64 seeded circuits, grids 5x5..7x7, depths 1+16+1..1+32+1, 16 bitstrings "
+                               "each, bags <= 2^26, one tnq_amplitudes_batch call per step",
+                   "amplitudes_per_step": n_amp, "items_per_step": n_items, "plan_s": t_plan, "autotune_s": t_tune,
+                   "precision": args.precision, "reorder_every": args.reorder_every,
+                   "l2": "inputs larger than L2 (the large plans stream GBs per batch)"},
+        "amplitudes_per_s": args.steps * n_amp / t_dev,
+        "time_per_amplitude_s": t_dev / (args.steps * n_amp),
+        "rel_err_vs_fp64": max(errs) if errs else None,
+        "rel_err_vs_fp64_detail": {"sample": f"first bitstring of {len(errs)} 5x5 circuits", "max": max(errs)
+                                   if errs else None},
+        "e2e": {"value": args.steps * n_items / t_wall, "unit": "slices/s",
+                "h2d_bytes_per_step": sum(len(b) * p.n_qubits for p, b in zip(plans, bitlists)),
+                "d2h_bytes_per_step": 16 * n_amp},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "cpu_baseline": {"value": n_cpu / t_cpu, "unit": "amplitudes/s (5x5 circuits only)",
+                         "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": f"{n_cpu} 5x5 amplitudes of the workload"} if n_cpu else None,
+        "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -321,7 +470,9 @@ def main():
                     help="timed steps (default 60, about 1 s of GPU time; 5 oracle slices for --impl reference)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="tnq", choices=["tnq", "reference"])
-    ap.add_argument("--config", default="7x7_d1+32+1", choices=sorted(CONFIGS))
+    ap.add_argument("--config", default="7x7_d1+32+1", choices=sorted(CONFIGS) + ["batched"],
+                    help="workload; 'batched' = 64 circuits (5x5..7x7 grids, depths 1+16+1..1+32+1) x 16 "
+                         "bitstrings per step in one tnq_amplitudes_batch call")
     ap.add_argument("--max-batch", type=int, default=256, help="slices contracted at once")
     ap.add_argument("--no-cpu-baseline", action="store_true",
                     help="skip the FP64 oracle (CPU baseline and the amplitude's error)")
@@ -354,6 +505,11 @@ def main():
     if args.steps is None:
         args.steps = 5 if args.impl == "reference" else 60
 
+    if args.config == "batched":
+        if args.steps is None or args.steps == 60:
+            args.steps = 3
+        run_batched(args)
+        return
     if args.impl == "reference":
         run_reference(args, args.config)
         return
@@ -393,7 +549,10 @@ def main():
     n_fused = None
     if args.tune_file and os.path.exists(args.tune_file) and not args.no_autotune:
         with open(args.tune_file) as f:
-            plan.keep_chains(json.load(f)["kept_chains"])
+            tf = json.load(f)
+        if "tuning" in tf:
+            plan.set_tuning(*tf["tuning"])
+        plan.keep_chains(tf["kept_chains"])
         n_fused = len(plan.fused_chains())
     elif not args.no_autotune:
         tune_ws = torch.empty(args.tune_gb << 30, dtype=torch.uint8, device="cuda")
@@ -401,7 +560,7 @@ def main():
         del tune_ws
         if args.tune_file and rank == 0:
             with open(args.tune_file, "w") as f:
-                json.dump({"kept_chains": plan.fused_chains()}, f)
+                json.dump({"tuning": list(plan.tuning()), "kept_chains": plan.fused_chains()}, f)
     t_tune = time.perf_counter() - t_tune
     info = plan.info()
     my_b, my_e = 0, n_sl
@@ -494,7 +653,8 @@ def main():
                        "autotune_s": t_tune, "fused_chains": info["n_fused_groups"],
                        "gemm_buckets": info["n_gemm_buckets"], "precision": args.precision,
                        "form": "plain per-slice" if args.plain else "batched, fused, autotuned",
-                       "reorder_every": args.reorder_every, "order_trials": args.order_trials},
+                       "reorder_every": args.reorder_every, "order_trials": args.order_trials,
+                       "tuning": {"gemm_min_k_log2": plan.tuning()[0], "tile_low": plan.tuning()[1]}},
             "time_per_amplitude_s": t_dev / args.steps,
             "rel_err_vs_fp64": chk["amp_err"] if chk else None,
             "rel_err_vs_fp64_detail": {

@@ -238,8 +238,10 @@ tnq_status tnq_contract_sliced(const tnq_plan* plan, const uint8_t* bits,
 /* tnq_plan_autotune: measures on the current device, for batches of up to
  * max_batch slices, every fused chain of buckets (see fuse_min_rank) against
  * the same buckets run one launch each, and keeps the faster form of each
- * chain. Contraction results do not change (fusion only regroups the same
- * products). It modifies the plan: call it once, before the plan is shared
+ * chain; it does so for every tuning variant (tnq_plan_tuning: GEMM cut-over
+ * and tile shape) and keeps the variant whose selected configuration runs a
+ * batch fastest. Contraction results do not change beyond rounding (fusion
+ * and GEMM chains only regroup the same products). It modifies the plan: call it once, before the plan is shared
  * between threads. workspace/ws_bytes as for tnq_contract_sliced; bits is the
  * bitstring used for the trial batch. *out_n_fused (may be NULL) gets the
  * number of chains kept fused. */
@@ -261,6 +263,22 @@ tnq_status tnq_plan_fused_chains(const tnq_plan* plan, int32_t* last_bucket, siz
  * tuned plan reproduces it. Indices that name no chain are ignored. Drops the
  * plan's cached device configurations. */
 tnq_status tnq_plan_keep_chains(tnq_plan* plan, const int32_t* last_bucket, size_t n);
+
+/* Tuning of the plan's compiled program (an execution choice; the paper has
+ * no counterpart and results do not change beyond rounding):
+ *  gemm_min_k_log2: split precision only -- merged chains summing >= 2^this
+ *    values run as tensor-core GEMMs (the bucket-to-GEMM cut-over);
+ *  tile_low: a fused chain keeps its tile_low earliest output variables local
+ *    and picks its other local variables to minimise the operand entries a
+ *    tile reads (64: the earliest output variables only).
+ * tnq_plan_autotune measures cut-overs 2^3..2^6 and tile_low 3 / 64 and keeps
+ * the fastest. tnq_plan_set_tuning recompiles the program with the given
+ * values (every candidate chain fused; apply a stored selection afterwards
+ * with tnq_plan_keep_chains) and drops the plan's device configurations: call
+ * it before the plan is shared. TNQ_EINVAL for gemm_min_k_log2 outside
+ * [1, 16] or tile_low outside [0, 64]. Either output pointer may be NULL. */
+tnq_status tnq_plan_tuning(const tnq_plan* plan, int32_t* gemm_min_k_log2, int32_t* tile_low);
+tnq_status tnq_plan_set_tuning(tnq_plan* plan, int32_t gemm_min_k_log2, int32_t tile_low);
 
 /* tnq_amplitudes_batch: amplitudes of many bitstrings of many plans; each
  * amplitude is Eq. 5 for its bitstring (the sum over the plan's 2^p slices of

@@ -20,6 +20,18 @@ namespace tnq {
 static thread_local std::string g_last_error;
 void set_error(const std::string& msg) { g_last_error = msg; }
 int learned_propose(void* ctx, const Graph& g, const std::vector<int>& order, const TreeDecomposition& td, int p);
+void reset_device_state(const tnq_plan& P);
+
+void rebuild_program(tnq_plan* P, int gemm_min_k_log2, int tile_low) {
+  const tnq_plan_opts& o = P->opts;
+  P->prog = compile_program(P->net, P->order, P->mu);
+  P->prog.tile_low = tile_low;
+  P->gemm_min_k_log2 = gemm_min_k_log2;
+  if (o.precision != TNQ_PREC_C64) find_gemm_chains(P->prog, P->order, gemm_min_k_log2, 8);
+  if (o.leaf_absorb) absorb_leaves(P->prog);
+  fuse_chains(P->prog, P->order, o.fuse_min_rank);
+  reset_device_state(*P);
+}
 }  // namespace tnq
 
 using namespace tnq;
@@ -155,11 +167,7 @@ static void plan_network(tnq_plan* P, const tnq_plan_opts& o) {
   P->order = std::move(tr[best].order);
   P->tau = tr[best].tau;
   P->tau_full = treewidth_of_order(P->graph, P->order_full);
-  P->prog = compile_program(P->net, P->order, P->mu);
-  if (o.precision != TNQ_PREC_C64)
-    find_gemm_chains(P->prog, P->order, o.gemm_min_k_log2 > 0 ? o.gemm_min_k_log2 : 4, 8);
-  if (o.leaf_absorb) absorb_leaves(P->prog);
-  fuse_chains(P->prog, P->order, o.fuse_min_rank);
+  rebuild_program(P, o.gemm_min_k_log2 > 0 ? o.gemm_min_k_log2 : 4, 3);
   P->amp_scale_log2 = -0.5 * P->net.n_sqrt2 + (double)P->net.leaf_exp;
 }
 
@@ -298,6 +306,25 @@ tnq_status tnq_plan_buckets(const tnq_plan* P, int32_t* bag, int32_t* k, int32_t
     ++i;
   }
   return TNQ_OK;
+}
+
+tnq_status tnq_plan_tuning(const tnq_plan* P, int32_t* gemm_min_k_log2, int32_t* tile_low) {
+  if (!P) { set_error("NULL plan"); return TNQ_EINVAL; }
+  if (gemm_min_k_log2) *gemm_min_k_log2 = P->gemm_min_k_log2;
+  if (tile_low) *tile_low = P->prog.tile_low;
+  return TNQ_OK;
+}
+
+tnq_status tnq_plan_set_tuning(tnq_plan* P, int32_t gemm_min_k_log2, int32_t tile_low) {
+  if (!P) { set_error("NULL plan"); return TNQ_EINVAL; }
+  if (gemm_min_k_log2 < 1 || gemm_min_k_log2 > 16 || tile_low < 0 || tile_low > 64) {
+    set_error("gemm_min_k_log2 must be in [1, 16] and tile_low in [0, 64]");
+    return TNQ_EINVAL;
+  }
+  TNQ_TRY({
+    rebuild_program(P, gemm_min_k_log2, tile_low);
+    return TNQ_OK;
+  })
 }
 
 // ---- graph-level API ------------------------------------------------------

@@ -15,6 +15,13 @@ void destroy_device_state(DeviceState* s);
 void set_error(const std::string& msg);
 }  // namespace tnq
 
+namespace tnq {
+// (Re)compiles the plan's bucket program for its order and sliced set: GEMM
+// chains with K >= 2^gemm_min_k_log2 (split precision only), leaf absorption,
+// fused chains with tile_low forced output variables. Drops device state.
+void rebuild_program(tnq_plan* P, int gemm_min_k_log2, int tile_low);
+}  // namespace tnq
+
 struct tnq_plan {
   tnq_plan_opts opts{};
   tnq::Network net;
@@ -26,6 +33,7 @@ struct tnq_plan {
   int tau = 0;
   tnq::Program prog;
   double amp_scale_log2 = 0;     // amplitude *= 2^amp_scale_log2 (undoes the sqrt2 scaling)
+  int gemm_min_k_log2 = 4;       // GEMM cut-over the program was compiled with
   mutable std::mutex layout_mu;
   mutable std::map<std::pair<int, int>, size_t> layout_bytes;  // (mode, batch) -> workspace bytes
   mutable std::mutex dev_mu;

@@ -389,17 +389,9 @@ static std::vector<int> bag_of(const Program& P, const PBucket& b) {
 // operands one tile touches, i.e. what a block reads from L2 per tile (an
 // input holding no local variable becomes a per-block constant). With
 // keep_low >= the number of output variables this is the earliest-position
-// choice. TNQ_GROUP_TILE_LOW (environment, read once) overrides keep_low.
-static int group_tile_low() {
-  static const int v = [] {
-    const char* e = std::getenv("TNQ_GROUP_TILE_LOW");
-    return e ? std::atoi(e) : 3;
-  }();
-  return v;
-}
-
+// choice. keep_low is the program's tile_low.
 static void choose_tile(const Program& P, FusedGroup& g, const std::vector<int>& outv, int n_local) {
-  const int keep_low = group_tile_low();
+  const int keep_low = P.tile_low;
   std::vector<char> local(outv.size(), 0);
   int n = (int)g.local_vars.size();
   for (size_t i = 0; i < outv.size() && n < n_local && (int)i < keep_low; ++i, ++n) local[i] = 1;

@@ -1062,6 +1062,17 @@ __global__ void k_slice_sum(const double2* __restrict__ res, int B, const BatchH
   part[row] = make_double2(re, im);
 }
 
+// Adds one batch's per-bitstring partial sums (rows 0..n_rows-1) to the FP64
+// accumulators of those bitstrings. Batches are added in stream order, so each
+// bitstring's amplitude is summed in increasing item order (Eq. 5).
+__global__ void k_accumulate(const double2* __restrict__ part, int n_rows, double2* __restrict__ acc) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n_rows) {
+    acc[r].x += part[r].x;
+    acc[r].y += part[r].y;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // host side
 #define CU(call)                                                                  \
@@ -2099,8 +2110,12 @@ static bool use_graphs() {
 }
 
 // Runs the batch: header upload, then the captured graph (or direct launches).
-static tnq_status run_batch(const tnq_plan& P, ExecConfig& C, char* ws, cudaStream_t s, const BatchHdr& h) {
-  CU(cudaMemcpyAsync(ws + C.L.hdr_off, &h, sizeof(h), cudaMemcpyHostToDevice, s));
+// The header comes from host memory, or (d_hdr != nullptr) from device memory
+// already holding it, which keeps the copy asynchronous.
+static tnq_status run_batch(const tnq_plan& P, ExecConfig& C, char* ws, cudaStream_t s, const BatchHdr& h,
+                            const BatchHdr* d_hdr = nullptr) {
+  if (d_hdr) CU(cudaMemcpyAsync(ws + C.L.hdr_off, d_hdr, sizeof(BatchHdr), cudaMemcpyDeviceToDevice, s));
+  else CU(cudaMemcpyAsync(ws + C.L.hdr_off, &h, sizeof(h), cudaMemcpyHostToDevice, s));
   if (!use_graphs()) {
     enqueue_batch(P, C, ws, s);
     CU(cudaGetLastError());
@@ -2433,7 +2448,7 @@ static tnq_status profile_steps(const tnq_plan* plan, const uint8_t* bits, uint6
 }
 
 // Drops every device configuration of the plan (after its program changed).
-static void reset_device_state(const tnq_plan& P) {
+void reset_device_state(const tnq_plan& P) {
   {
     std::lock_guard<std::mutex> lk(P.dev_mu);
     if (P.dev) {
@@ -2555,32 +2570,35 @@ static tnq_status profile_steps_min(const tnq_plan* plan, const uint8_t* bits, u
 }
 }  // namespace tnq
 
-tnq_status tnq_plan_autotune(tnq_plan* plan, const uint8_t* bits, void* workspace, size_t ws_bytes,
-                             uint32_t max_batch, void* stream, int32_t* out_n_fused) {
-  if (!plan || (!bits && plan->net.n_qubits > 0) || !workspace) { set_error("NULL argument"); return TNQ_EINVAL; }
-  for (int q = 0; q < plan->net.n_qubits; ++q)
-    if (bits[q] > 1) { set_error("bitstring bytes must be 0 or 1"); return TNQ_EINVAL; }
+}  // extern "C"
+
+namespace tnq {
+// Chain selection for the plan's current program: times one batch with every
+// candidate chain fused and one with every bucket separate (CUDA events per
+// launch) and keeps each chain only where it is faster; when a GEMM chain is
+// rejected, the fusion pass is run again around the kept GEMM chains and the
+// new candidates are timed the same way. Leaves the selection applied and
+// returns the batch time of the selected configuration in *total_ms.
+static tnq_status select_chains(tnq_plan* plan, const uint8_t* bits, void* workspace, size_t ws_bytes, uint64_t cap,
+                                void* stream, float* total_ms) {
   Program& prog = plan->prog;
   const std::vector<FusedGroup> all = prog.groups;
   const uint64_t n_sl = 1ull << plan->mu.size();
+  // one batch size for both forms: the largest that fits both layouts
+  const int b_fused = pick_batch(*plan, 0, ws_bytes, cap);
+  set_groups(prog, {});
+  reset_device_state(*plan);
+  const int b_plain = pick_batch(*plan, 0, ws_bytes, cap);
+  set_groups(prog, all);
+  reset_device_state(*plan);
+  const int B = std::min(b_fused, b_plain);
+  if (B == 0) { set_error("workspace too small for one slice of the unfused plan"); return TNQ_ENOMEM; }
+  std::vector<float> tf, tu;
+  ExecConfig* C = nullptr;
+  tnq_status st;
+  std::vector<FusedGroup> keep;
   if (!all.empty()) {
-    tnq_status st = check_device();
-    if (st != TNQ_OK) return st;
-    // one batch size for both forms: the largest that fits both layouts
-    uint64_t cap = 1;
-    while (cap < n_sl && cap < (1ull << MAX_ITEM_BITS)) cap <<= 1;
-    if (max_batch > 0) cap = std::min<uint64_t>(cap, 1ull << ilog2_floor(max_batch));
-    const int b_fused = pick_batch(*plan, 0, ws_bytes, cap);
-    set_groups(prog, {});
-    reset_device_state(*plan);
-    const int b_plain = pick_batch(*plan, 0, ws_bytes, cap);
-    set_groups(prog, all);
-    reset_device_state(*plan);
-    const int B = std::min(b_fused, b_plain);
-    if (B == 0) { set_error("workspace too small for one slice of the unfused plan"); return TNQ_ENOMEM; }
     // every candidate chain fused
-    std::vector<float> tf, tu;
-    ExecConfig* C = nullptr;
     st = profile_steps_min(plan, bits, 0, n_sl, workspace, ws_bytes, (uint32_t)B, stream, tf, &C);
     if (st != TNQ_OK) return st;
     std::vector<float> group_ms(all.size(), 0.f);
@@ -2595,7 +2613,6 @@ tnq_status tnq_plan_autotune(tnq_plan* plan, const uint8_t* bits, void* workspac
       reset_device_state(*plan);
       return st;
     }
-    std::vector<FusedGroup> keep;
     bool gemm_dropped = false;
     for (size_t g = 0; g < all.size(); ++g) {
       float t_unfused = 0.f;
@@ -2631,10 +2648,63 @@ tnq_status tnq_plan_autotune(tnq_plan* plan, const uint8_t* bits, void* workspac
         if (all2[g].gemm || ms2[g] < t_unfused) keep.push_back(all2[g]);
       }
     }
-    set_groups(prog, keep);
-    reset_device_state(*plan);
   }
-  if (out_n_fused) *out_n_fused = (int32_t)prog.groups.size();
+  set_groups(prog, keep);
+  reset_device_state(*plan);
+  // the selected configuration, timed as a whole
+  std::vector<float> tsel;
+  st = profile_steps_min(plan, bits, 0, n_sl, workspace, ws_bytes, (uint32_t)B, stream, tsel, &C);
+  if (st != TNQ_OK) return st;
+  float tot = 0.f;
+  for (float x : tsel) tot += x;
+  *total_ms = tot;
+  return TNQ_OK;
+}
+}  // namespace tnq
+
+extern "C" {
+
+tnq_status tnq_plan_autotune(tnq_plan* plan, const uint8_t* bits, void* workspace, size_t ws_bytes,
+                             uint32_t max_batch, void* stream, int32_t* out_n_fused) {
+  if (!plan || (!bits && plan->net.n_qubits > 0) || !workspace) { set_error("NULL argument"); return TNQ_EINVAL; }
+  for (int q = 0; q < plan->net.n_qubits; ++q)
+    if (bits[q] > 1) { set_error("bitstring bytes must be 0 or 1"); return TNQ_EINVAL; }
+  tnq_status st = check_device();
+  if (st != TNQ_OK) return st;
+  const uint64_t n_sl = 1ull << plan->mu.size();
+  uint64_t cap = 1;
+  while (cap < n_sl && cap < (1ull << MAX_ITEM_BITS)) cap <<= 1;
+  if (max_batch > 0) cap = std::min<uint64_t>(cap, 1ull << ilog2_floor(max_batch));
+  // tuning variants: the GEMM cut-over (split precision only) and the fused
+  // chains' tile shape; each is compiled, its chains selected and the result
+  // timed; the fastest is kept (the first of equals)
+  std::vector<std::pair<int, int>> variants;
+  const std::vector<int> cuts = plan->opts.precision == TNQ_PREC_C64 ? std::vector<int>{plan->gemm_min_k_log2}
+                                                                      : std::vector<int>{3, 4, 5, 6};
+  for (int c : cuts)
+    for (int k : {3, 64}) variants.push_back({c, k});
+  int best = -1;
+  float best_ms = 0.f;
+  std::vector<FusedGroup> best_groups;
+  for (size_t v = 0; v < variants.size(); ++v) {
+    try {
+      rebuild_program(plan, variants[v].first, variants[v].second);
+    } catch (const std::exception& e) {
+      set_error(e.what());
+      return TNQ_EINVAL;
+    }
+    float ms = 0.f;
+    if ((st = select_chains(plan, bits, workspace, ws_bytes, cap, stream, &ms)) != TNQ_OK) return st;
+    if (best < 0 || ms < best_ms) {
+      best = (int)v;
+      best_ms = ms;
+      best_groups = plan->prog.groups;
+    }
+  }
+  rebuild_program(plan, variants[best].first, variants[best].second);
+  set_groups(plan->prog, best_groups);
+  reset_device_state(*plan);
+  if (out_n_fused) *out_n_fused = (int32_t)plan->prog.groups.size();
   return TNQ_OK;
 }
 
@@ -2761,62 +2831,185 @@ tnq_status tnq_amplitudes_batch(const tnq_plan* const* plans, size_t n_plans, co
   if (bits_offset[0] != 0) { set_error("bits_offset[0] must be 0"); return TNQ_EINVAL; }
   for (size_t i = 0; i < n_plans; ++i)
     if (!plans[i] || bits_offset[i + 1] < bits_offset[i]) { set_error("bad plan or bits_offset"); return TNQ_EINVAL; }
+  {
+    size_t pos = 0;
+    for (size_t i = 0; i < n_plans; ++i) {
+      const size_t nbytes = (bits_offset[i + 1] - bits_offset[i]) * (size_t)plans[i]->net.n_qubits;
+      for (size_t k = 0; k < nbytes; ++k)
+        if (bits[pos + k] > 1) { set_error("bitstring bytes must be 0 or 1"); return TNQ_EINVAL; }
+      pos += nbytes;
+    }
+  }
   tnq_status st = check_device();
   if (st != TNQ_OK) return st;
   if (!workspace) { set_error("workspace is NULL"); return TNQ_EINVAL; }
+  const size_t n_bits = bits_offset[n_plans];
+  if (n_bits == 0) return TNQ_OK;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   char* ws = reinterpret_cast<char*>(workspace);
-  size_t byte_pos = 0;
-  for (size_t pi = 0; pi < n_plans; ++pi) {
-    const tnq_plan& P = *plans[pi];
-    const int n = P.net.n_qubits;
-    const size_t nb = bits_offset[pi + 1] - bits_offset[pi];
-    const uint8_t* pb = bits + byte_pos;
-    byte_pos += nb * (size_t)n;
-    for (size_t i = 0; i < nb * (size_t)n; ++i)
-      if (pb[i] > 1) { set_error("bitstring bytes must be 0 or 1"); return TNQ_EINVAL; }
-    if (nb == 0) continue;
-    const int p = (int)P.mu.size();
-    const uint64_t n_items = (uint64_t)nb << p;
-    uint64_t cap = 1;
-    while (cap < n_items && cap < (1ull << MAX_ITEM_BITS)) cap <<= 1;
-    const int B = pick_batch(P, 1, ws_bytes, cap);
-    if (B == 0) { set_error("workspace too small for one item"); return TNQ_ENOMEM; }
-    ExecConfig* C = nullptr;
-    if ((st = get_config(P, 1, B, &C)) != TNQ_OK) return st;
-    std::vector<double> part(2 * (size_t)C->L.n_rows);
-    std::vector<double> acc(2 * nb, 0.0);
-    std::lock_guard<std::mutex> lk(P.dev_mu);
-    for (uint64_t base = 0; base < n_items; base += B) {
-      const uint64_t end = std::min<uint64_t>(n_items, base + B);
-      const uint64_t b0 = base >> p, b1 = (end - 1) >> p;  // bitstrings touched by this batch
-      std::vector<unsigned> words((size_t)C->L.n_words * C->L.n_rows, 0u);
-      for (uint64_t b = b0; b <= b1; ++b)
-        for (int q = 0; q < n; ++q)
-          if (pb[b * n + q]) words[(size_t)(b - b0) * C->L.n_words + (q >> 5)] |= 1u << (q & 31);
-      CU(cudaMemcpyAsync(ws + C->L.bits_off, words.data(), words.size() * 4, cudaMemcpyHostToDevice, s));
-      CU(cudaMemsetAsync(ws + C->L.status_off, 0, 4, s));
-      BatchHdr h;
-      std::memset(&h, 0, sizeof(h));
-      h.item_base = base;
-      h.item_end = n_items;
-      h.bstr_base = b0;
-      h.mode = 1;
-      h.p = p;
-      h.n_words = C->L.n_words;
-      if ((st = run_batch(P, *C, ws, s, h)) != TNQ_OK) return st;
-      CU(cudaMemcpyAsync(part.data(), ws + C->L.part_off, 16 * (size_t)C->L.n_rows, cudaMemcpyDeviceToHost, s));
-      int dev_status = 0;
-      CU(cudaMemcpyAsync(&dev_status, ws + C->L.status_off, 4, cudaMemcpyDeviceToHost, s));
-      CU(cudaStreamSynchronize(s));
-      if (dev_status) { set_error("a tensor-core wait timed out on the device"); return TNQ_ETIMEOUT; }
-      for (uint64_t b = b0; b <= b1; ++b) {
-        acc[2 * b] += part[2 * (b - b0)];
-        acc[2 * b + 1] += part[2 * (b - b0) + 1];
+
+  // Lanes: the plans run on up to N_LANES streams at once, each with its own
+  // part of the workspace (a plan always takes the lane of its first
+  // occurrence, so a repeated call reuses its captured graphs). Every batch's
+  // header and bitstrings go up in one copy at the start; each batch then adds
+  // its per-bitstring partial sums to device accumulators, and the call
+  // synchronises once, at the end.
+  constexpr int N_LANES = 4;
+  std::vector<int> lane_of(n_plans, -1);
+  int n_distinct = 0;
+  for (size_t i = 0; i < n_plans; ++i) {
+    if (bits_offset[i + 1] == bits_offset[i]) continue;
+    for (size_t j = 0; j < i && lane_of[i] < 0; ++j)
+      if (plans[j] == plans[i] && lane_of[j] >= 0) lane_of[i] = lane_of[j];
+    if (lane_of[i] < 0) lane_of[i] = n_distinct++;
+  }
+  const size_t tail_bytes = align_up(n_bits * sizeof(double2), 256) + 256;  // accumulators + lane status words
+  struct Job {
+    size_t plan;
+    uint64_t base, end;
+    int B, lane, rows;
+    ExecConfig* C;
+  };
+  std::vector<Job> jobs;
+  int n_lanes = 0;
+  size_t region = 0;
+  for (int K = std::min(N_LANES, n_distinct); K >= 1; --K) {
+    // the staging area for headers and bits is sized after the jobs are known;
+    // keep an eighth of the workspace for it and the accumulators
+    if (ws_bytes < tail_bytes + 4096) break;
+    const size_t usable = (ws_bytes - tail_bytes) / 8 * 7;
+    region = usable / K / 256 * 256;
+    bool fits = true;
+    for (size_t i = 0; i < n_plans && fits; ++i)
+      if (lane_of[i] >= 0 && pick_batch(*plans[i], 1, region, 1) == 0) fits = false;
+    if (fits) {
+      n_lanes = K;
+      break;
+    }
+  }
+  if (n_lanes == 0) { set_error("workspace too small for one item of some plan"); return TNQ_ENOMEM; }
+  for (size_t i = 0; i < n_plans; ++i) lane_of[i] = lane_of[i] < 0 ? -1 : lane_of[i] % n_lanes;
+  // batches of every plan, and their headers and bitstring words
+  std::vector<BatchHdr> hdrs;
+  std::vector<size_t> word_off;  // per job: first word of its bitstrings in `words`
+  std::vector<unsigned> words;
+  {
+    size_t byte_pos = 0;
+    for (size_t pi = 0; pi < n_plans; ++pi) {
+      const tnq_plan& P = *plans[pi];
+      const int n = P.net.n_qubits;
+      const size_t nb = bits_offset[pi + 1] - bits_offset[pi];
+      const uint8_t* pb = bits + byte_pos;
+      byte_pos += nb * (size_t)n;
+      if (nb == 0) continue;
+      const int p = (int)P.mu.size();
+      const uint64_t n_items = (uint64_t)nb << p;
+      uint64_t cap = 1;
+      while (cap < n_items && cap < (1ull << MAX_ITEM_BITS)) cap <<= 1;
+      const int B = pick_batch(P, 1, region, cap);
+      ExecConfig* C = nullptr;
+      if ((st = get_config(P, 1, B, &C)) != TNQ_OK) return st;
+      for (uint64_t base = 0; base < n_items; base += B) {
+        const uint64_t end = std::min<uint64_t>(n_items, base + B);
+        const uint64_t b0 = base >> p, b1 = (end - 1) >> p;  // bitstrings touched by this batch
+        Job J{pi, base, end, B, lane_of[pi], (int)(b1 - b0 + 1), C};
+        word_off.push_back(words.size());
+        words.resize(words.size() + (size_t)C->L.n_words * C->L.n_rows, 0u);
+        unsigned* w = words.data() + word_off.back();
+        for (uint64_t b = b0; b <= b1; ++b)
+          for (int q = 0; q < n; ++q)
+            if (pb[b * n + q]) w[(size_t)(b - b0) * C->L.n_words + (q >> 5)] |= 1u << (q & 31);
+        BatchHdr h;
+        std::memset(&h, 0, sizeof(h));
+        h.item_base = base;
+        h.item_end = n_items;
+        h.bstr_base = b0;
+        h.mode = 1;
+        h.p = p;
+        h.n_words = C->L.n_words;
+        hdrs.push_back(h);
+        jobs.push_back(J);
       }
     }
-    std::memcpy(out_amps + 2 * bits_offset[pi], acc.data(), 16 * nb);
   }
+  // tail of the workspace: staging (headers, then bitstring words), accumulators, lane status words
+  const size_t stage_bytes = align_up(hdrs.size() * sizeof(BatchHdr), 256) + align_up(words.size() * 4 + 4, 256);
+  const size_t lanes_bytes = (size_t)n_lanes * region;
+  if (lanes_bytes + stage_bytes + tail_bytes > ws_bytes) { set_error("workspace too small for the staging area"); return TNQ_ENOMEM; }
+  char* stage = ws + lanes_bytes;
+  BatchHdr* d_hdrs = reinterpret_cast<BatchHdr*>(stage);
+  unsigned* d_words = reinterpret_cast<unsigned*>(stage + align_up(hdrs.size() * sizeof(BatchHdr), 256));
+  double2* acc = reinterpret_cast<double2*>(stage + stage_bytes);
+  int* lane_status = reinterpret_cast<int*>(stage + stage_bytes + align_up(n_bits * sizeof(double2), 256));
+  CU(cudaMemcpyAsync(d_hdrs, hdrs.data(), hdrs.size() * sizeof(BatchHdr), cudaMemcpyHostToDevice, s));
+  if (!words.empty()) CU(cudaMemcpyAsync(d_words, words.data(), words.size() * 4, cudaMemcpyHostToDevice, s));
+  CU(cudaMemsetAsync(acc, 0, tail_bytes - 0, s));  // accumulators and lane status words
+  // lane streams: lane 0 is the caller's stream, the others fork from it and join it at the end
+  cudaStream_t ls[N_LANES] = {s};
+  cudaEvent_t fork = nullptr, join[N_LANES] = {};
+  auto cleanup = [&]() {
+    for (int k = 1; k < n_lanes; ++k) {
+      if (join[k]) cudaEventDestroy(join[k]);
+      if (ls[k]) cudaStreamDestroy(ls[k]);
+    }
+    if (fork) cudaEventDestroy(fork);
+  };
+  cudaError_t e = cudaSuccess;
+  if (n_lanes > 1) {
+    e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(fork, s);
+    for (int k = 1; k < n_lanes && e == cudaSuccess; ++k) {
+      e = cudaStreamCreateWithFlags(&ls[k], cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join[k], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(ls[k], fork, 0);
+    }
+    if (e != cudaSuccess) {
+      cleanup();
+      set_error(std::string("lane streams: ") + cudaGetErrorString(e));
+      return TNQ_ECUDA;
+    }
+  }
+  for (int k = 0; k < n_lanes; ++k) {  // the lane's status word (timeouts of the tensor-core waits)
+    e = cudaMemsetAsync(ws + (size_t)k * region + jobs[0].C->L.status_off, 0, 4, ls[k]);
+    if (e != cudaSuccess) break;
+  }
+  for (size_t ji = 0; ji < jobs.size() && e == cudaSuccess; ++ji) {
+    const Job& J = jobs[ji];
+    const tnq_plan& P = *plans[J.plan];
+    char* lws = ws + (size_t)J.lane * region;
+    cudaStream_t q = ls[J.lane];
+    ExecConfig& C = *J.C;
+    std::lock_guard<std::mutex> lk(P.dev_mu);  // one capture/launch sequence per plan at a time
+    e = cudaMemcpyAsync(lws + C.L.bits_off, d_words + word_off[ji], (size_t)C.L.n_words * C.L.n_rows * 4,
+                        cudaMemcpyDeviceToDevice, q);
+    if (e != cudaSuccess) break;
+    if ((st = run_batch(P, C, lws, q, hdrs[ji], d_hdrs + ji)) != TNQ_OK) {
+      cleanup();
+      return st;
+    }
+    k_accumulate<<<(J.rows + 127) / 128, 128, 0, q>>>(reinterpret_cast<const double2*>(lws + C.L.part_off), J.rows,
+                                                      acc + bits_offset[J.plan] + (J.base >> hdrs[ji].p));
+    e = cudaGetLastError();
+  }
+  for (int k = 0; k < n_lanes && e == cudaSuccess; ++k) {
+    e = cudaMemcpyAsync(lane_status + k, ws + (size_t)k * region + jobs[0].C->L.status_off, 4,
+                        cudaMemcpyDeviceToDevice, ls[k]);
+    if (e == cudaSuccess && k > 0) e = cudaEventRecord(join[k], ls[k]);
+    if (e == cudaSuccess && k > 0) e = cudaStreamWaitEvent(s, join[k], 0);
+  }
+  std::vector<double> out(2 * n_bits);
+  std::vector<int> lstat(n_lanes, 0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out.data(), acc, n_bits * sizeof(double2), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(lstat.data(), lane_status, n_lanes * 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cleanup();
+  if (e != cudaSuccess) {
+    set_error(std::string("batched amplitudes: ") + cudaGetErrorString(e));
+    return TNQ_ECUDA;
+  }
+  for (int k = 0; k < n_lanes; ++k)
+    if (lstat[k]) { set_error("a tensor-core wait timed out on the device"); return TNQ_ETIMEOUT; }
+  std::memcpy(out_amps, out.data(), 16 * n_bits);
   return TNQ_OK;
 }
 

@@ -99,6 +99,8 @@ SIGNATURES = {
     "tnq_graph_betweenness": (ctypes.c_int, [ctypes.c_int32, ctypes.c_size_t, _i32p, _f64p]),
     "tnq_plan_fused_chains": (ctypes.c_int, [_vp, _i32p, ctypes.c_size_t, _szp]),
     "tnq_plan_keep_chains": (ctypes.c_int, [_vp, _i32p, ctypes.c_size_t]),
+    "tnq_plan_tuning": (ctypes.c_int, [_vp, _i32p, _i32p]),
+    "tnq_plan_set_tuning": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32]),
     "tnq_circuit_graph": (ctypes.c_int, [ctypes.c_int32, _P(Gate), ctypes.c_size_t, ctypes.c_size_t, _i32p, _szp, _i32p]),
 }
 
@@ -232,6 +234,16 @@ class Plan:
         """Keep fused only the listed chains (tnq_plan_keep_chains)."""
         arr = np.ascontiguousarray(np.array(list(last_buckets) or [0], dtype=np.int32))
         _check(lib().tnq_plan_keep_chains(self.handle, _ptr(arr, ctypes.c_int32), len(last_buckets)))
+
+    def tuning(self):
+        """(gemm_min_k_log2, tile_low) the program is compiled with (tnq_plan_tuning)."""
+        k, t = ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().tnq_plan_tuning(self.handle, ctypes.byref(k), ctypes.byref(t)))
+        return k.value, t.value
+
+    def set_tuning(self, gemm_min_k_log2: int, tile_low: int):
+        """Recompile with the given GEMM cut-over and tile shape (tnq_plan_set_tuning)."""
+        _check(lib().tnq_plan_set_tuning(self.handle, gemm_min_k_log2, tile_low))
 
     def workspace_bytes(self, batch: int = 1) -> int:
         return int(lib().tnq_plan_workspace_bytes(self.handle, batch))

@@ -297,3 +297,24 @@ def test_parity_plans_cover_every_register_tail(tnq_lib):
             seen.update(buf[i] for i in range(n.value))
     assert {0, 2, 3, 4} <= seen, seen
     assert seen <= {0, 2, 3, 4}, seen  # depth 1 is not used (shared-memory stage instead)
+
+
+def test_tuning_roundtrip_and_validation(tnq_lib):
+    """tnq_plan_set_tuning recompiles the program (GEMM cut-over, tile shape);
+    every launch of the recompiled plan stays in bounds; bad values are refused."""
+    circ = I.random_grid_circuit(6, 6, 24, 5)
+    plan = tnq_lib.Plan(circ, max_bag_log2=18, max_p=20, reorder_every=1, precision=1, gemm_min_k_log2=4)
+    assert plan.tuning() == (4, 3)
+    n_gemm = {}
+    for k, low in ((3, 64), (6, 0), (4, 3)):
+        plan.set_tuning(k, low)
+        assert plan.tuning() == (k, low)
+        n_gemm[k] = plan.info()["n_gemm_buckets"]
+        msg = ctypes.create_string_buffer(512)
+        for mode in (0, 1):
+            assert tnq_lib.lib().tnq_internal_validate(plan.handle, mode, 4, msg, 512) == 0, msg.value
+    assert n_gemm[3] >= n_gemm[4] >= n_gemm[6]
+    for bad in ((0, 3), (17, 3), (4, -1), (4, 65)):
+        with pytest.raises(tnq_lib.TnqError) as e:
+            plan.set_tuning(*bad)
+        assert e.value.status == tnq_lib.EINVAL

@@ -392,3 +392,26 @@ def test_every_slicer_gives_the_same_amplitude(cuda, tnq_lib, oracle_lib, slicer
     for s in range(len(per)):
         assert rel_err(per[s], ref_per[s], 25) < TOL, s
     assert rel_err(amp, oracle_lib.contract(circ, bits), 25) < TOL
+
+
+def test_autotuned_tuning_reproduces_and_matches_oracle(cuda, tnq_lib, oracle_lib):
+    """The autotuner picks a GEMM cut-over and tile shape per plan; a plan built
+    later with the same options, given that tuning and chain selection, gives
+    bit-identical slices, and both match the oracle."""
+    circ = I.random_grid_circuit(6, 6, 24, 7)
+    bits = I.random_bitstring(36, 7)
+    kw = dict(max_bag_log2=20, max_p=20, reorder_every=1, precision=1, gemm_min_k_log2=4, fuse_min_rank=10)
+    plan = tnq_lib.Plan(circ, **kw)
+    plan.autotune(bits, max_batch=16)
+    tuning, kept = plan.tuning(), plan.fused_chains()
+    assert tuning[0] in (3, 4, 5, 6) and tuning[1] in (3, 64)
+    _, per = tnq_lib.contract_sliced(plan, bits, per_slice=True)
+    again = tnq_lib.Plan(circ, **kw)
+    again.set_tuning(*tuning)
+    again.keep_chains(kept)
+    assert again.fused_chains() == kept
+    _, per2 = tnq_lib.contract_sliced(again, bits, per_slice=True)
+    assert np.array_equal(per, per2)
+    ref, ref_per = oracle_lib.contract(circ, bits, order=plan.order(), mu=plan.sliced(), per_slice=True)
+    for s in range(len(per)):
+        assert rel_err(per[s], ref_per[s], 36) < SPLIT_TOL, s
