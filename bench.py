@@ -463,6 +463,70 @@ def run_batched(args):
         print(json.dumps(line), flush=True)
 
 
+def run_learned(args):
+    """Learned slicing proposer against tree-trimming on the 8x8 depth 1+32+1
+    circuit (seed 0) at bags <= 2^28: the exact cost model of both plans, and
+    their measured contraction speed on the GPU. One step = a fixed batch of 32
+    slices of the plan (the full amplitudes have thousands of slices; time per
+    amplitude = measured time per slice x 2^p, stated as extrapolated)."""
+    import numpy as np
+    import torch
+
+    from paper_2004_10892_gb300 import build as native_build
+    from paper_2004_10892_gb300 import inputs, learned, tnq
+    from paper_2004_10892_gb300.train_proposer import plan_pair
+
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    native_build.build()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    circ = inputs.random_grid_circuit(8, 8, 32, 0)
+    bits = inputs.random_bitstring(64, 0)
+    w = np.load(learned.TRAINED)
+    t_plan = time.perf_counter()
+    tt, ln = plan_pair(circ, w, max_bag_log2=28, max_p=60)
+    t_plan = time.perf_counter() - t_plan
+    stream = torch.cuda.current_stream()
+    n = 32
+    res = {}
+    for name, plan in (("tree_trimming", tt), ("learned", ln)):
+        ws = torch.empty(plan.workspace_bytes(n), dtype=torch.uint8, device="cuda")
+        for _ in range(args.warmup):
+            tnq.contract_sliced(plan, bits, 0, n, workspace=ws, max_batch=n, stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            tnq.contract_sliced(plan, bits, 0, n, workspace=ws, max_batch=n, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        i = plan.info()
+        res[name] = {"p": i["p"], "tau": i["tau"], "max_bag": i["max_bag"], "total_flops": i["total_flops"],
+                     "log2_total_flops": float(np.log2(i["total_flops"])), "flops_per_slice": i["flops_per_slice"],
+                     "bytes_per_slice": i["bytes_per_slice"], "slices_per_s": args.steps * n / t,
+                     "s_per_amplitude_extrapolated": t / (args.steps * n) * i["n_slices"]}
+        del ws
+    L, T = res["learned"], res["tree_trimming"]
+    line = {
+        "metric": "slice-contractions/s & time per amplitude, learned proposer vs tree-trimming, 8x8 d1+32+1",
+        "value": L["slices_per_s"], "unit": "slices/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * n / L["slices_per_s"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c64", "data": "synthetic",
+        "config": {"workload": "grid 8x8 depth 1+32+1 (seed 0), bags <= 2^28; a step = 32 slices of the learned "
+                               "plan", "weights": "paper_2004_10892_gb300/data/proposer_h128.npy", "plan_s": t_plan,
+                   "l2": "inputs larger than L2 (each slice streams hundreds of MB)"},
+        "time_per_amplitude_s": L["s_per_amplitude_extrapolated"],
+        "learned": L, "tree_trimming": T,
+        "learned_vs_tree_trimming": {"log2_total_flops": L["log2_total_flops"] - T["log2_total_flops"],
+                                     "time_per_amplitude_ratio": L["s_per_amplitude_extrapolated"] /
+                                     T["s_per_amplitude_extrapolated"]},
+        "e2e": None, "rel_err_vs_fp64": None, "cpu_baseline": None,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -470,9 +534,10 @@ def main():
                     help="timed steps (default 60, about 1 s of GPU time; 5 oracle slices for --impl reference)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="tnq", choices=["tnq", "reference"])
-    ap.add_argument("--config", default="7x7_d1+32+1", choices=sorted(CONFIGS) + ["batched"],
+    ap.add_argument("--config", default="7x7_d1+32+1", choices=sorted(CONFIGS) + ["batched", "learned"],
                     help="workload; 'batched' = 64 circuits (5x5..7x7 grids, depths 1+16+1..1+32+1) x 16 "
-                         "bitstrings per step in one tnq_amplitudes_batch call")
+                         "bitstrings per step in one tnq_amplitudes_batch call; 'learned' = the 8x8 depth 1+32+1 "
+                         "circuit sliced by the learned proposer against tree-trimming (bags <= 2^28)")
     ap.add_argument("--max-batch", type=int, default=256, help="slices contracted at once")
     ap.add_argument("--no-cpu-baseline", action="store_true",
                     help="skip the FP64 oracle (CPU baseline and the amplitude's error)")
@@ -509,6 +574,11 @@ def main():
         if args.steps is None or args.steps == 60:
             args.steps = 3
         run_batched(args)
+        return
+    if args.config == "learned":
+        if args.steps is None or args.steps == 60:
+            args.steps = 10
+        run_learned(args)
         return
     if args.impl == "reference":
         run_reference(args, args.config)
