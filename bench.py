@@ -117,26 +117,28 @@ class ClockSampler:
 
 
 # ncu DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of every
-# k_group launch of a one-slice batch of this workload (the autotuned chain
-# selection, reused through --tune-file; capture command in
-# profiles/k_group_7x7_d1+32+1.md), valid only for the runtime.cu with this
-# SHA-1 (reported as null once it changes). Per launch at batch B:
+# k_group launch of a one-slice batch of this workload (capture command in
+# profiles/k_group_7x7_d1+32+1.md), valid only while the fused-chain kernel's
+# source (runtime.cu between the "Fused chain of buckets" and "K4: amplitude"
+# comments) hashes to `kernel_sha1` and the plan has the recorded tuning and
+# k_group launch count (reported as null otherwise). Per launch at batch B:
 # bytes_one_slice x B / k_group launches per batch (traffic scales with the
 # slices of a batch; item-invariant operands are read once per batch, so this
 # slightly overstates it).
-# (counters taken on runtime.cu f5f103d8; the kernels are unchanged in the recorded source, which
-# only adds a host-side inspection hook)
-MEASURED_TRAFFIC = {"k_group": {"source_sha1": "b112175e81786ca76289bd4feee63bd6c9ca2027",
-                                "bytes_one_slice": 104181248.0, "launches": 12,
+MEASURED_TRAFFIC = {"k_group": {"kernel_sha1": None, "tuning": None, "bytes_one_slice": 0.0, "launches": 0,
                                 "capture": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:k_group "
-                                           "on a one-slice batch of the tuned default plan (12 launches)"}}
+                                           "on a one-slice batch of the tuned default plan"}}
 
 
-def runtime_source_sha1():
+def kernel_source_sha1():
+    """SHA-1 of the fused-chain kernel's source region of runtime.cu."""
     import hashlib
 
-    with open(os.path.join(ROOT, "paper_2004_10892_gb300", "csrc", "runtime.cu"), "rb") as f:
-        return hashlib.sha1(f.read()).hexdigest()
+    with open(os.path.join(ROOT, "paper_2004_10892_gb300", "csrc", "runtime.cu")) as f:
+        text = f.read()
+    a = text.index("// Fused chain of buckets")
+    b = text.index("// K4: amplitude")
+    return hashlib.sha1(text[a:b].encode()).hexdigest()
 
 
 # FP32 CUDA-core peak of GB300 from unit counts and clocks: 152 SMs x 128 FP32
@@ -222,7 +224,8 @@ def launch_roofline(L, plan, bits, ws, B, n_sl, stream, peaks, info):
         out["largest_launch"] = {"ms": ms[big], "flops": fl[big], "algorithmic_bytes": by[big],
                                  "achieved_tflops": fl[big] / (ms[big] / 1e3) / 1e12 if ms[big] > 0 else None}
         mt = MEASURED_TRAFFIC["k_group"]
-        if mt["source_sha1"] == runtime_source_sha1() and mt["bytes_one_slice"] > 0:
+        if (mt["kernel_sha1"] == kernel_source_sha1() and mt["tuning"] == list(plan.tuning())
+                and mt["launches"] == len(grp) and mt["bytes_one_slice"] > 0):
             out["traffic"] = mt["bytes_one_slice"] * b_out.value / len(grp)
             out["traffic_source"] = mt["capture"] + ", x batch / k_group launches per batch"
     out["peak_source"] = dom.get("peak_source", "measured (MEASURED_PEAKS.json hbm_gbs)")
