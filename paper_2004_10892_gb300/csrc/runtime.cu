@@ -2318,6 +2318,15 @@ int tnq_internal_group_text(const tnq_plan* plan, int mode, uint32_t batch, char
       }
     }
   }
+  for (size_t gi = 0; gi < C.gb.size(); ++gi) {
+    const GemmBucketArgs& G = C.gb[gi];
+    out += "gemm " + std::to_string(gi) + " ns " + std::to_string(G.ns) + " nx " + std::to_string(G.nx) + " ny " +
+           std::to_string(G.ny) + " nk " + std::to_string(G.nk) + " items " + std::to_string(G.items) + " pads " +
+           std::to_string(G.m_pad) + "x" + std::to_string(G.n_pad) + "x" + std::to_string(G.k_pad) + " na " +
+           std::to_string(G.na) + " nb " + std::to_string(G.nb) + " a0.kstride";
+    for (int q = 0; q < G.nk && q < 6; ++q) out += " " + std::to_string(G.a[0].kstride[q]);
+    out += "\n";
+  }
   std::snprintf(buf, cap, "%s", out.c_str());
   return out.size() + 1 > cap ? 2 : 0;
 }
