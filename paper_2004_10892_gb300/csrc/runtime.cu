@@ -2318,6 +2318,17 @@ int tnq_internal_group_text(const tnq_plan* plan, int mode, uint32_t batch, char
       }
     }
   }
+  for (size_t ki = 0; ki < C.kp.size(); ++ki) {
+    const KParams& K = C.kp[ki];
+    if (K.out_bits < 18) continue;
+    out += "bucket " + std::to_string(ki) + " G " + std::to_string(K.G) + " out_bits " + std::to_string(K.out_bits) +
+           " nin " + std::to_string(C.kshape[ki].first) + " sum " + std::to_string(K.sum) + "\n";
+    for (int j = 0; j < C.kshape[ki].first; ++j) {
+      out += "   in " + std::to_string(j) + " strides(bits 0-9):";
+      for (int b = 0; b < 10 && b < K.G; ++b) out += " " + std::to_string(K.stride[j][b]);
+      out += "\n";
+    }
+  }
   for (size_t gi = 0; gi < C.gb.size(); ++gi) {
     const GemmBucketArgs& G = C.gb[gi];
     out += "gemm " + std::to_string(gi) + " ns " + std::to_string(G.ns) + " nx " + std::to_string(G.nx) + " ny " +

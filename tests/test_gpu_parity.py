@@ -415,3 +415,31 @@ def test_autotuned_tuning_reproduces_and_matches_oracle(cuda, tnq_lib, oracle_li
     ref, ref_per = oracle_lib.contract(circ, bits, order=plan.order(), mu=plan.sliced(), per_slice=True)
     for s in range(len(per)):
         assert rel_err(per[s], ref_per[s], 36) < SPLIT_TOL, s
+
+
+def test_batched_call_lanes_duplicates_and_small_workspace(cuda, tnq_lib, oracle_lib):
+    """tnq_amplitudes_batch with the same plan listed twice, a plan with no
+    bitstrings between, several circuit sizes on the concurrent lanes, and a
+    workspace only large enough for one lane: every amplitude equals its own
+    single-bitstring contraction and the oracle."""
+    import torch
+
+    circs = [I.random_grid_circuit(4, 5, 16, 60 + k) for k in range(3)] + [I.random_grid_circuit(5, 5, 20, 63)]
+    plans = [tnq_lib.Plan(c, min_p=2, max_p=2) for c in circs]
+    order = [0, 1, 0, 2, 3, 1]
+    bl = [[I.random_bitstring(circs[i].n_qubits, 100 * j + k) for k in range(3)] for j, i in enumerate(order)]
+    bl[4] = []
+    lst = [plans[i] for i in order]
+    want = []
+    for j, i in enumerate(order):
+        for b in bl[j]:
+            want.append(tnq_lib.contract_sliced(plans[i], b))
+            ref = oracle_lib.contract(circs[i], b)
+            assert rel_err(want[-1], ref, circs[i].n_qubits) < TOL
+    got = tnq_lib.amplitudes_batch(lst, bl)
+    assert np.max(np.abs(got - np.array(want))) <= 1e-9 * np.max(np.abs(want))
+    # one lane: a workspace that fits one item of the largest plan plus the call's staging
+    need = max(p.workspace_bytes(1) for p in plans)
+    ws = torch.empty(need + need // 4 + (1 << 20), dtype=torch.uint8, device="cuda")
+    got1 = tnq_lib.amplitudes_batch(lst, bl, workspace=ws)
+    assert np.max(np.abs(got1 - np.array(want))) <= 1e-9 * np.max(np.abs(want))
