@@ -125,10 +125,12 @@ class ClockSampler:
 # bytes_one_slice x B / k_group launches per batch (traffic scales with the
 # slices of a batch; item-invariant operands are read once per batch, so this
 # slightly overstates it).
-MEASURED_TRAFFIC = {"k_group": {"kernel_sha1": "5f1d625d9404814f53a890ed81173b9e98775fee", "tuning": [3, 64],
-                                "bytes_one_slice": 105639680.0, "launches": 11,
-                                "capture": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:k_group "
-                                           "on a one-slice batch of the tuned default plan"}}
+MEASURED_TRAFFIC = {"k_group": [
+    {"kernel_sha1": "5f1d625d9404814f53a890ed81173b9e98775fee", "tuning": [3, 64], "bytes_one_slice": 105639680.0,
+     "launches": 11,
+     "capture": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:k_group -s 11 -c 11 on a one-slice "
+                "batch of the tuned default plan (tuning 2^3 / 64)"},
+]}
 
 
 def kernel_source_sha1():
@@ -224,11 +226,11 @@ def launch_roofline(L, plan, bits, ws, B, n_sl, stream, peaks, info):
         big = max(grp, key=lambda i: ms[i])
         out["largest_launch"] = {"ms": ms[big], "flops": fl[big], "algorithmic_bytes": by[big],
                                  "achieved_tflops": fl[big] / (ms[big] / 1e3) / 1e12 if ms[big] > 0 else None}
-        mt = MEASURED_TRAFFIC["k_group"]
-        if (mt["kernel_sha1"] == kernel_source_sha1() and mt["tuning"] == list(plan.tuning())
-                and mt["launches"] == len(grp) and mt["bytes_one_slice"] > 0):
-            out["traffic"] = mt["bytes_one_slice"] * b_out.value / len(grp)
-            out["traffic_source"] = mt["capture"] + ", x batch / k_group launches per batch"
+        for mt in MEASURED_TRAFFIC["k_group"]:
+            if (mt["kernel_sha1"] == kernel_source_sha1() and mt["tuning"] == list(plan.tuning())
+                    and mt["launches"] == len(grp) and mt["bytes_one_slice"] > 0):
+                out["traffic"] = mt["bytes_one_slice"] * b_out.value / len(grp)
+                out["traffic_source"] = mt["capture"] + ", x batch / k_group launches per batch"
     out["peak_source"] = dom.get("peak_source", "measured (MEASURED_PEAKS.json hbm_gbs)")
     out["batch"] = b_out.value
     out["other_kernel"] = other
