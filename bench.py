@@ -570,8 +570,9 @@ def main():
     ap.add_argument("--split-slices", action="store_true",
                     help="under torchrun: every rank contracts its contiguous share of one amplitude's 2^p slices "
                          "and the FP64 partial sums are all-reduced (strong scaling; Eq. 5)")
-    ap.add_argument("--tune-batch", type=int, default=16, help="slices per batch while autotuning")
-    ap.add_argument("--tune-gb", type=int, default=48, help="workspace GiB while autotuning")
+    ap.add_argument("--tune-batch", type=int, default=0,
+                    help="slices per batch while autotuning (0: the timed batch, so the choice is made at the size "
+                         "it is used at)")
     args = ap.parse_args()
     if args.steps is None:
         args.steps = 5 if args.impl == "reference" else 60
@@ -631,8 +632,11 @@ def main():
         plan.keep_chains(tf["kept_chains"])
         n_fused = len(plan.fused_chains())
     elif not args.no_autotune:
-        tune_ws = torch.empty(args.tune_gb << 30, dtype=torch.uint8, device="cuda")
-        n_fused = plan.autotune(bits, workspace=tune_ws, max_batch=min(args.tune_batch, n_sl), stream=stream)
+        tb = min(args.tune_batch if args.tune_batch > 0 else args.max_batch, n_sl)
+        free, _ = torch.cuda.mem_get_info()
+        # (the autotuner lowers the batch itself when the unfused layout does not fit)
+        tune_ws = torch.empty(int(0.9 * free) // 256 * 256, dtype=torch.uint8, device="cuda")
+        n_fused = plan.autotune(bits, workspace=tune_ws, max_batch=tb, stream=stream)
         del tune_ws
         if args.tune_file and rank == 0:
             with open(args.tune_file, "w") as f:

@@ -454,6 +454,8 @@ __device__ __forceinline__ void split16(const float* x, uint4* hi, uint4* lo) {
 // tensor has at most two), and an operand that does not vary with the low K
 // bits is loaded once per chunk.
 constexpr int PK_BITS = 3 * GB_BITS;
+constexpr int PK_TABS = PK_BITS / 8;   // byte tables of operand 0's offset (W bits 8q .. 8q+7)
+constexpr int PK_ITEMS = 64;           // items whose operand scales are kept in shared memory
 template <int KIND>
 __global__ void k_gemm_pack(const GemmBucketArgs g, int side) {
   __shared__ int s_nz[GB_SIDE];
@@ -461,6 +463,9 @@ __global__ void k_gemm_pack(const GemmBucketArgs g, int side) {
   __shared__ long long s_str[GB_SIDE][PK_BITS];
   __shared__ int s_klo[GB_SIDE][8];
   __shared__ int s_kdep[GB_SIDE];
+  __shared__ int s_kvec[GB_SIDE];          // 1: the chunk's K values are consecutive entries (vector loads)
+  __shared__ long long s_tab0[PK_TABS][256];  // operand 0: offset of each value of W's byte q
+  __shared__ float s_f[GB_SIDE][PK_ITEMS];    // power-of-two scale of operand j for item it
   constexpr int ES = KIND == GEMM_BF16 ? 2 : 4;
   constexpr int CH = 16 / ES;
   constexpr int CHB = KIND == GEMM_BF16 ? 3 : 2;  // log2 CH
@@ -498,7 +503,36 @@ __global__ void k_gemm_pack(const GemmBucketArgs g, int side) {
       kdep |= a != 0;
     }
     s_kdep[j] = kdep;
+    int kvec = CHB <= g.nk;
+    for (int q = 0; q < CH && kvec; ++q) kvec = s_klo[j][q] == q;
+    s_kvec[j] = kvec;
   }
+  // operand 0 (the large one): its offset as a sum of per-byte table values
+  // of W, so an element costs one table read per byte instead of one test
+  // per nonzero stride
+  for (int e = threadIdx.x; e < PK_TABS * 256; e += blockDim.x) {
+    const int q = e >> 8, v = e & 255;
+    const GemmOperand& o = ops[0];
+    long long a = 0;
+    for (int b = 0; b < 8; ++b) {
+      const int p = 8 * q + b;
+      if (!((v >> b) & 1) || p >= wbits) continue;
+      a += p < g.ns ? o.sstride[p] : (p < g.ns + nr ? o.rstride[p - g.ns] : o.kstride[p - g.ns - nr + CHB]);
+    }
+    s_tab0[q][v] = a;
+  }
+  const bool f_tab = g.items <= PK_ITEMS;
+  if (f_tab)
+    for (int e = threadIdx.x; e < nops * g.items; e += blockDim.x) {
+      const int j = e / g.items, it = e - j * g.items;
+      const GemmOperand& o = ops[j];
+      float f = 1.f;
+      if (o.meta >= 0) {
+        int m;
+        f = pack_scale(g.meta_m[(long long)o.meta * g.B + (o.dep ? it : 0)], &m);
+      }
+      s_f[j][it] = f;
+    }
   __syncthreads();
   if (side == 0 && blockIdx.x == 0) {
     // output exponent per item: sum over every operand of its exponent and scale shift
@@ -534,20 +568,39 @@ __global__ void k_gemm_pack(const GemmBucketArgs g, int side) {
       im[q] = 0.f;
     }
     if (row_ok && k0 < (1 << g.nk)) {
+      const unsigned long long W = (unsigned long long)sidx | ((unsigned long long)r << g.ns) |
+                                   ((unsigned long long)(k0 >> CHB) << (g.ns + nr));
       for (int j = 0; j < nops; ++j) {
         const GemmOperand& o = ops[j];
         float f = 1.f;
-        if (o.meta >= 0) {
+        if (f_tab) {
+          f = s_f[j][item];
+        } else if (o.meta >= 0) {
           int m;
           f = pack_scale(g.meta_m[(long long)o.meta * g.B + (o.dep ? item : 0ll)], &m);
         }
         long long base = o.dep ? item * o.istride : 0ll;
-        const unsigned long long W = (unsigned long long)sidx | ((unsigned long long)r << g.ns) |
-                                     ((unsigned long long)(k0 >> CHB) << (g.ns + nr));
-        const int nz = s_nz[j];
-        for (int i = 0; i < nz; ++i)
-          if ((W >> s_pos[j][i]) & 1ull) base += s_str[j][i];
-        if (!s_kdep[j]) {  // the same value for every K of the chunk
+        if (j == 0) {
+#pragma unroll
+          for (int q = 0; q < PK_TABS; ++q)
+            if (8 * q < wbits) base += s_tab0[q][(W >> (8 * q)) & 255ull];
+        } else {
+          const int nz = s_nz[j];
+          for (int i = 0; i < nz; ++i)
+            if ((W >> s_pos[j][i]) & 1ull) base += s_str[j][i];
+        }
+        if (s_kvec[j] && j == 0 && k0 + CH <= (1 << g.nk)) {
+          // CH consecutive entries: vector loads; operand 0 is the first factor
+          const float4* src = reinterpret_cast<const float4*>(o.ptr + base);
+#pragma unroll
+          for (int q = 0; q < CH / 2; ++q) {
+            const float4 v = __ldg(src + q);
+            re[2 * q] = v.x * f;
+            im[2 * q] = v.y * f;
+            re[2 * q + 1] = v.z * f;
+            im[2 * q + 1] = v.w * f;
+          }
+        } else if (!s_kdep[j]) {  // the same value for every K of the chunk
           const float2 v = o.ptr[base];
           const float vx = v.x * f, vy = v.y * f;
 #pragma unroll
