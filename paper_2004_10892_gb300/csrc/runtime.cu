@@ -52,6 +52,7 @@ struct KParams {
   int out_bits;                  // output variables per item
   int G;                         // out_bits + item bits
   int sum;                       // 1: sum over bit 0 of every input (Eq. 2); 0: product only
+  int n_var;                     // inputs 0..n_var-1 vary with output bits 0-7; the others do not
   int B;                         // meta row length
   int* meta_e;
   unsigned* meta_m;
@@ -66,7 +67,7 @@ struct HoistDev {
   int in_meta[KMAX];              // meta row of input j, -1 for gate tensors (unit scale)
   int nin, bits, sum, out_meta;   // inputs, output bits, 1: sum over bit 0 (Eq. 2), meta row of the result
   int blk0;                       // first block of this bucket in its level's launch
-  int pad;
+  int nvar;                       // inputs 0..nvar-1 vary with the output's low 8 bits (k_bucket's order)
 };
 
 struct LeafDev {
@@ -217,6 +218,7 @@ __global__ void __launch_bounds__(TPB) k_bucket(const __grid_constant__ KParams 
   constexpr int ITER = (LT > 8) ? (1 << (LT - 8)) : 1;
   __shared__ long long sh_off[NIN][ITER];
   __shared__ float sh_red[TPB / 32];
+  __shared__ float4 sh_c[ITER];  // product of the thread-invariant inputs per iteration (pair over u)
   const int t = threadIdx.x;
   const long long g0 = (long long)blockIdx.x << LT;
   const long long total = 1ll << P.G;
@@ -259,6 +261,30 @@ __global__ void __launch_bounds__(TPB) k_bucket(const __grid_constant__ KParams 
     }
   };
   if (uniform) load_scales(g0 >> ob);
+  // thread-invariant inputs (n_var..NIN-1) of a block with one item: their
+  // scaled (u = 0, u = 1) product per iteration, once per block
+  const bool use_c = uniform && P.n_var < NIN;
+  if (use_c) {
+    if (t < ITER && g0 + ((long long)t << 8) < total) {
+      float2 c0 = make_float2(1.f, 0.f), c1 = make_float2(1.f, 0.f);
+#pragma unroll
+      for (int j = 0; j < NIN; ++j) {
+        if (j < P.n_var) continue;
+        const long long idx = sh_off[j][t];
+        if (P.sum) {
+          const float4 v = __ldg(reinterpret_cast<const float4*>(P.in[j] + idx));
+          c0 = cmul(c0, make_float2(v.x * f[j], v.y * f[j]));
+          c1 = cmul(c1, make_float2(v.z * f[j], v.w * f[j]));
+        } else {
+          const float2 v = __ldg(P.in[j] + idx);
+          c0 = cmul(c0, make_float2(v.x * f[j], v.y * f[j]));
+        }
+      }
+      sh_c[t] = make_float4(c0.x, c0.y, c1.x, c1.y);
+    }
+    __syncthreads();
+  }
+  const int nv = P.n_var;
 
   const long long omask = (1ll << ob) - 1ll;
   const int lane = t & 31;
@@ -271,32 +297,49 @@ __global__ void __launch_bounds__(TPB) k_bucket(const __grid_constant__ KParams 
     float m = 0.f;
     if (valid) {
       if (!uniform) load_scales(item);
+      // the same arithmetic in both forms (so a slice's value does not depend on
+      // the batch size): the thread-invariant inputs' product from (1, 0) in
+      // input order, then the varying inputs in input order
       float2 r;
-      if (P.sum) {
-        float2 a0 = make_float2(1.f, 0.f), a1 = make_float2(1.f, 0.f);
+      float4 cc;
+      if (use_c) {
+        cc = sh_c[it];
+      } else {
+        float2 c0 = make_float2(1.f, 0.f), c1 = make_float2(1.f, 0.f);
 #pragma unroll
         for (int j = 0; j < NIN; ++j) {
+          if (j < nv) continue;
+          const long long idx = sh_off[j][it];
+          if (P.sum) {
+            const float4 v = __ldg(reinterpret_cast<const float4*>(P.in[j] + idx));
+            c0 = cmul(c0, make_float2(v.x * f[j], v.y * f[j]));
+            c1 = cmul(c1, make_float2(v.z * f[j], v.w * f[j]));
+          } else {
+            const float2 v = __ldg(P.in[j] + idx);
+            c0 = cmul(c0, make_float2(v.x * f[j], v.y * f[j]));
+          }
+        }
+        cc = make_float4(c0.x, c0.y, c1.x, c1.y);
+      }
+      if (P.sum) {
+        float2 a0 = make_float2(cc.x, cc.y), a1 = make_float2(cc.z, cc.w);
+#pragma unroll
+        for (int j = 0; j < NIN; ++j) {
+          if (j >= nv) break;
           const long long idx = sh_off[j][it] + tp[j];
           float4 v = __ldg(reinterpret_cast<const float4*>(P.in[j] + idx));
-          const float2 x0 = make_float2(v.x * f[j], v.y * f[j]);
-          const float2 x1 = make_float2(v.z * f[j], v.w * f[j]);
-          if (j == 0) {
-            a0 = x0;
-            a1 = x1;
-          } else {
-            a0 = cmul(a0, x0);
-            a1 = cmul(a1, x1);
-          }
+          a0 = cmul(a0, make_float2(v.x * f[j], v.y * f[j]));
+          a1 = cmul(a1, make_float2(v.z * f[j], v.w * f[j]));
         }
         r = make_float2(a0.x + a1.x, a0.y + a1.y);
       } else {
-        float2 a = make_float2(1.f, 0.f);
+        float2 a = make_float2(cc.x, cc.y);
 #pragma unroll
         for (int j = 0; j < NIN; ++j) {
+          if (j >= nv) break;
           const long long idx = sh_off[j][it] + tp[j];
           const float2 v = __ldg(P.in[j] + idx);
-          const float2 x = make_float2(v.x * f[j], v.y * f[j]);
-          a = (j == 0) ? x : cmul(a, x);
+          a = cmul(a, make_float2(v.x * f[j], v.y * f[j]));
         }
         r = a;
       }
@@ -364,21 +407,23 @@ __global__ void __launch_bounds__(256) k_bucket_level(const HoistDev* __restrict
   const long long g = (long long)(blockIdx.x - H.blk0) * 256 + t;
   float mx = 0.f;
   if (g < (1ll << bits)) {
+    // the arithmetic order of k_bucket (thread-invariant inputs nvar.. first,
+    // then 0..nvar-1), so that a bucket's value does not depend on which
+    // kernel runs it
     float2 a0 = make_float2(1.f, 0.f), a1 = make_float2(1.f, 0.f);
-    for (int j = 0; j < nin; ++j) {
+    for (int jj = 0; jj < nin; ++jj) {
+      const int j = jj < nin - H.nvar ? H.nvar + jj : jj - (nin - H.nvar);
       long long idx = 0;
       for (int i = 0; i < bits; ++i)
         if ((g >> i) & 1ll) idx += s_str[j][i];
       const float f = s_f[j];
       if (H.sum) {
         const float4 v = __ldg(reinterpret_cast<const float4*>(s_in[j] + idx));
-        const float2 x0 = make_float2(v.x * f, v.y * f), x1 = make_float2(v.z * f, v.w * f);
-        a0 = j ? cmul(a0, x0) : x0;
-        a1 = j ? cmul(a1, x1) : x1;
+        a0 = cmul(a0, make_float2(v.x * f, v.y * f));
+        a1 = cmul(a1, make_float2(v.z * f, v.w * f));
       } else {
         const float2 v = __ldg(s_in[j] + idx);
-        const float2 x = make_float2(v.x * f, v.y * f);
-        a0 = j ? cmul(a0, x) : x;
+        a0 = cmul(a0, make_float2(v.x * f, v.y * f));
       }
     }
     const float2 r = H.sum ? make_float2(a0.x + a1.x, a0.y + a1.y) : a0;
@@ -1364,6 +1409,26 @@ static KParams single_kparams(const tnq_plan& P, const Layout& L, const PBucket&
     }
     for (int i = k.out_bits; i < k.G; ++i) k.stride[j][i] = L.dep[tid] ? ((1ll << x.rank()) << (i - k.out_bits)) : 0;
   }
+  // inputs that vary with the low 8 bits (a block's threads) first; the others
+  // are the same for every thread of a block's iteration (k_bucket multiplies
+  // them once per block into a constant pair)
+  auto varies = [&](int j) {
+    for (int i = 0; i < 8 && i < k.G; ++i)
+      if (k.stride[j][i]) return true;
+    return false;
+  };
+  int nv = 0;
+  for (int j = 0; j < b.k; ++j)
+    if (varies(j)) {
+      if (j != nv) {
+        std::swap(k.in[j], k.in[nv]);
+        std::swap(k.in_meta[j], k.in_meta[nv]);
+        std::swap(k.in_dep[j], k.in_dep[nv]);
+        for (int i = 0; i < GMAX; ++i) std::swap(k.stride[j][i], k.stride[nv][i]);
+      }
+      ++nv;
+    }
+  k.n_var = nv;
   return k;
 }
 
@@ -1740,6 +1805,7 @@ static bool build_steps(const tnq_plan& P, const Layout& L, ExecConfig& C) {
       h.sum = k.sum;
       h.out_meta = k.out_meta;
       h.blk0 = blocks;
+      h.nvar = k.n_var;
       for (int j = 0; j < h.nin; ++j) {
         h.in[j] = (long long)reinterpret_cast<size_t>(k.in[j]);
         h.in_meta[j] = k.in_meta[j];
@@ -1789,11 +1855,16 @@ static std::string validate_config(const tnq_plan& P, int mode, int B) {
     const KParams& k = C.kp[single++];
     if ((1ll << k.G) > alloc(b.output)) return "bucket " + std::to_string(bi) + ": output overflows";
     if (off_of(k.out) != L.off[b.output]) return "bucket output pointer";
-    for (int j = 0; j < b.k; ++j) {
+    for (int jb = 0; jb < b.k; ++jb) {
+      // the launch lists the bucket's inputs reordered (thread-varying ones first)
+      int j = -1;
+      for (int q = 0; q < b.k; ++q)
+        if (off_of(k.in[q]) == L.off[b.inputs[jb]]) j = q;
+      if (j < 0) return "bucket " + std::to_string(bi) + ": input pointer";
       long long mx = 0;
       for (int i = 0; i < k.G; ++i) mx += k.stride[j][i];
       if (k.sum) mx += 1;
-      if (mx >= alloc(b.inputs[j])) return "bucket " + std::to_string(bi) + ": input " + std::to_string(j) + " overflows";
+      if (mx >= alloc(b.inputs[jb])) return "bucket " + std::to_string(bi) + ": input " + std::to_string(jb) + " overflows";
       if (k.sum && (((size_t)k.in[j] / 8) & 1)) return "unaligned input";
       for (int i = 0; i < k.G; ++i)
         if (k.sum && (k.stride[j][i] & 1)) return "odd stride in a summing bucket";
