@@ -417,7 +417,7 @@ def run_batched(args):
         B = 1
         while B < items and B < (1 << 16) and p.workspace_bytes(2 * B) <= region:
             B *= 2
-        launches += -(-items // B) * (tnq.lib().tnq_internal_launches_per_batch(p.handle) + 1)
+        launches += -(-items // B) * (tnq.lib().tnq_internal_launches_per_batch(p.handle, 1, B) + 1)
     launches *= args.steps
     # the plan with the most work: per-launch roofline of one of its batches
     big = max(range(len(plans)), key=lambda i: plans[i].info()["total_flops"])
@@ -691,7 +691,8 @@ def main():
     value = total_slices / t_dev
     e2e_value = total_slices / t_wall
     n_batches = (my_e - my_b + B - 1) // B
-    launches = args.steps * n_batches * L.tnq_internal_launches_per_batch(plan.handle)
+    L.tnq_internal_launches_per_batch.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32]
+    launches = args.steps * n_batches * L.tnq_internal_launches_per_batch(plan.handle, 0, B)
 
     # live per-launch timing of one batch (CUDA events on the launching stream)
     roof = None

@@ -63,11 +63,13 @@ struct KParams {
 struct HoistDev {
   long long out;                  // arena byte offset of the result
   long long in[KMAX];             // arena byte offsets of the inputs
-  long long stride[KMAX][HOIST_MAX_BITS];  // element stride of each output bit, per input
+  long long stride[KMAX][HOIST_MAX_BITS];  // element stride of each index bit (output bits, then item bits), per input
   int in_meta[KMAX];              // meta row of input j, -1 for gate tensors (unit scale)
-  int nin, bits, sum, out_meta;   // inputs, output bits, 1: sum over bit 0 (Eq. 2), meta row of the result
+  int in_dep[KMAX];               // 1: input j's meta row is per item
+  int nin, bits, sum, out_meta;   // inputs, index bits, 1: sum over bit 0 (Eq. 2), meta row of the result
+  int obits, out_dep;             // output bits per item; 1: the result is per item (items above bit obits)
   int blk0;                       // first block of this bucket in its level's launch
-  int nvar;                       // inputs 0..nvar-1 vary with the output's low 8 bits (k_bucket's order)
+  int nvar;                       // inputs 0..nvar-1 vary with the index's low 8 bits (k_bucket's order)
 };
 
 struct LeafDev {
@@ -371,14 +373,17 @@ __global__ void __launch_bounds__(TPB) k_bucket(const __grid_constant__ KParams 
 }
 
 // K1 for the early buckets of one level (see hoist_levels): every bucket of
-// the level in one launch, 256 entries per block; block b works on the bucket
-// whose blk0 is the largest not above b. Item-invariant: one meta row each.
+// the level in one launch, 256 index entries per block; block b works on the
+// bucket whose blk0 is the largest not above b. Item-dependent buckets carry
+// the item above their output bits; their scales, exponents and maxima are
+// per item, as in k_bucket, and so is the arithmetic order.
 __global__ void __launch_bounds__(256) k_bucket_level(const HoistDev* __restrict__ hd, int n, char* arena,
                                                      int* meta_e, unsigned* meta_m, int B) {
   __shared__ int s_b;
   __shared__ long long s_str[KMAX][HOIST_MAX_BITS];
   __shared__ const float2* s_in[KMAX];
   __shared__ float s_f[KMAX];
+  __shared__ int s_e;
   __shared__ float s_red[8];
   const int t = threadIdx.x;
   if (t == 0) {
@@ -392,21 +397,38 @@ __global__ void __launch_bounds__(256) k_bucket_level(const HoistDev* __restrict
   }
   __syncthreads();
   const HoistDev& H = hd[s_b];
-  const int nin = H.nin, bits = H.bits;
+  const int nin = H.nin, bits = H.bits, ob = H.obits;
+  const long long g0 = (long long)(blockIdx.x - H.blk0) * 256;
+  const bool uniform = ob >= 8 || ob == bits;  // one item for the whole block
   for (int e = t; e < nin * bits; e += 256) s_str[e / bits][e % bits] = H.stride[e / bits][e % bits];
-  if (t < nin) {
-    s_in[t] = reinterpret_cast<const float2*>(arena + H.in[t]);
-    if (H.in_meta[t] < 0) {
-      s_f[t] = 1.f;
-    } else {
+  if (t < nin) s_in[t] = reinterpret_cast<const float2*>(arena + H.in[t]);
+  if (uniform && t == 0) {  // the block's item: scales and the output exponent
+    const long long item = g0 >> ob;
+    int e = 0;
+    for (int j = 0; j < nin; ++j) {
+      if (H.in_meta[j] < 0) {
+        s_f[j] = 1.f;
+        continue;
+      }
+      const long long row = (long long)H.in_meta[j] * B + (H.in_dep[j] ? item : 0ll);
       int m;
-      s_f[t] = scale_of_max(meta_m[(long long)H.in_meta[t] * B], &m);
+      s_f[j] = scale_of_max(meta_m[row], &m);
+      e += meta_e[row] + m;
     }
+    s_e = e;
   }
   __syncthreads();
-  const long long g = (long long)(blockIdx.x - H.blk0) * 256 + t;
+  const long long g = g0 + t;
+  const long long item = g >> ob;
   float mx = 0.f;
   if (g < (1ll << bits)) {
+    // scale of input j for this entry's item
+    auto scale = [&](int j) -> float {
+      if (uniform) return s_f[j];
+      if (H.in_meta[j] < 0) return 1.f;
+      int m;
+      return scale_of_max(meta_m[(long long)H.in_meta[j] * B + (H.in_dep[j] ? item : 0ll)], &m);
+    };
     // the arithmetic order of k_bucket (thread-invariant inputs nvar.. first,
     // then 0..nvar-1), so that a bucket's value does not depend on which
     // kernel runs it
@@ -416,38 +438,50 @@ __global__ void __launch_bounds__(256) k_bucket_level(const HoistDev* __restrict
       long long idx = 0;
       for (int i = 0; i < bits; ++i)
         if ((g >> i) & 1ll) idx += s_str[j][i];
-      const float f = s_f[j];
+      const float fj = scale(j);
       if (H.sum) {
         const float4 v = __ldg(reinterpret_cast<const float4*>(s_in[j] + idx));
-        a0 = cmul(a0, make_float2(v.x * f, v.y * f));
-        a1 = cmul(a1, make_float2(v.z * f, v.w * f));
+        a0 = cmul(a0, make_float2(v.x * fj, v.y * fj));
+        a1 = cmul(a1, make_float2(v.z * fj, v.w * fj));
       } else {
         const float2 v = __ldg(s_in[j] + idx);
-        a0 = cmul(a0, make_float2(v.x * f, v.y * f));
+        a0 = cmul(a0, make_float2(v.x * fj, v.y * fj));
       }
     }
     const float2 r = H.sum ? make_float2(a0.x + a1.x, a0.y + a1.y) : a0;
     reinterpret_cast<float2*>(arena + H.out)[g] = r;
     mx = fmaxf(fabsf(r.x), fabsf(r.y));
-  }
-  for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-  if ((t & 31) == 0) s_red[t >> 5] = mx;
-  __syncthreads();
-  if (t == 0) {
-    float b = 0.f;
-    for (int w = 0; w < 8; ++w) b = fmaxf(b, s_red[w]);
-    if (b > 0.f) atomic_max_pos(&meta_m[(long long)H.out_meta * B], b);
-    if ((int)blockIdx.x == H.blk0) {
-      int e = 0;
-      for (int j = 0; j < nin; ++j) {
-        if (H.in_meta[j] < 0) continue;
-        const long long row = (long long)H.in_meta[j] * B;
-        int m;
-        scale_of_max(meta_m[row], &m);
-        e += meta_e[row] + m;
+    if ((g & ((1ll << ob) - 1ll)) == 0) {  // the item's first entry writes its exponent
+      int esum = 0;
+      if (uniform) {
+        esum = s_e;
+      } else {
+        for (int j = 0; j < nin; ++j) {
+          if (H.in_meta[j] < 0) continue;
+          const long long row = (long long)H.in_meta[j] * B + (H.in_dep[j] ? item : 0ll);
+          int m;
+          scale_of_max(meta_m[row], &m);
+          esum += meta_e[row] + m;
+        }
       }
-      meta_e[(long long)H.out_meta * B] = e;
+      meta_e[(long long)H.out_meta * B + (H.out_dep ? item : 0ll)] = esum;
     }
+  }
+  if (uniform) {
+    for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if ((t & 31) == 0) s_red[t >> 5] = mx;
+    __syncthreads();
+    if (t == 0) {
+      float b = 0.f;
+      for (int w = 0; w < 8; ++w) b = fmaxf(b, s_red[w]);
+      if (b > 0.f) atomic_max_pos(&meta_m[(long long)H.out_meta * B + (H.out_dep ? (g0 >> ob) : 0ll)], b);
+    }
+  } else {
+    // items change every 2^ob entries: reduce within aligned lane groups
+    const int grp = 1 << (ob < 5 ? ob : 5);
+    for (int off = 1; off < grp; off <<= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if ((t & (grp - 1)) == 0 && mx > 0.f && g < (1ll << bits))
+      atomic_max_pos(&meta_m[(long long)H.out_meta * B + (H.out_dep ? item : 0ll)], mx);
   }
 }
 
@@ -1169,19 +1203,21 @@ GemmShape gemm_shape(const tnq_plan& P, const FusedGroup& g, int items) {
   return s;
 }
 
-// Early buckets: a single (unfused) bucket whose result does not depend on
-// the item and whose inputs are gate tensors or results of early buckets
-// depends on nothing the batch computes otherwise. These run first, before
-// every other step, one launch per level (level = 1 + the highest level among
-// the producers of its inputs). Their results are given a lifetime from the
-// start of the batch, so no other tensor shares their memory meanwhile.
-std::vector<int> hoist_levels(const Program& prog, const std::vector<char>& dep) {
+// Early buckets: a single (unfused) bucket whose inputs are gate tensors or
+// results of early buckets depends on nothing the batch computes otherwise.
+// These run first, before every other step, one launch per level (level = 1 +
+// the highest level among the producers of its inputs), when the result with
+// its item bits has at most HOIST_MAX_BITS index bits. Their results are given
+// a lifetime from the start of the batch, so no other tensor shares their
+// memory meanwhile.
+std::vector<int> hoist_levels(const Program& prog, const std::vector<char>& dep, int item_bits) {
   const int nb = (int)prog.buckets.size();
   std::vector<int> lv(nb, 0);
   for (int b = 0; b < nb; ++b) {
     if (!prog.group_of.empty() && prog.group_of[b] >= 0) continue;
     const PBucket& B = prog.buckets[b];
-    if (dep[B.output] || prog.tensors[B.output].rank() > HOIST_MAX_BITS || B.k > KMAX || B.k < 1) continue;
+    if (prog.tensors[B.output].rank() + (dep[B.output] ? item_bits : 0) > HOIST_MAX_BITS || B.k > KMAX || B.k < 1)
+      continue;
     int l = 0;
     bool ok = true;
     for (int t : B.inputs) {
@@ -1215,7 +1251,7 @@ Layout make_layout(const tnq_plan& P, int mode, int B) {
   L.off.assign(T, 0);
   L.dep.assign(T, 0);
   for (int t = 0; t < T; ++t) L.dep[t] = tensor_dep(prog.tensors[t], mode);
-  L.hoist = hoist_levels(prog, L.dep);
+  L.hoist = hoist_levels(prog, L.dep, L.item_bits);
   const Liveness LV = layout_liveness(prog, L.hoist);
   const std::vector<int>& lo = LV.lo;
   const std::vector<int>& hi = LV.hi;
@@ -1806,9 +1842,12 @@ static bool build_steps(const tnq_plan& P, const Layout& L, ExecConfig& C) {
       h.out_meta = k.out_meta;
       h.blk0 = blocks;
       h.nvar = k.n_var;
+      h.obits = k.out_bits;
+      h.out_dep = k.G > k.out_bits;
       for (int j = 0; j < h.nin; ++j) {
         h.in[j] = (long long)reinterpret_cast<size_t>(k.in[j]);
         h.in_meta[j] = k.in_meta[j];
+        h.in_dep[j] = k.in_dep[j];
         for (int b = 0; b < k.G; ++b) h.stride[j][b] = k.stride[j][b];
       }
       blocks += (int)(((1ll << k.G) + 255) >> 8);
@@ -1836,9 +1875,7 @@ static std::string validate_config(const tnq_plan& P, int mode, int B) {
   for (size_t i = 0; i < C.steps.size(); ++i) {  // early buckets: item-invariant, inputs ready before their level
     if (!C.step_hoist[i]) continue;
     const KParams& k = C.kp[C.steps[i].second];
-    if (k.G != k.out_bits || k.G > HOIST_MAX_BITS) return "early bucket shape";
-    for (int j = 0; j < C.kshape[C.steps[i].second].first; ++j)
-      if (k.in_dep[j]) return "early bucket reads an item-dependent tensor";
+    if (k.G > HOIST_MAX_BITS || (k.G != k.out_bits && k.G != k.out_bits + L.item_bits)) return "early bucket shape";
   }
   for (size_t bi = 0; bi < prog.buckets.size(); ++bi) {
     if (!L.hoist[bi]) continue;
@@ -2834,14 +2871,18 @@ tnq_status tnq_plan_keep_chains(tnq_plan* plan, const int32_t* last_bucket, size
   return TNQ_OK;
 }
 
-// Internal: kernel launches of one batch of configuration (mode, batch).
-int tnq_internal_launches_per_batch(const tnq_plan* plan) {
+// Internal: kernel launches of one batch of configuration (mode, batch): one
+// per remaining bucket or chain step (three per GEMM chain), one per level of
+// early buckets, and the leaf, scalar, final and slice-sum kernels.
+int tnq_internal_launches_per_batch(const tnq_plan* plan, int mode, uint32_t batch) {
   if (!plan) return 0;
   int n = 0;
   const auto& prog = plan->prog;
   std::vector<char> dep(prog.tensors.size());
-  for (size_t t = 0; t < dep.size(); ++t) dep[t] = tensor_dep(prog.tensors[t], 0);
-  const std::vector<int> hoist = hoist_levels(prog, dep);  // single-bitstring calls
+  for (size_t t = 0; t < dep.size(); ++t) dep[t] = tensor_dep(prog.tensors[t], mode);
+  int item_bits = 0;
+  while ((1u << item_bits) < batch) ++item_bits;
+  const std::vector<int> hoist = hoist_levels(prog, dep, item_bits);
   int levels = 0;
   for (size_t b = 0; b < prog.buckets.size(); ++b) {
     levels = std::max(levels, hoist[b]);
@@ -2967,18 +3008,43 @@ tnq_status tnq_amplitudes_batch(const tnq_plan* const* plans, size_t n_plans, co
   std::vector<Job> jobs;
   int n_lanes = 0;
   size_t region = 0;
-  for (int K = std::min(N_LANES, n_distinct); K >= 1; --K) {
-    // the staging area for headers and bits is sized after the jobs are known;
-    // keep an eighth of the workspace for it and the accumulators
-    if (ws_bytes < tail_bytes + 4096) break;
-    const size_t usable = (ws_bytes - tail_bytes) / 8 * 7;
-    region = usable / K / 256 * 256;
-    bool fits = true;
-    for (size_t i = 0; i < n_plans && fits; ++i)
-      if (lane_of[i] >= 0 && pick_batch(*plans[i], 1, region, 1) == 0) fits = false;
-    if (fits) {
-      n_lanes = K;
-      break;
+  // batch size of plan i in a lane of `reg` bytes, and the staging bytes
+  // (headers and bitstring words of every batch) that choice needs
+  auto batch_of = [&](size_t i, size_t reg) {
+    const uint64_t n_items = (uint64_t)(bits_offset[i + 1] - bits_offset[i]) << plans[i]->mu.size();
+    uint64_t cap = 1;
+    while (cap < n_items && cap < (1ull << MAX_ITEM_BITS)) cap <<= 1;
+    return pick_batch(*plans[i], 1, reg, cap);
+  };
+  auto staging = [&](size_t reg) {
+    size_t nh = 0, nw = 0;
+    for (size_t i = 0; i < n_plans; ++i) {
+      if (lane_of[i] < 0) continue;
+      const int B = batch_of(i, reg);
+      const uint64_t n_items = (uint64_t)(bits_offset[i + 1] - bits_offset[i]) << plans[i]->mu.size();
+      const uint64_t nbat = (n_items + B - 1) / B;
+      nh += nbat;
+      nw += nbat * (size_t)((plans[i]->net.n_qubits + 31) / 32) * (size_t)(B + 1);
+    }
+    return align_up(nh * sizeof(BatchHdr), 256) + align_up(nw * 4 + 4, 256);
+  };
+  for (int K = std::min(N_LANES, n_distinct); K >= 1 && !n_lanes; --K) {
+    // the lanes take what the staging area and the accumulators leave; the
+    // staging area depends on the batch sizes, which depend on the lane size
+    size_t stage = 0;
+    for (int iter = 0; iter < 8; ++iter) {
+      if (ws_bytes < tail_bytes + stage + 256 * (size_t)K) break;
+      region = (ws_bytes - tail_bytes - stage) / K / 256 * 256;
+      bool fits = true;
+      for (size_t i = 0; i < n_plans && fits; ++i)
+        if (lane_of[i] >= 0 && batch_of(i, region) == 0) fits = false;
+      if (!fits) break;
+      const size_t need = staging(region);
+      if ((size_t)K * region + need + tail_bytes <= ws_bytes) {
+        n_lanes = K;
+        break;
+      }
+      stage = need;
     }
   }
   if (n_lanes == 0) { set_error("workspace too small for one item of some plan"); return TNQ_ENOMEM; }

@@ -279,9 +279,9 @@ def _stream_ptr(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
-def default_workspace(plans, want_items: int, fraction: float = 0.5):
-    """A device workspace (torch uint8) for the largest power-of-two batch of at
-    most want_items that fits every plan in `fraction` of the free device memory."""
+def default_workspace_bytes(plans, want_items: int, fraction: float = 0.5) -> int:
+    """Bytes of workspace for the largest power-of-two batch of at most
+    want_items that fits every plan in `fraction` of the free device memory."""
     import torch
 
     free, _ = torch.cuda.mem_get_info()
@@ -289,8 +289,14 @@ def default_workspace(plans, want_items: int, fraction: float = 0.5):
     batch = 1
     while batch * 2 <= max(want_items, 1) and max(p.workspace_bytes(batch * 2) for p in plans) <= budget:
         batch *= 2
-    need = max(p.workspace_bytes(batch) for p in plans) if plans else 256
-    return torch.empty(need, dtype=torch.uint8, device="cuda")
+    return max(p.workspace_bytes(batch) for p in plans) if plans else 256
+
+
+def default_workspace(plans, want_items: int, fraction: float = 0.5):
+    """A device workspace (torch uint8) of default_workspace_bytes."""
+    import torch
+
+    return torch.empty(default_workspace_bytes(plans, want_items, fraction), dtype=torch.uint8, device="cuda")
 
 
 def contract_sliced(plan: Plan, bits=None, slice_begin: int = 0, slice_end: int | None = None, workspace=None,
@@ -354,8 +360,13 @@ def amplitudes_batch(plans, bitstrings, workspace=None, stream=None):
     offsets = np.array(offs, dtype=np.uint64).astype(np.uintp)
     handles = (ctypes.c_void_p * max(len(plans), 1))(*[p.handle for p in plans])
     if workspace is None:
+        import torch
+
         want = max([(1 << p.info()["p"]) * len(b) for p, b in zip(plans, bitstrings)] or [1])
-        workspace = default_workspace(plans, want)
+        lanes = min(4, len({id(p) for p, b in zip(plans, bitstrings) if len(b)}) or 1)
+        one = default_workspace_bytes(plans, want, fraction=0.5 / lanes)
+        # one share per concurrent lane, plus the call's staging area and accumulators
+        workspace = torch.empty(lanes * one + 32 * offs[-1] + (1 << 20), dtype=torch.uint8, device="cuda")
     out = np.zeros(2 * max(offs[-1], 1), np.float64)
     _check(lib().tnq_amplitudes_batch(handles, len(plans), _ptr(allbits, ctypes.c_uint8),
                                       offsets.ctypes.data_as(_P(ctypes.c_size_t)),

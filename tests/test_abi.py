@@ -246,10 +246,11 @@ def test_concurrent_step_schedule_never_reads_a_clobbered_tensor(tnq_lib):
 
 
 def test_early_buckets_of_the_7x7_plan(tnq_lib):
-    """Host-only: the item-invariant buckets that only read gate tensors and each
-    other run first, one launch per level; the configuration stays in bounds
-    (their results keep their memory from the start of the batch) and the
-    batch issues fewer launches than it has steps."""
+    """Host-only: the buckets that only read gate tensors and each other
+    (item-invariant or per item) run first, one launch per level; the
+    configuration stays in bounds (their results keep their memory from the
+    start of the batch) and the batch issues far fewer launches than it has
+    steps."""
     L = tnq_lib.lib()
     f = L.tnq_internal_validate
     f.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32, ctypes.c_char_p, ctypes.c_size_t]
@@ -257,7 +258,7 @@ def test_early_buckets_of_the_7x7_plan(tnq_lib):
     P = ctypes.POINTER
     k.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32, P(ctypes.c_int32), P(ctypes.c_int32), ctypes.c_int,
                   P(ctypes.c_int32)]
-    L.tnq_internal_launches_per_batch.argtypes = [ctypes.c_void_p]
+    L.tnq_internal_launches_per_batch.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32]
     plan = tnq_lib.Plan(I.random_grid_circuit(7, 7, 32, 0), max_bag_log2=28, max_p=40, precision=1,
                         reorder_every=1, order_trials=4)
     buf = ctypes.create_string_buffer(256)
@@ -269,8 +270,9 @@ def test_early_buckets_of_the_7x7_plan(tnq_lib):
     assert k(plan.handle, 0, 32, kind, None, 4096, ctypes.byref(n)) == 0
     steps = [kind[i] for i in range(n.value)]
     per_step = len(steps) + 2 * steps.count(2) + 4  # GEMM steps launch two packs and the MMA
-    launches = L.tnq_internal_launches_per_batch(plan.handle)
-    assert 0 < launches < per_step - 100, (launches, per_step)
+    launches = L.tnq_internal_launches_per_batch(plan.handle, 0, 32)
+    assert 0 < launches < per_step - 150, (launches, per_step)
+    assert launches < 80, launches
 
 
 def test_parity_plans_cover_every_register_tail(tnq_lib):
