@@ -213,7 +213,9 @@ def launch_roofline(L, plan, bits, ws, B, n_sl, stream, peaks, info):
     if big1 and t_big1 > 0:
         gbs = sum(by[i] for i in big1) / (t_big1 / 1e3) / 1e9
         k_bucket["launches_ge_64MB"] = {"launches": len(big1), "achieved": gbs, "frac": gbs / hbm,
-                                        "share_of_k_bucket_time": t_big1 / t_one}
+                                        "share_of_k_bucket_time": t_big1 / t_one,
+                                        "each": [{"bag": bag[i], "MB": round(by[i] / 1e6, 1), "ms": round(ms[i], 4),
+                                                  "gbs": round(by[i] / (ms[i] / 1e3) / 1e9, 1)} for i in big1]}
     k_group = {"kernel": "k_group", "bound": "alu", "achieved": grp_tfs, "peak": fp32, "unit": "TFLOP/s",
                "frac": grp_tfs / fp32 if grp_tfs else None, "launches": len(grp), "time_share": t_grp / tot,
                "flops_per_launch": sum(fl[i] for i in grp) / max(len(grp), 1),
