@@ -271,8 +271,9 @@ tnq_status tnq_plan_keep_chains(tnq_plan* plan, const int32_t* last_bucket, size
  *  tile_low: a fused chain keeps its tile_low earliest output variables local
  *    and picks its other local variables to minimise the operand entries a
  *    tile reads (64: the earliest output variables only).
+ * A new plan has the cut-over of opts (2^4 by default) and tile_low 64;
  * tnq_plan_autotune measures cut-overs 2^3..2^6 and tile_low 3 / 64 and keeps
- * the fastest. tnq_plan_set_tuning recompiles the program with the given
+ * another tuning only when it is at least 3% faster than the plan's own. tnq_plan_set_tuning recompiles the program with the given
  * values (every candidate chain fused; apply a stored selection afterwards
  * with tnq_plan_keep_chains) and drops the plan's device configurations: call
  * it before the plan is shared. TNQ_EINVAL for gemm_min_k_log2 outside

@@ -167,7 +167,7 @@ static void plan_network(tnq_plan* P, const tnq_plan_opts& o) {
   P->order = std::move(tr[best].order);
   P->tau = tr[best].tau;
   P->tau_full = treewidth_of_order(P->graph, P->order_full);
-  rebuild_program(P, o.gemm_min_k_log2 > 0 ? o.gemm_min_k_log2 : 4, 3);
+  rebuild_program(P, o.gemm_min_k_log2 > 0 ? o.gemm_min_k_log2 : 4, 64);
   P->amp_scale_log2 = -0.5 * P->net.n_sqrt2 + (double)P->net.leaf_exp;
 }
 

@@ -143,7 +143,7 @@ struct Program {
   double flops_per_slice = 0, bytes_per_slice = 0;
   double bytes_unfused = 0;  // bytes_per_slice with no fused group
   int max_bag = 0;
-  int tile_low = 3;          // output variables a fused chain always keeps local (fuse_chains' tile shape)
+  int tile_low = 64;         // output variables a fused chain always keeps local (fuse_chains' tile shape)
 };
 
 // GEMM pass: chains whose product is a batched contraction of two tensors of

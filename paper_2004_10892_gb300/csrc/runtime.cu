@@ -2806,7 +2806,7 @@ tnq_status tnq_plan_autotune(tnq_plan* plan, const uint8_t* bits, void* workspac
   // tuning variants: the GEMM cut-over (split precision only) and the fused
   // chains' tile shape; each is compiled, its chains selected and the result
   // timed. The plan's own tuning is tried first and kept unless another
-  // variant is at least 2% faster (so that timing noise does not flip the
+  // variant is at least 3% faster (so that timing noise does not flip the
   // choice between runs); the fastest such variant wins.
   std::vector<std::pair<int, int>> variants{{plan->gemm_min_k_log2, plan->prog.tile_low}};
   const std::vector<int> cuts = plan->opts.precision == TNQ_PREC_C64 ? std::vector<int>{plan->gemm_min_k_log2}
@@ -2826,7 +2826,7 @@ tnq_status tnq_plan_autotune(tnq_plan* plan, const uint8_t* bits, void* workspac
     }
     float ms = 0.f;
     if ((st = select_chains(plan, bits, workspace, ws_bytes, cap, stream, &ms)) != TNQ_OK) return st;
-    if (best < 0 || ms < (best == 0 ? 0.98f : 1.f) * best_ms) {
+    if (best < 0 || ms < (best == 0 ? 0.97f : 1.f) * best_ms) {
       best = (int)v;
       best_ms = ms;
       best_groups = plan->prog.groups;

@@ -306,9 +306,9 @@ def test_tuning_roundtrip_and_validation(tnq_lib):
     every launch of the recompiled plan stays in bounds; bad values are refused."""
     circ = I.random_grid_circuit(6, 6, 24, 5)
     plan = tnq_lib.Plan(circ, max_bag_log2=18, max_p=20, reorder_every=1, precision=1, gemm_min_k_log2=4)
-    assert plan.tuning() == (4, 3)
+    assert plan.tuning() == (4, 64)
     n_gemm = {}
-    for k, low in ((3, 64), (6, 0), (4, 3)):
+    for k, low in ((3, 3), (6, 0), (4, 64)):
         plan.set_tuning(k, low)
         assert plan.tuning() == (k, low)
         n_gemm[k] = plan.info()["n_gemm_buckets"]
