@@ -14,6 +14,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -81,13 +82,14 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
 // Shared-memory matrix descriptor: no swizzle, K-major core matrices of
-// 8 rows x 16 bytes, 128 bytes apart along K (leading) and 1024 bytes apart
-// along rows (stride); descriptor version 1.
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+// 8 rows x 16 bytes, 128 bytes apart along K (leading) and `sbo` bytes apart
+// along rows (stride: 1024 for tiles with 128 bytes of K per row, 512 for 64);
+// descriptor version 1.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t sbo = 1024u) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
   d |= (uint64_t)((128u >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((1024u >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
   d |= (uint64_t)1 << 46;
   return d;
 }
@@ -148,6 +150,133 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 
 __device__ __forceinline__ void epi_sync() {  // the four epilogue warps
   asm volatile("bar.sync 1, 128;" ::: "memory");
+}
+
+// Power-of-two scale bringing a tensor with largest |re|,|im| bits `mbits`
+// into [0.5, 1) (same rule as the bucket kernels).
+__device__ __forceinline__ float pack_scale(unsigned mbits, int* mexp) {
+  if (mbits == 0u) {
+    *mexp = 0;
+    return 1.f;
+  }
+  int ex = (int)((mbits >> 23) & 0xffu);
+  if (ex == 0) ex = 1;
+  int m = ex - 126;
+  if (m > 126) m = 126;
+  *mexp = m;
+  return __int_as_float((127 - m) << 23);
+}
+
+// 16 bytes of hi and lo parts of CH consecutive values (CH = 8 BF16 or 4 TF32).
+template <int KIND, int CH>
+__device__ __forceinline__ void split16(const float* x, uint4* hi, uint4* lo) {
+  uint32_t h[4], l[4];
+  if (KIND == GEMM_BF16) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const __nv_bfloat16 h0 = __float2bfloat16_rn(x[2 * q]), h1 = __float2bfloat16_rn(x[2 * q + 1]);
+      const __nv_bfloat16 l0 = __float2bfloat16_rn(x[2 * q] - __bfloat162float(h0));
+      const __nv_bfloat16 l1 = __float2bfloat16_rn(x[2 * q + 1] - __bfloat162float(h1));
+      h[q] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+      l[q] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h[q]) : "f"(x[q]));
+      const float rest = x[q] - __uint_as_float(h[q]);
+      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l[q]) : "f"(rest));
+    }
+  }
+  *hi = make_uint4(h[0], h[1], h[2], h[3]);
+  *lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// Epilogue warps (four, one per TMEM lane quarter): for every tile of the
+// block, wait for its accumulator buffer, read it with tcgen05.ld and write
+// the tile (plain FP32 rows, or complex pairs scattered into the bucket's
+// output with the tile's maximum), then release the buffer.
+__device__ __forceinline__ void epilogue_warps(const GemmArgs& a, uint32_t tmem_base, uint64_t* tfull_bar,
+                                               uint64_t* tempty_bar, volatile int* s_fail, long long (*s_yoff)[64],
+                                               int* s_epi_stop, int e, int quarter, int lane, long long n_tiles) {
+  const int r_in = quarter * 32 + lane;
+  long long i = 0;
+  for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++i) {
+    const int buf = (int)(i & 1);
+    const long long j = i >> 1;
+    const int ct = (int)(tile % a.row_tiles_b);
+    const int rt = (int)((tile / a.row_tiles_b) % a.row_tiles_a);
+    const long long b = tile / ((long long)a.row_tiles_b * a.row_tiles_a);
+    const GemmEpilogue& ep = a.ep;
+    if (!a.out_c && e < 64) {  // column offsets of this tile (complex column n = ct * 64 + e)
+      const int n = ct * 64 + e;
+      long long off = -1;
+      if (n < (1 << ep.ny)) {
+        off = 0;
+        for (int q = 0; q < ep.ny; ++q)
+          if ((n >> q) & 1) off += ep.y[q];
+      }
+      s_yoff[buf][e] = off;
+    }
+    // the four warps take the same decision: a failed wait is published in
+    // this tile parity's flag before the barrier and read after it
+    if (!mbar_wait(&tfull_bar[buf], (uint32_t)(j & 1)) || *s_fail) s_epi_stop[buf] = 1;
+    epi_sync();
+    if (s_epi_stop[buf]) {
+      *s_fail = 1;
+      atomicExch(a.status, 2);
+      break;
+    }
+    tc_fence_after();
+    const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)buf * 128u;
+    if (a.out_c) {
+      float* crow = a.out_c + ((long long)b * a.row_tiles_a * GT_ROWS + rt * GT_ROWS + r_in) * a.ldc +
+                    (long long)ct * 128;
+#pragma unroll 1
+      for (int chunk = 0; chunk < 4; ++chunk) {
+        float v[32];
+        tmem_ld32(taddr + (uint32_t)(chunk * 32), v);
+#pragma unroll
+        for (int q = 0; q < 32; q += 4)
+          *reinterpret_cast<float4*>(crow + chunk * 32 + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+      }
+    } else {
+      // row = X assignment m, column pair (2n, 2n+1) = (Re, Im) of Y assignment n
+      const int m = rt * GT_ROWS + r_in;
+      const long long item = b >> ep.ns, sidx = b & ((1ll << ep.ns) - 1);
+      const bool row_ok = m < (1 << ep.nx);
+      long long rbase = ep.dep ? item * ep.istride : 0ll;
+      for (int q = 0; q < ep.ns; ++q)
+        if ((sidx >> q) & 1) rbase += ep.s[q];
+      for (int q = 0; q < ep.nx; ++q)
+        if ((m >> q) & 1) rbase += ep.x[q];
+      float tmax = 0.f;
+#pragma unroll 1
+      for (int chunk = 0; chunk < 4; ++chunk) {
+        float v[32];
+        tmem_ld32(taddr + (uint32_t)(chunk * 32), v);  // warp-collective: every lane loads
+        if (row_ok) {
+#pragma unroll
+          for (int q = 0; q < 32; q += 2) {
+            const long long yo = s_yoff[buf][chunk * 16 + (q >> 1)];
+            if (yo >= 0) {
+              ep.out[rbase + yo] = make_float2(v[q], v[q + 1]);
+              tmax = fmaxf(tmax, fmaxf(fabsf(v[q]), fabsf(v[q + 1])));
+            }
+          }
+        }
+      }
+      for (int off = 16; off > 0; off >>= 1) tmax = fmaxf(tmax, __shfl_xor_sync(0xffffffffu, tmax, off));
+      if (lane == 0 && tmax > 0.f) {
+        unsigned* p = &ep.meta_m[(long long)ep.meta * ep.B + (ep.dep ? item : 0ll)];
+        const unsigned bits = __float_as_uint(tmax);
+        if (bits > *reinterpret_cast<volatile unsigned*>(p)) atomicMax(p, bits);
+      }
+    }
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&tempty_bar[buf]);
+  }
 }
 
 // Persistent, warp-specialised GEMM. Each block loops over output tiles
@@ -283,91 +412,284 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_gemm_tc(const GemmArgs a) {
       mbar_wait(&drain_bar, 0);
     }
   } else if (warp >= 2) {
-    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 = tile rows
-    const int quarter = warp & 3;
-    const int r_in = quarter * 32 + lane;
-    const int e = tid - 64;  // 0..127
-    long long i = 0;
-    for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++i) {
-      const int buf = (int)(i & 1);
-      const long long j = i >> 1;
-      const int ct = (int)(tile % a.row_tiles_b);
-      const int rt = (int)((tile / a.row_tiles_b) % a.row_tiles_a);
-      const long long b = tile / ((long long)a.row_tiles_b * a.row_tiles_a);
-      const GemmEpilogue& ep = a.ep;
-      if (!a.out_c && e < 64) {  // column offsets of this tile (complex column n = ct * 64 + e)
-        const int n = ct * 64 + e;
-        long long off = -1;
-        if (n < (1 << ep.ny)) {
-          off = 0;
-          for (int q = 0; q < ep.ny; ++q)
-            if ((n >> q) & 1) off += ep.y[q];
-        }
-        s_yoff[buf][e] = off;
-      }
-      // the four warps take the same decision: a failed wait is published in
-      // this tile parity's flag before the barrier and read after it
-      if (!mbar_wait(&tfull_bar[buf], (uint32_t)(j & 1)) || s_fail) s_epi_stop[buf] = 1;
-      epi_sync();
-      if (s_epi_stop[buf]) {
-        s_fail = 1;
-        atomicExch(a.status, 2);
-        break;
-      }
-      tc_fence_after();
-      const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)buf * 128u;
-      if (a.out_c) {
-        float* crow = a.out_c + ((long long)b * a.row_tiles_a * GT_ROWS + rt * GT_ROWS + r_in) * a.ldc +
-                      (long long)ct * 128;
-#pragma unroll 1
-        for (int chunk = 0; chunk < 4; ++chunk) {
-          float v[32];
-          tmem_ld32(taddr + (uint32_t)(chunk * 32), v);
-#pragma unroll
-          for (int q = 0; q < 32; q += 4)
-            *reinterpret_cast<float4*>(crow + chunk * 32 + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
-        }
-      } else {
-        // row = X assignment m, column pair (2n, 2n+1) = (Re, Im) of Y assignment n
-        const int m = rt * GT_ROWS + r_in;
-        const long long item = b >> ep.ns, sidx = b & ((1ll << ep.ns) - 1);
-        const bool row_ok = m < (1 << ep.nx);
-        long long rbase = ep.dep ? item * ep.istride : 0ll;
-        for (int q = 0; q < ep.ns; ++q)
-          if ((sidx >> q) & 1) rbase += ep.s[q];
-        for (int q = 0; q < ep.nx; ++q)
-          if ((m >> q) & 1) rbase += ep.x[q];
-        float tmax = 0.f;
-#pragma unroll 1
-        for (int chunk = 0; chunk < 4; ++chunk) {
-          float v[32];
-          tmem_ld32(taddr + (uint32_t)(chunk * 32), v);  // warp-collective: every lane loads
-          if (row_ok) {
-#pragma unroll
-            for (int q = 0; q < 32; q += 2) {
-              const long long yo = s_yoff[buf][chunk * 16 + (q >> 1)];
-              if (yo >= 0) {
-                ep.out[rbase + yo] = make_float2(v[q], v[q + 1]);
-                tmax = fmaxf(tmax, fmaxf(fabsf(v[q]), fabsf(v[q + 1])));
-              }
-            }
-          }
-        }
-        for (int off = 16; off > 0; off >>= 1) tmax = fmaxf(tmax, __shfl_xor_sync(0xffffffffu, tmax, off));
-        if (lane == 0 && tmax > 0.f) {
-          unsigned* p = &ep.meta_m[(long long)ep.meta * ep.B + (ep.dep ? item : 0ll)];
-          const unsigned bits = __float_as_uint(tmax);
-          if (bits > *reinterpret_cast<volatile unsigned*>(p)) atomicMax(p, bits);
-        }
-      }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&tempty_bar[buf]);
-    }
+    epilogue_warps(a, tmem_base, tfull_bar, tempty_bar, &s_fail, s_yoff, s_epi_stop, tid - 64, warp & 3, lane, n_tiles);
   }
   tc_fence_before();
   __syncthreads();
   if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+// Fused-A form (BF16): A is read from its complex64 tensor by the kernel
+// itself. Per block: warps 0-7 (256 producer threads) write, for every K step
+// of 32 complex values, the hi and lo half tiles of A's real parts and of its
+// imaginary parts (one read of the complex values gives both); warp 8 (one
+// thread) copies B's four packed half tiles of the step (real-part and
+// imaginary-part positions of K, hi and lo); warp 9 (one thread) issues the
+// 12 MMAs of the step (per part: 2 K sub-steps x 3 split-precision passes);
+// warps 10-13 are the epilogue. Stage layout: A re hi, re lo, im hi, im lo,
+// B re hi, re lo, im hi, im lo (8 KB each). Waits bounded as in k_gemm_tc.
+constexpr int GEMM_THREADS_FA = 448;
+constexpr int FA_PRODUCERS = 256;
+
+__global__ void __launch_bounds__(GEMM_THREADS_FA, 1) k_gemm_tc_fa(const GemmArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ uint64_t full_bar[N_STAGES], empty_bar[N_STAGES], tfull_bar[2], tempty_bar[2], drain_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int s_fail;
+  __shared__ long long s_yoff[2][64];
+  __shared__ int s_epi_stop[2];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  const long long n_tiles = (long long)a.batch * a.row_tiles_a * a.row_tiles_b;
+  constexpr int HB = GT_TILE_BYTES_H;
+  if (tid == 0) {
+    for (int s = 0; s < N_STAGES; ++s) {
+      mbar_init(&full_bar[s], 1 + FA_PRODUCERS);  // the B copy thread and every producer thread
+      mbar_init(&empty_bar[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull_bar[b], 1);
+      mbar_init(&tempty_bar[b], 4);
+    }
+    mbar_init(&drain_bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    s_fail = 0;
+    s_epi_stop[0] = s_epi_stop[1] = 0;
+  }
+  if (warp == 9) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = tmem_slot;
+
+  if (warp < 8) {
+    // ---- producers. Thread t handles rows 8 (t >> 5) + (t & 7) and that + 64
+    // and the 8-value K chunk (t >> 3) & 3 of every step: eight consecutive
+    // threads fill one 128-byte core matrix with one 16-byte store per tile.
+    // The loads of step g + 1 are issued before step g is converted and
+    // stored, so each thread keeps 128 bytes in flight while it works.
+    const GemmOperand& o = a.fa;
+    const int r_lo = tid & 7, c = (tid >> 3) & 3, rg = tid >> 5;
+    long long kc_off = 0;  // offset of this thread's K chunk within a 32-value step
+    for (int q = 3; q < 5 && q < a.fa_nk; ++q)
+      if (((8 * c) >> q) & 1) kc_off += o.kstride[q];
+    // per tile: the offsets of this thread's two rows (-1 past the X range) and the operand's scale
+    auto tile_setup = [&](long long tile, long long* roff, float* f) {
+      const int rt = (int)((tile / a.row_tiles_b) % a.row_tiles_a);
+      const long long b = tile / ((long long)a.row_tiles_b * a.row_tiles_a);
+      const long long item = b >> a.fa_ns, sidx = b & ((1ll << a.fa_ns) - 1);
+      *f = 1.f;
+      if (o.meta >= 0) {
+        int m;
+        *f = pack_scale(a.fa_meta_m[(long long)o.meta * a.fa_B + (o.dep ? item : 0ll)], &m);
+      }
+      long long bb = o.dep ? item * o.istride : 0ll;
+      for (int q = 0; q < a.fa_ns; ++q)
+        if ((sidx >> q) & 1) bb += o.sstride[q];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int m = rt * GT_ROWS + 8 * rg + 64 * h + r_lo;
+        long long v = -1;
+        if (m < (1 << a.fa_nx)) {
+          v = bb;
+          for (int q = 0; q < a.fa_nx; ++q)
+            if ((m >> q) & 1) v += o.rstride[q];
+        }
+        roff[h] = v;
+      }
+    };
+    auto load_step = [&](const long long* roff, int q, float4* v) {
+      const int k0 = 32 * q;
+      long long koff = kc_off;
+      for (int t = 5; t < a.fa_nk; ++t)
+        if ((k0 >> t) & 1) koff += o.kstride[t];
+      const bool k_ok = k0 + 8 * c < (1 << a.fa_nk);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const bool ld = roff[h] >= 0 && k_ok;
+        const float4* src = reinterpret_cast<const float4*>(o.ptr + (ld ? roff[h] + koff : 0ll));
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[4 * h + u] = ld ? __ldg(src + u) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    };
+    const long long my_tiles = blockIdx.x < n_tiles ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const long long n_steps = my_tiles * a.k_tiles;
+    long long lt = blockIdx.x;  // load cursor: tile and K step of the next load
+    int lq = 0;
+    long long lroff[2] = {-1, -1};
+    float lf = 1.f;
+    float4 cur[8];
+    if (n_steps > 0) {
+      tile_setup(lt, lroff, &lf);
+      load_step(lroff, 0, cur);
+    }
+    float fcur = lf;
+    int fills[N_STAGES] = {};
+    bool ok = true;
+    for (long long g = 0; g < n_steps; ++g) {
+      const int s = (int)(g % N_STAGES);
+      float4 nxt[8];
+      float fnxt = fcur;
+      if (g + 1 < n_steps) {
+        if (++lq == a.k_tiles) {
+          lq = 0;
+          lt += gridDim.x;
+          tile_setup(lt, lroff, &lf);
+        }
+        fnxt = lf;
+        load_step(lroff, lq, nxt);
+      }
+      // every producer thread waits for the MMAs that read stage s to finish
+      // before it overwrites the stage
+      const bool w_ok = fills[s] == 0 || mbar_wait(&empty_bar[s], (fills[s] - 1) & 1);
+      if (!__all_sync(0xffffffffu, w_ok) || s_fail) {
+        ok = false;
+        break;
+      }
+      const uint32_t st = base + (uint32_t)s * STAGE_BYTES;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int r = 8 * rg + 64 * h + r_lo;
+        float re[8], im[8];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float4 v = cur[4 * h + u];
+          re[2 * u] = v.x * fcur;
+          im[2 * u] = v.y * fcur;
+          re[2 * u + 1] = v.z * fcur;
+          im[2 * u + 1] = v.w * fcur;
+        }
+        const uint32_t off = gt_offset_h(r, 8 * c, 2);
+        uint4 hv, lv;
+        split16<GEMM_BF16, 8>(re, &hv, &lv);
+        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(st + off), "r"(hv.x), "r"(hv.y), "r"(hv.z),
+                     "r"(hv.w)
+                     : "memory");
+        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(st + HB + off), "r"(lv.x), "r"(lv.y),
+                     "r"(lv.z), "r"(lv.w)
+                     : "memory");
+        split16<GEMM_BF16, 8>(im, &hv, &lv);
+        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(st + 2 * HB + off), "r"(hv.x), "r"(hv.y),
+                     "r"(hv.z), "r"(hv.w)
+                     : "memory");
+        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(st + 3 * HB + off), "r"(lv.x), "r"(lv.y),
+                     "r"(lv.z), "r"(lv.w)
+                     : "memory");
+      }
+      // the tensor cores read shared memory through the async proxy: every
+      // thread orders its own stores before its arrival
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(&full_bar[s]);
+      ++fills[s];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) cur[u] = nxt[u];
+      fcur = fnxt;
+    }
+    if (!ok) {
+      s_fail = 1;
+      if (lane == 0) atomicExch(a.status, 1);
+    }
+  } else if (warp == 8 && lane == 0) {
+    // ---- B copies: the real-part and imaginary-part half tiles of every step
+    int fills[N_STAGES] = {};
+    long long g = 0;
+    bool ok = true;
+    const int kth = 2 * a.fa_kpad / 32;  // B half tiles along K per (batch, column tile)
+    for (long long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+      const int ct = (int)(tile % a.row_tiles_b);
+      const long long b = tile / ((long long)a.row_tiles_b * a.row_tiles_a);
+      const char* B_hi = (const char*)a.b_hi + (size_t)(b * a.row_tiles_b + ct) * kth * HB;
+      const char* B_lo = (const char*)a.b_lo + (size_t)(b * a.row_tiles_b + ct) * kth * HB;
+      for (int q = 0; q < a.k_tiles; ++q, ++g) {
+        const int s = (int)(g % N_STAGES);
+        if (fills[s] > 0 && !mbar_wait(&empty_bar[s], (fills[s] - 1) & 1)) {
+          ok = false;
+          break;
+        }
+        if (s_fail) {
+          ok = false;
+          break;
+        }
+        const uint32_t st = base + (uint32_t)s * STAGE_BYTES;
+        const size_t kre = (size_t)q, kim = (size_t)(a.fa_kpad / 32 + q);  // half tiles of real-K positions
+        mbar_expect_tx(&full_bar[s], 4 * HB);
+        bulk_g2s(st + 4 * HB, B_hi + kre * HB, HB, &full_bar[s]);
+        bulk_g2s(st + 5 * HB, B_lo + kre * HB, HB, &full_bar[s]);
+        bulk_g2s(st + 6 * HB, B_hi + kim * HB, HB, &full_bar[s]);
+        bulk_g2s(st + 7 * HB, B_lo + kim * HB, HB, &full_bar[s]);
+        ++fills[s];
+      }
+    }
+    if (!ok) {
+      s_fail = 1;
+      atomicExch(a.status, 1);
+    }
+    for (int s = 0; s < N_STAGES; ++s)
+      if (fills[s] > 0) mbar_wait(&full_bar[s], (fills[s] - 1) & 1);
+  } else if (warp == 9 && lane == 0) {
+    // ---- MMA issuer
+    long long g = 0;
+    bool ok = true, issued = false;
+    long long i = 0;
+    for (long long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++i) {
+      const int buf = (int)(i & 1);
+      const long long j = i >> 1;
+      if (j >= 1 && !mbar_wait(&tempty_bar[buf], (uint32_t)((j - 1) & 1))) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t tmem_d = tmem_base + (uint32_t)buf * 128u;
+      for (int q = 0; q < a.k_tiles; ++q, ++g) {
+        const int s = (int)(g % N_STAGES);
+        const long long n = g / N_STAGES;
+        if (!mbar_wait(&full_bar[s], (uint32_t)(n & 1)) || s_fail) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t st = base + (uint32_t)s * STAGE_BYTES;
+#pragma unroll
+        for (int part = 0; part < 2; ++part) {
+          const uint32_t ah = st + (uint32_t)(2 * part) * HB, al = ah + HB;
+          const uint32_t bh = st + (uint32_t)(4 + 2 * part) * HB, bl = bh + HB;
+#pragma unroll
+          for (int k2 = 0; k2 < 2; ++k2) {  // 2 MMAs of 32 bytes of K per 64-byte half-tile row
+            const uint32_t off = (uint32_t)k2 * 256u;
+            mma<GEMM_BF16>(tmem_d, sdesc(ah + off, 512u), sdesc(bh + off, 512u), (q > 0 || part > 0 || k2 > 0) ? 1u : 0u);
+            mma<GEMM_BF16>(tmem_d, sdesc(ah + off, 512u), sdesc(bl + off, 512u), 1u);
+            mma<GEMM_BF16>(tmem_d, sdesc(al + off, 512u), sdesc(bh + off, 512u), 1u);
+          }
+        }
+        mma_commit(&empty_bar[s]);
+        issued = true;
+      }
+      if (ok) mma_commit(&tfull_bar[buf]);
+    }
+    if (!ok) {
+      s_fail = 1;
+      atomicExch(a.status, 2);
+    }
+    if (issued) {
+      mma_commit(&drain_bar);
+      mbar_wait(&drain_bar, 0);
+    }
+  } else if (warp >= 10) {
+    epilogue_warps(a, tmem_base, tfull_bar, tempty_bar, &s_fail, s_yoff, s_epi_stop, tid - 320, warp & 3, lane,
+                   n_tiles);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 9) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS) : "memory");
   }
@@ -404,46 +726,6 @@ __global__ void k_pack_real(const float* __restrict__ X, int rows, int K, int ba
 }
 
 
-// Power-of-two scale bringing a tensor with largest |re|,|im| bits `mbits`
-// into [0.5, 1) (same rule as the bucket kernels).
-__device__ __forceinline__ float pack_scale(unsigned mbits, int* mexp) {
-  if (mbits == 0u) {
-    *mexp = 0;
-    return 1.f;
-  }
-  int ex = (int)((mbits >> 23) & 0xffu);
-  if (ex == 0) ex = 1;
-  int m = ex - 126;
-  if (m > 126) m = 126;
-  *mexp = m;
-  return __int_as_float((127 - m) << 23);
-}
-
-// 16 bytes of hi and lo parts of CH consecutive values (CH = 8 BF16 or 4 TF32).
-template <int KIND, int CH>
-__device__ __forceinline__ void split16(const float* x, uint4* hi, uint4* lo) {
-  uint32_t h[4], l[4];
-  if (KIND == GEMM_BF16) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const __nv_bfloat16 h0 = __float2bfloat16_rn(x[2 * q]), h1 = __float2bfloat16_rn(x[2 * q + 1]);
-      const __nv_bfloat16 l0 = __float2bfloat16_rn(x[2 * q] - __bfloat162float(h0));
-      const __nv_bfloat16 l1 = __float2bfloat16_rn(x[2 * q + 1] - __bfloat162float(h1));
-      h[q] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-      l[q] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
-    }
-  } else {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h[q]) : "f"(x[q]));
-      const float rest = x[q] - __uint_as_float(h[q]);
-      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l[q]) : "f"(rest));
-    }
-  }
-  *hi = make_uint4(h[0], h[1], h[2], h[3]);
-  *lo = make_uint4(l[0], l[1], l[2], l[3]);
-}
-
 // side 0: A rows = X assignments, columns [Re | Im] over K.
 // side 1: B rows 2n, 2n+1 = [Re | -Im], [Im | Re] over K for Y assignment n.
 // A thread forms CH consecutive K values of one row (one 16-byte chunk of a
@@ -456,7 +738,7 @@ __device__ __forceinline__ void split16(const float* x, uint4* hi, uint4* lo) {
 constexpr int PK_BITS = 3 * GB_BITS;
 constexpr int PK_TABS = PK_BITS / 8;   // byte tables of operand 0's offset (W bits 8q .. 8q+7)
 constexpr int PK_ITEMS = 64;           // items whose operand scales are kept in shared memory
-template <int KIND>
+template <int KIND, bool HALF>
 __global__ void k_gemm_pack(const GemmBucketArgs g, int side) {
   __shared__ int s_nz[GB_SIDE];
   __shared__ unsigned char s_pos[GB_SIDE][PK_BITS];
@@ -476,7 +758,8 @@ __global__ void k_gemm_pack(const GemmBucketArgs g, int side) {
   const long long batch = (long long)g.items << g.ns;
   const int kch = g.k_pad / CH;  // chunks per row (k_pad is a multiple of 64 / ES)
   const long long n = batch * rows * kch;
-  const int kt_count = 2 * g.k_pad * ES / GT_KBYTES;
+  constexpr int KB = HALF ? GT_KBYTES_H : GT_KBYTES;  // bytes of K per tile row
+  const int kt_count = 2 * g.k_pad * ES / KB;
   const int rt_count = (int)((side == 0 ? rows : 2 * rows) / GT_ROWS);
   char* hi = (char*)(side == 0 ? g.a_hi : g.b_hi);
   char* lo = (char*)(side == 0 ? g.a_lo : g.b_lo);
@@ -534,8 +817,8 @@ __global__ void k_gemm_pack(const GemmBucketArgs g, int side) {
       s_f[j][it] = f;
     }
   __syncthreads();
-  if (side == 0 && blockIdx.x == 0) {
-    // output exponent per item: sum over every operand of its exponent and scale shift
+  if ((side == 0 || HALF) && blockIdx.x == 0) {
+    // output exponent per item (by the A pack, or by the B pack when A is fused): sum over every operand of its exponent and scale shift
     for (int it = threadIdx.x; it < g.items; it += blockDim.x) {
       int e = 0;
       for (int j = 0; j < g.na + g.nb; ++j) {
@@ -623,16 +906,17 @@ __global__ void k_gemm_pack(const GemmBucketArgs g, int side) {
       }
     }
     uint4 h, l;
-    const size_t tb = (size_t)GT_TILE_BYTES;
+    auto goff = [](int rr, int kk) { return HALF ? gt_offset_h(rr, kk, ES) : gt_offset(rr, kk, ES); };
+    const size_t tb = HALF ? (size_t)GT_TILE_BYTES_H : (size_t)GT_TILE_BYTES;
     const int kre = k0, kim = g.k_pad + k0;
     if (side == 0) {
       const size_t t0 = (size_t)(bi * rt_count + r / GT_ROWS) * kt_count;
       split16<KIND, CH>(re, &h, &l);
-      size_t off = (t0 + (size_t)(kre * ES / GT_KBYTES)) * tb + gt_offset((int)(r % GT_ROWS), kre, ES);
+      size_t off = (t0 + (size_t)(kre * ES / KB)) * tb + goff((int)(r % GT_ROWS), kre);
       *reinterpret_cast<uint4*>(hi + off) = h;
       *reinterpret_cast<uint4*>(lo + off) = l;
       split16<KIND, CH>(im, &h, &l);
-      off = (t0 + (size_t)(kim * ES / GT_KBYTES)) * tb + gt_offset((int)(r % GT_ROWS), kim, ES);
+      off = (t0 + (size_t)(kim * ES / KB)) * tb + goff((int)(r % GT_ROWS), kim);
       *reinterpret_cast<uint4*>(hi + off) = h;
       *reinterpret_cast<uint4*>(lo + off) = l;
     } else {
@@ -644,20 +928,20 @@ __global__ void k_gemm_pack(const GemmBucketArgs g, int side) {
       const size_t t1 = (size_t)(bi * rt_count + r1 / GT_ROWS) * kt_count;
       // row 2r: [Re | -Im]
       split16<KIND, CH>(re, &h, &l);
-      size_t off = (t0 + (size_t)(kre * ES / GT_KBYTES)) * tb + gt_offset((int)(r0 % GT_ROWS), kre, ES);
+      size_t off = (t0 + (size_t)(kre * ES / KB)) * tb + goff((int)(r0 % GT_ROWS), kre);
       *reinterpret_cast<uint4*>(hi + off) = h;
       *reinterpret_cast<uint4*>(lo + off) = l;
       split16<KIND, CH>(nim, &h, &l);
-      off = (t0 + (size_t)(kim * ES / GT_KBYTES)) * tb + gt_offset((int)(r0 % GT_ROWS), kim, ES);
+      off = (t0 + (size_t)(kim * ES / KB)) * tb + goff((int)(r0 % GT_ROWS), kim);
       *reinterpret_cast<uint4*>(hi + off) = h;
       *reinterpret_cast<uint4*>(lo + off) = l;
       // row 2r + 1: [Im | Re]
       split16<KIND, CH>(im, &h, &l);
-      off = (t1 + (size_t)(kre * ES / GT_KBYTES)) * tb + gt_offset((int)(r1 % GT_ROWS), kre, ES);
+      off = (t1 + (size_t)(kre * ES / KB)) * tb + goff((int)(r1 % GT_ROWS), kre);
       *reinterpret_cast<uint4*>(hi + off) = h;
       *reinterpret_cast<uint4*>(lo + off) = l;
       split16<KIND, CH>(re, &h, &l);
-      off = (t1 + (size_t)(kim * ES / GT_KBYTES)) * tb + gt_offset((int)(r1 % GT_ROWS), kim, ES);
+      off = (t1 + (size_t)(kim * ES / KB)) * tb + goff((int)(r1 % GT_ROWS), kim);
       *reinterpret_cast<uint4*>(hi + off) = h;
       *reinterpret_cast<uint4*>(lo + off) = l;
     }
@@ -689,6 +973,26 @@ void gemm_tc_launch(int kind, const GemmArgs& args, void* stream) {
   }
 }
 
+bool gemm_fused_a(const GemmBucketArgs& g) {
+  const char* env = std::getenv("TNQ_GEMM_FUSED_A");  // "0": always pack A (for comparisons)
+  if ((env && env[0] == '0') || g.kind != GEMM_BF16 || g.na != 1 || g.nk < 3 || g.k_pad % 32) return false;
+  const GemmOperand& o = g.a[0];
+  // the three lowest summed variables are the tensor's lowest bits (8
+  // consecutive complex values, 64 bytes, per load), every other stride a
+  // multiple of 8 entries and the tensor 64-byte aligned
+  if (o.kstride[0] != 1 || o.kstride[1] != 2 || o.kstride[2] != 4) return false;
+  if (reinterpret_cast<uintptr_t>(o.ptr) % 64) return false;
+  auto mult8 = [](long long v) { return v % 8 == 0; };
+  if (!mult8(o.istride)) return false;
+  for (int q = 0; q < g.ns; ++q)
+    if (!mult8(o.sstride[q])) return false;
+  for (int q = 0; q < g.nx; ++q)
+    if (!mult8(o.rstride[q])) return false;
+  for (int q = 3; q < g.nk; ++q)
+    if (!mult8(o.kstride[q])) return false;
+  return true;
+}
+
 void gemm_bucket_launch(const GemmBucketArgs& g, const GemmEpilogue& ep, int* status, void* stream) {
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int esize = g.kind == GEMM_BF16 ? 2 : 4;
@@ -698,26 +1002,44 @@ void gemm_bucket_launch(const GemmBucketArgs& g, const GemmEpilogue& ep, int* st
   const long long cap = 16ll * device_sms();  // grid-stride pack: 16 blocks of 256 threads per SM
   const int blocks_a = (int)std::max<long long>(1, std::min<long long>((na + 255) / 256, cap));
   const int blocks_b = (int)std::max<long long>(1, std::min<long long>((nb + 255) / 256, cap));
-  if (g.kind == GEMM_BF16) {
-    k_gemm_pack<GEMM_BF16><<<blocks_a, 256, 0, s>>>(g, 0);
-    k_gemm_pack<GEMM_BF16><<<blocks_b, 256, 0, s>>>(g, 1);
-  } else {
-    k_gemm_pack<GEMM_TF32><<<blocks_a, 256, 0, s>>>(g, 0);
-    k_gemm_pack<GEMM_TF32><<<blocks_b, 256, 0, s>>>(g, 1);
-  }
   GemmArgs a;
   std::memset(&a, 0, sizeof(a));
-  a.a_hi = g.a_hi;
-  a.a_lo = g.a_lo;
-  a.b_hi = g.b_hi;
-  a.b_lo = g.b_lo;
   a.row_tiles_a = g.m_pad / GT_ROWS;
   a.row_tiles_b = 2 * g.n_pad / GT_ROWS;
-  a.k_tiles = 2 * g.k_pad * esize / GT_KBYTES;
   a.batch = (int)batch;
   a.status = status;
   a.out_c = nullptr;
   a.ep = ep;
+  if (gemm_fused_a(g)) {
+    k_gemm_pack<GEMM_BF16, true><<<blocks_b, 256, 0, s>>>(g, 1);
+    a.b_hi = g.b_hi;
+    a.b_lo = g.b_lo;
+    a.k_tiles = g.k_pad / 32;  // K steps of 32 complex values
+    a.fa = g.a[0];
+    a.fa_ns = g.ns;
+    a.fa_nx = g.nx;
+    a.fa_nk = g.nk;
+    a.fa_kpad = g.k_pad;
+    a.fa_B = g.B;
+    a.fa_meta_m = g.meta_m;
+    const long long tiles = batch * a.row_tiles_a * a.row_tiles_b;
+    const unsigned grid = (unsigned)std::max<long long>(1, std::min<long long>(tiles, device_sms()));
+    cudaFuncSetAttribute(k_gemm_tc_fa, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    k_gemm_tc_fa<<<grid, GEMM_THREADS_FA, SMEM_BYTES, s>>>(a);
+    return;
+  }
+  if (g.kind == GEMM_BF16) {
+    k_gemm_pack<GEMM_BF16, false><<<blocks_a, 256, 0, s>>>(g, 0);
+    k_gemm_pack<GEMM_BF16, false><<<blocks_b, 256, 0, s>>>(g, 1);
+  } else {
+    k_gemm_pack<GEMM_TF32, false><<<blocks_a, 256, 0, s>>>(g, 0);
+    k_gemm_pack<GEMM_TF32, false><<<blocks_b, 256, 0, s>>>(g, 1);
+  }
+  a.a_hi = g.a_hi;
+  a.a_lo = g.a_lo;
+  a.b_hi = g.b_hi;
+  a.b_lo = g.b_lo;
+  a.k_tiles = 2 * g.k_pad * esize / GT_KBYTES;
   gemm_tc_launch(g.kind, a, stream);
 }
 

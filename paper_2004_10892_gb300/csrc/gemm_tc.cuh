@@ -30,6 +30,15 @@ __host__ __device__ inline uint32_t gt_offset(int r, int k, int esize) {
   return (uint32_t)((r >> 3) * 1024 + (kb >> 4) * 128 + (r & 7) * 16 + (kb & 15));
 }
 
+// The same layout for half tiles of 64 bytes of K per row (8 KB; the fused-A
+// GEMM's operand tiles): 8-row groups 512 bytes apart.
+constexpr int GT_KBYTES_H = 64;
+constexpr int GT_TILE_BYTES_H = GT_ROWS * GT_KBYTES_H;  // 8 KB
+__host__ __device__ inline uint32_t gt_offset_h(int r, int k, int esize) {
+  const int kb = (k * esize) & (GT_KBYTES_H - 1);
+  return (uint32_t)((r >> 3) * 512 + (kb >> 4) * 128 + (r & 7) * 16 + (kb & 15));
+}
+
 // ---- merged bucket as a complex GEMM --------------------------------------
 // out[item, S, X, Y] = Sum_K A'[item, S, X, K] B'[item, S, Y, K], where A' (B')
 // is the product of the large operand and the small tensors folded into its
@@ -88,13 +97,25 @@ struct GemmArgs {
   float* out_c;
   long long ldc;
   GemmEpilogue ep;  // used when out_c is null
+  // Fused A (k_gemm_tc_fa, BF16): A is read directly from the complex64
+  // tensor described by fa (one operand, no folded tensors; its three lowest
+  // summed variables are its lowest bits), scaled, split into hi/lo and
+  // written to the shared-memory tiles by producer warps. B then comes packed
+  // in half tiles (64 bytes of K per row) and k_tiles counts 32-value complex
+  // K steps.
+  GemmOperand fa;
+  int fa_ns, fa_nx, fa_nk, fa_kpad, fa_B;
+  const unsigned* fa_meta_m;
 };
 
 // Launches C = sum_passes A_p B_p^T for every batch (grid = col tiles x row tiles x batch).
 void gemm_tc_launch(int kind, const GemmArgs& args, void* stream);
 
-// Packs both operands, writes the output exponents and runs the GEMM with the
-// bucket epilogue on `stream`.
+// True when gemm_bucket_launch runs the fused-A form for g.
+bool gemm_fused_a(const GemmBucketArgs& g);
+
+// Packs both operands (in the fused-A form only B), writes the output
+// exponents and runs the GEMM with the bucket epilogue on `stream`.
 void gemm_bucket_launch(const GemmBucketArgs& g, const GemmEpilogue& ep, int* status, void* stream);
 
 }  // namespace tnq

@@ -2395,6 +2395,26 @@ int tnq_internal_group_tails(const tnq_plan* plan, int mode, uint32_t batch, int
   return 0;
 }
 
+// Internal hook (not in include/tnq.h; host only): for every GEMM step of
+// configuration (mode, batch), in program order, 1 when it runs in the fused-A
+// form (A read from its complex tensor inside the GEMM kernel) for a workspace
+// whose base is 256-byte aligned, else 0.
+int tnq_internal_gemm_forms(const tnq_plan* plan, int mode, uint32_t batch, int32_t* fused, int cap,
+                            int32_t* out_n) {
+  if (!plan || !out_n) return 1;
+  ExecConfig C;
+  C.L = make_layout(*plan, mode, (int)batch);
+  if (!build_steps(*plan, C.L, C)) return 1;
+  *out_n = (int32_t)C.gb.size();
+  if ((int)C.gb.size() > cap) return 1;
+  for (size_t i = 0; i < C.gb.size(); ++i) {
+    GemmBucketArgs g = C.gb[i];
+    g.a[0].ptr = reinterpret_cast<const float2*>(reinterpret_cast<size_t>(g.a[0].ptr) + 256);  // arena offset + base
+    fused[i] = gemm_fused_a(g) ? 1 : 0;
+  }
+  return 0;
+}
+
 // Internal hook (not in include/tnq.h; host only): a text description of every
 // fused-chain step of configuration (mode, batch): per stage its local bits,
 // and per operand its source and the local bits it holds (nonzero strides),
@@ -2872,8 +2892,9 @@ tnq_status tnq_plan_keep_chains(tnq_plan* plan, const int32_t* last_bucket, size
 }
 
 // Internal: kernel launches of one batch of configuration (mode, batch): one
-// per remaining bucket or chain step (three per GEMM chain), one per level of
-// early buckets, and the leaf, scalar, final and slice-sum kernels.
+// per remaining bucket or chain step (three per GEMM chain, two in the fused-A
+// form), one per level of early buckets, and the leaf, scalar, final and
+// slice-sum kernels.
 int tnq_internal_launches_per_batch(const tnq_plan* plan, int mode, uint32_t batch) {
   if (!plan) return 0;
   int n = 0;
@@ -2890,6 +2911,14 @@ int tnq_internal_launches_per_batch(const tnq_plan* plan, int mode, uint32_t bat
     if (gi < 0) n += !hoist[b];
     else if (prog.groups[gi].buckets.back() == (int)b) n += prog.groups[gi].gemm ? 3 : 1;  // GEMM: 2 packs + MMA
   }
+  ExecConfig C;  // a GEMM in the fused-A form packs only B
+  C.L = make_layout(*plan, mode, (int)batch);
+  if (build_steps(*plan, C.L, C))
+    for (const GemmBucketArgs& g0 : C.gb) {
+      GemmBucketArgs g = g0;
+      g.a[0].ptr = reinterpret_cast<const float2*>(reinterpret_cast<size_t>(g.a[0].ptr) + 256);
+      n -= gemm_fused_a(g) ? 1 : 0;
+    }
   return n + levels + 4;  // + leaf, scalar, final and slice-sum kernels
 }
 

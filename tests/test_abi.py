@@ -139,6 +139,40 @@ def test_step_kinds_of_the_7x7_plan(tnq_lib):
     assert sum(nbk[i] for i in range(n.value)) == info["n_buckets"]
 
 
+def test_fused_a_gemm_form_selection(tnq_lib, monkeypatch):
+    """Host-only: GEMM steps with one A operand whose three lowest summed
+    variables are its lowest bits read A inside the GEMM kernel (fused-A form:
+    no A pack launch); operands with folded tensors keep the packed form, and
+    TNQ_GEMM_FUSED_A=0 packs every operand."""
+    L = tnq_lib.lib()
+    P = ctypes.POINTER
+    f = L.tnq_internal_gemm_forms
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32, P(ctypes.c_int32), ctypes.c_int, P(ctypes.c_int32)]
+    L.tnq_internal_launches_per_batch.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32]
+    txt = L.tnq_internal_group_text
+    txt.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32, ctypes.c_char_p, ctypes.c_size_t]
+    plan = tnq_lib.Plan(I.random_grid_circuit(7, 7, 24, 1), max_bag_log2=20, max_p=30, reorder_every=1, precision=1,
+                        gemm_min_k_log2=4)
+    plan.set_tuning(3, 64)
+    buf = (ctypes.c_int32 * 64)()
+    n = ctypes.c_int32()
+
+    def forms():
+        assert f(plan.handle, 0, 16, buf, 64, ctypes.byref(n)) == 0
+        return [buf[i] for i in range(n.value)]
+
+    tb = ctypes.create_string_buffer(1 << 20)
+    assert txt(plan.handle, 0, 16, tb, 1 << 20) == 0
+    na = [int(l.split(" na ")[1].split()[0]) for l in tb.value.decode().splitlines() if l.startswith("gemm ")]
+    fused = forms()
+    assert len(fused) == len(na) >= 2 and 1 in fused
+    assert all(na[i] == 1 for i in range(len(na)) if fused[i])
+    launches = L.tnq_internal_launches_per_batch(plan.handle, 0, 16)
+    monkeypatch.setenv("TNQ_GEMM_FUSED_A", "0")
+    assert forms() == [0] * len(na)
+    assert L.tnq_internal_launches_per_batch(plan.handle, 0, 16) == launches + sum(fused)
+
+
 def test_fused_chain_selection_roundtrip(tnq_lib):
     """A plan's fused-chain selection can be read and applied to a plan built
     later from the same circuit and options (planning is deterministic)."""

@@ -63,3 +63,52 @@ def test_bounded_wait_reports_timeout(cuda, tnq_lib):
     A = np.ones((1, 128, 64), np.float32)
     C = tc_gemm(tnq_lib, BF16, A, A)
     assert np.all(C == 64)
+
+
+def _gemm_forms(tnq_lib, plan, mode, batch):
+    L = tnq_lib.lib()
+    f = L.tnq_internal_gemm_forms
+    P = ctypes.POINTER
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32, P(ctypes.c_int32), ctypes.c_int, P(ctypes.c_int32)]
+    buf = (ctypes.c_int32 * 256)()
+    n = ctypes.c_int32()
+    assert f(plan.handle, mode, batch, buf, 256, ctypes.byref(n)) == 0
+    return [buf[i] for i in range(n.value)]
+
+
+@pytest.mark.parametrize("case", ["7x7-24", "6x6-24"])
+def test_fused_a_gemm_matches_packed_form_and_oracle(cuda, tnq_lib, oracle_lib, monkeypatch, case):
+    """GEMM steps whose A operand is read, scaled and split inside the GEMM
+    kernel (fused-A form; here with K of 2^3..2^6 values, so partly zero-filled
+    K steps, item-dependent and item-invariant operands) against the same plan
+    with every operand packed first, and every slice against the oracle at the
+    split-precision tolerance."""
+    from paper_2004_10892_gb300 import inputs as I
+
+    if case == "7x7-24":
+        circ, bits = I.random_grid_circuit(7, 7, 24, 1), I.random_bitstring(49, 1)
+        kw, tuning = dict(max_bag_log2=20, max_p=30, reorder_every=1, precision=1, gemm_min_k_log2=4), (3, 64)
+    else:
+        circ, bits = I.random_grid_circuit(6, 6, 24, 7), I.random_bitstring(36, 7)
+        kw, tuning = dict(max_bag_log2=20, max_p=20, reorder_every=1, precision=1, gemm_min_k_log2=4,
+                          fuse_min_rank=10), (4, 64)
+    n = circ.n_qubits
+    plan = tnq_lib.Plan(circ, **kw)
+    plan.set_tuning(*tuning)
+    n_sl = plan.info()["n_slices"]
+    assert 1 in _gemm_forms(tnq_lib, plan, 0, n_sl)
+    amp, per = tnq_lib.contract_sliced(plan, bits, per_slice=True)
+    monkeypatch.setenv("TNQ_GEMM_FUSED_A", "0")
+    packed = tnq_lib.Plan(circ, **kw)
+    packed.set_tuning(*tuning)
+    assert set(_gemm_forms(tnq_lib, packed, 0, n_sl)) == {0}
+    amp0, per0 = tnq_lib.contract_sliced(packed, bits, per_slice=True)
+    monkeypatch.delenv("TNQ_GEMM_FUSED_A")
+    scale = np.abs(per0).max()
+    assert np.max(np.abs(per - per0)) <= 1e-5 * scale
+    ref, ref_per = oracle_lib.contract(circ, bits, order=plan.order(), mu=plan.sliced(), per_slice=True)
+    floor = 2.0 ** (-n / 2) / np.sqrt(len(per))
+    for s in range(len(per)):
+        den = max(abs(ref_per[s]), floor)
+        assert abs(per[s] - ref_per[s]) / den < 1e-4, (s, per[s], ref_per[s])
+    assert abs(amp - ref) / max(abs(ref), 2.0 ** (-n / 2)) < 1e-4
