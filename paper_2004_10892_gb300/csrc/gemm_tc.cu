@@ -172,13 +172,16 @@ template <int KIND, int CH>
 __device__ __forceinline__ void split16(const float* x, uint4* hi, uint4* lo) {
   uint32_t h[4], l[4];
   if (KIND == GEMM_BF16) {
+    // two values per conversion (round to nearest even); a BF16 value is
+    // the upper half of its FP32 bits, so the residuals need no conversion back
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const __nv_bfloat16 h0 = __float2bfloat16_rn(x[2 * q]), h1 = __float2bfloat16_rn(x[2 * q + 1]);
-      const __nv_bfloat16 l0 = __float2bfloat16_rn(x[2 * q] - __bfloat162float(h0));
-      const __nv_bfloat16 l1 = __float2bfloat16_rn(x[2 * q + 1] - __bfloat162float(h1));
-      h[q] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-      l[q] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+      const __nv_bfloat162 hp = __floats2bfloat162_rn(x[2 * q], x[2 * q + 1]);
+      const uint32_t hb = *reinterpret_cast<const uint32_t*>(&hp);
+      const __nv_bfloat162 lp =
+          __floats2bfloat162_rn(x[2 * q] - __uint_as_float(hb << 16), x[2 * q + 1] - __uint_as_float(hb & 0xffff0000u));
+      h[q] = hb;
+      l[q] = *reinterpret_cast<const uint32_t*>(&lp);
     }
   } else {
 #pragma unroll
