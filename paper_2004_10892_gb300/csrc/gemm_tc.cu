@@ -527,37 +527,27 @@ __global__ void __launch_bounds__(GEMM_THREADS_FA, 1) k_gemm_tc_fa(const GemmArg
     const long long my_tiles = blockIdx.x < n_tiles ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     const long long n_steps = my_tiles * a.k_tiles;
     long long lt = blockIdx.x;  // load cursor: tile and K step of the next load
-    int lq = 0;
+    int lq = -1;
     long long lroff[2] = {-1, -1};
     float lf = 1.f;
-    float4 cur[8];
-    if (n_steps > 0) {
-      tile_setup(lt, lroff, &lf);
-      load_step(lroff, 0, cur);
-    }
-    float fcur = lf;
+    auto load_next = [&](float4* v, float* f) {  // the next step's values and scale
+      if (++lq == a.k_tiles || lq == 0) {
+        if (lq == a.k_tiles) lt += gridDim.x;
+        lq = 0;
+        tile_setup(lt, lroff, &lf);
+      }
+      *f = lf;
+      load_step(lroff, lq, v);
+    };
     int fills[N_STAGES] = {};
     bool ok = true;
-    for (long long g = 0; g < n_steps; ++g) {
+    // converts and stores step g from v; false when a wait gave up
+    auto store_step = [&](long long g, const float4* v, float f) {
       const int s = (int)(g % N_STAGES);
-      float4 nxt[8];
-      float fnxt = fcur;
-      if (g + 1 < n_steps) {
-        if (++lq == a.k_tiles) {
-          lq = 0;
-          lt += gridDim.x;
-          tile_setup(lt, lroff, &lf);
-        }
-        fnxt = lf;
-        load_step(lroff, lq, nxt);
-      }
       // every producer thread waits for the MMAs that read stage s to finish
       // before it overwrites the stage
       const bool w_ok = fills[s] == 0 || mbar_wait(&empty_bar[s], (fills[s] - 1) & 1);
-      if (!__all_sync(0xffffffffu, w_ok) || s_fail) {
-        ok = false;
-        break;
-      }
+      if (!__all_sync(0xffffffffu, w_ok) || s_fail) return false;
       const uint32_t st = base + (uint32_t)s * STAGE_BYTES;
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
@@ -565,11 +555,11 @@ __global__ void __launch_bounds__(GEMM_THREADS_FA, 1) k_gemm_tc_fa(const GemmArg
         float re[8], im[8];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const float4 v = cur[4 * h + u];
-          re[2 * u] = v.x * fcur;
-          im[2 * u] = v.y * fcur;
-          re[2 * u + 1] = v.z * fcur;
-          im[2 * u + 1] = v.w * fcur;
+          const float4 x = v[4 * h + u];
+          re[2 * u] = x.x * f;
+          im[2 * u] = x.y * f;
+          re[2 * u + 1] = x.z * f;
+          im[2 * u + 1] = x.w * f;
         }
         const uint32_t off = gt_offset_h(r, 8 * c, 2);
         uint4 hv, lv;
@@ -593,9 +583,22 @@ __global__ void __launch_bounds__(GEMM_THREADS_FA, 1) k_gemm_tc_fa(const GemmArg
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mbar_arrive(&full_bar[s]);
       ++fills[s];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) cur[u] = nxt[u];
-      fcur = fnxt;
+      return true;
+    };
+    // two register buffers in turn: the loads of step g + 1 are in flight
+    // while step g waits for its stage and is converted
+    float4 va[8], vb[8];
+    float fa = 1.f, fb = 1.f;
+    if (n_steps > 0) load_next(va, &fa);
+    for (long long g = 0; g < n_steps && ok; g += 2) {
+      if (g + 1 < n_steps) load_next(vb, &fb);
+      if (!store_step(g, va, fa)) {
+        ok = false;
+        break;
+      }
+      if (g + 1 >= n_steps) break;
+      if (g + 2 < n_steps) load_next(va, &fa);
+      if (!store_step(g + 1, vb, fb)) ok = false;
     }
     if (!ok) {
       s_fail = 1;

@@ -2464,6 +2464,11 @@ int tnq_internal_group_text(const tnq_plan* plan, int mode, uint32_t batch, char
            std::to_string(G.m_pad) + "x" + std::to_string(G.n_pad) + "x" + std::to_string(G.k_pad) + " na " +
            std::to_string(G.na) + " nb " + std::to_string(G.nb) + " a0.kstride";
     for (int q = 0; q < G.nk && q < 6; ++q) out += " " + std::to_string(G.a[0].kstride[q]);
+    out += " a0.rstride";
+    for (int q = 0; q < G.nx; ++q) out += " " + std::to_string(G.a[0].rstride[q]);
+    out += " a0.sstride";
+    for (int q = 0; q < G.ns; ++q) out += " " + std::to_string(G.a[0].sstride[q]);
+    out += " a0.istride " + std::to_string(G.a[0].istride) + " dep " + std::to_string(G.a[0].dep);
     out += "\n";
   }
   std::snprintf(buf, cap, "%s", out.c_str());
