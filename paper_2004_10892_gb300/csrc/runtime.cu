@@ -653,7 +653,9 @@ __device__ __forceinline__ void stage_pf(const GSt& S, int t, const float2* prev
                                          const float2* const* s_ptr, float F, const int (*tab)[TABW],
                                          const int* s_out_hi, long long out_base, int out_lo, float* tmax) {
   static_assert(NV >= 1 && NV <= 3, "one to three varying operands");
-  constexpr int PF = NHI < 2 ? NHI : ((NV >= 3 && GTB >= 8) ? 1 : 2);  // 64 registers at 256 threads
+  // loads in flight per operand: one entry ahead for one or two operands
+  // (more leaves less of the L1 cache to the operands' reuse), two for three
+  constexpr int PF = NHI < 2 ? NHI : (NV <= 2 ? 1 : 2);
   constexpr int U = NHI < 4 ? NHI : 4;  // entries per block (a multiple of PF)
   constexpr int NB = NHI / U;
   float2 k0 = make_float2(F, 0.f), k1 = make_float2(F, 0.f);
