@@ -291,73 +291,91 @@ __global__ void __launch_bounds__(TPB) k_bucket(const __grid_constant__ KParams 
   const long long omask = (1ll << ob) - 1ll;
   const int lane = t & 31;
   float tmax = 0.f;
-#pragma unroll 2
-  for (int it = 0; it < ITER; ++it) {
-    const long long g = g0 + t + ((long long)it << 8);
-    const bool valid = g < total;
-    const long long item = g >> ob;
-    float m = 0.f;
-    if (valid) {
-      if (!uniform) load_scales(item);
-      // the same arithmetic in both forms (so a slice's value does not depend on
-      // the batch size): the thread-invariant inputs' product from (1, 0) in
-      // input order, then the varying inputs in input order
-      float2 r;
-      float4 cc;
-      if (use_c) {
-        cc = sh_c[it];
-      } else {
-        float2 c0 = make_float2(1.f, 0.f), c1 = make_float2(1.f, 0.f);
+  // input 0's pairs of UB iterations are loaded together, ahead of the
+  // arithmetic and the stores of those iterations (the stores could alias the
+  // loads as far as the compiler knows, so it would not move a later load
+  // above an earlier store)
+  constexpr int UB = ITER >= 4 ? 4 : ITER;
+#pragma unroll 1
+  for (int it0 = 0; it0 < ITER; it0 += UB) {
+    float4 v0[UB];
+    if (P.sum && nv >= 1) {
 #pragma unroll
-        for (int j = 0; j < NIN; ++j) {
-          if (j < nv) continue;
-          const long long idx = sh_off[j][it];
-          if (P.sum) {
-            const float4 v = __ldg(reinterpret_cast<const float4*>(P.in[j] + idx));
-            c0 = cmul(c0, make_float2(v.x * f[j], v.y * f[j]));
-            c1 = cmul(c1, make_float2(v.z * f[j], v.w * f[j]));
-          } else {
-            const float2 v = __ldg(P.in[j] + idx);
-            c0 = cmul(c0, make_float2(v.x * f[j], v.y * f[j]));
-          }
-        }
-        cc = make_float4(c0.x, c0.y, c1.x, c1.y);
+      for (int k = 0; k < UB; ++k) {
+        const long long g = g0 + t + ((long long)(it0 + k) << 8);
+        v0[k] = g < total ? __ldg(reinterpret_cast<const float4*>(P.in[0] + sh_off[0][it0 + k] + tp[0]))
+                          : make_float4(0.f, 0.f, 0.f, 0.f);
       }
-      if (P.sum) {
-        float2 a0 = make_float2(cc.x, cc.y), a1 = make_float2(cc.z, cc.w);
-#pragma unroll
-        for (int j = 0; j < NIN; ++j) {
-          if (j >= nv) break;
-          const long long idx = sh_off[j][it] + tp[j];
-          float4 v = __ldg(reinterpret_cast<const float4*>(P.in[j] + idx));
-          a0 = cmul(a0, make_float2(v.x * f[j], v.y * f[j]));
-          a1 = cmul(a1, make_float2(v.z * f[j], v.w * f[j]));
-        }
-        r = make_float2(a0.x + a1.x, a0.y + a1.y);
-      } else {
-        float2 a = make_float2(cc.x, cc.y);
-#pragma unroll
-        for (int j = 0; j < NIN; ++j) {
-          if (j >= nv) break;
-          const long long idx = sh_off[j][it] + tp[j];
-          const float2 v = __ldg(P.in[j] + idx);
-          a = cmul(a, make_float2(v.x * f[j], v.y * f[j]));
-        }
-        r = a;
-      }
-      P.out[g] = r;
-      m = fmaxf(fabsf(r.x), fabsf(r.y));
-      if ((g & omask) == 0) P.meta_e[(long long)P.out_meta * P.B + item] = esum;
     }
-    if (uniform) {
-      tmax = fmaxf(tmax, m);
-    } else {
-      // items change every 2^ob elements: reduce within aligned lane groups
-      for (int off = 1; off < 32 && off < (1 << min(ob, 5)); off <<= 1)
-        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
-      const int grp = 1 << min(ob, 5);
-      if (valid && (lane & (grp - 1)) == 0 && m > 0.f)
-        atomic_max_pos(&P.meta_m[(long long)P.out_meta * P.B + item], m);
+#pragma unroll
+    for (int k = 0; k < UB; ++k) {
+      const int it = it0 + k;
+      const long long g = g0 + t + ((long long)it << 8);
+      const bool valid = g < total;
+      const long long item = g >> ob;
+      float m = 0.f;
+      if (valid) {
+        if (!uniform) load_scales(item);
+        // the same arithmetic in both forms (so a slice's value does not depend on
+        // the batch size): the thread-invariant inputs' product from (1, 0) in
+        // input order, then the varying inputs in input order
+        float2 r;
+        float4 cc;
+        if (use_c) {
+          cc = sh_c[it];
+        } else {
+          float2 c0 = make_float2(1.f, 0.f), c1 = make_float2(1.f, 0.f);
+#pragma unroll
+          for (int j = 0; j < NIN; ++j) {
+            if (j < nv) continue;
+            const long long idx = sh_off[j][it] + tp[j];  // tp[j]: item bits among the thread bits
+            if (P.sum) {
+              const float4 v = __ldg(reinterpret_cast<const float4*>(P.in[j] + idx));
+              c0 = cmul(c0, make_float2(v.x * f[j], v.y * f[j]));
+              c1 = cmul(c1, make_float2(v.z * f[j], v.w * f[j]));
+            } else {
+              const float2 v = __ldg(P.in[j] + idx);
+              c0 = cmul(c0, make_float2(v.x * f[j], v.y * f[j]));
+            }
+          }
+          cc = make_float4(c0.x, c0.y, c1.x, c1.y);
+        }
+        if (P.sum) {
+          float2 a0 = make_float2(cc.x, cc.y), a1 = make_float2(cc.z, cc.w);
+#pragma unroll
+          for (int j = 0; j < NIN; ++j) {
+            if (j >= nv) break;
+            const long long idx = sh_off[j][it] + tp[j];
+            const float4 v = j == 0 ? v0[k] : __ldg(reinterpret_cast<const float4*>(P.in[j] + idx));
+            a0 = cmul(a0, make_float2(v.x * f[j], v.y * f[j]));
+            a1 = cmul(a1, make_float2(v.z * f[j], v.w * f[j]));
+          }
+          r = make_float2(a0.x + a1.x, a0.y + a1.y);
+        } else {
+          float2 a = make_float2(cc.x, cc.y);
+#pragma unroll
+          for (int j = 0; j < NIN; ++j) {
+            if (j >= nv) break;
+            const long long idx = sh_off[j][it] + tp[j];
+            const float2 v = __ldg(P.in[j] + idx);
+            a = cmul(a, make_float2(v.x * f[j], v.y * f[j]));
+          }
+          r = a;
+        }
+        P.out[g] = r;
+        m = fmaxf(fabsf(r.x), fabsf(r.y));
+        if ((g & omask) == 0) P.meta_e[(long long)P.out_meta * P.B + item] = esum;
+      }
+      if (uniform) {
+        tmax = fmaxf(tmax, m);
+      } else {
+        // items change every 2^ob elements: reduce within aligned lane groups
+        for (int off = 1; off < 32 && off < (1 << min(ob, 5)); off <<= 1)
+          m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+        const int grp = 1 << min(ob, 5);
+        if (valid && (lane & (grp - 1)) == 0 && m > 0.f)
+          atomic_max_pos(&P.meta_m[(long long)P.out_meta * P.B + item], m);
+      }
     }
   }
   if (uniform) {
@@ -1447,11 +1465,39 @@ static KParams single_kparams(const tnq_plan& P, const Layout& L, const PBucket&
     }
     for (int i = k.out_bits; i < k.G; ++i) k.stride[j][i] = L.dep[tid] ? ((1ll << x.rank()) << (i - k.out_bits)) : 0;
   }
+  // the input with the most distinct entries per block (then the largest)
+  // first, among those that vary with output bits 0-7: k_bucket loads input 0
+  // several iterations ahead. The choice depends on the bucket alone (not on
+  // the batch size or on which variables make an input item-dependent), so
+  // every configuration multiplies in the same order.
+  {
+    auto weight = [&](int j) {  // (-1: constant over output bits 0-7; else output bits 0-11 it varies with, rank)
+      int w8 = 0, w = 0, rank = 0;
+      for (int i = 0; i < k.out_bits; ++i) {
+        const bool nz = k.stride[j][i] != 0;
+        w8 += (i < 8) && nz;
+        w += (i < 12) && nz;
+        rank += nz;
+      }
+      return w8 ? std::make_pair(w, rank) : std::make_pair(-1, 0);
+    };
+    int best = 0;
+    for (int j = 1; j < b.k; ++j)
+      if (weight(j) > weight(best)) best = j;
+    if (best != 0 && weight(best).first >= 0) {
+      std::swap(k.in[best], k.in[0]);
+      std::swap(k.in_meta[best], k.in_meta[0]);
+      std::swap(k.in_dep[best], k.in_dep[0]);
+      for (int i = 0; i < GMAX; ++i) std::swap(k.stride[best][i], k.stride[0][i]);
+    }
+  }
   // inputs that vary with the low 8 bits (a block's threads) first; the others
   // are the same for every thread of a block's iteration (k_bucket multiplies
   // them once per block into a constant pair)
+  // (output bits only: whether an input varies with the item bits depends on
+  // the configuration, and the arithmetic order must not)
   auto varies = [&](int j) {
-    for (int i = 0; i < 8 && i < k.G; ++i)
+    for (int i = 0; i < 8 && i < k.out_bits; ++i)
       if (k.stride[j][i]) return true;
     return false;
   };
