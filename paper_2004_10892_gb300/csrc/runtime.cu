@@ -1834,7 +1834,8 @@ static bool build_steps(const tnq_plan& P, const Layout& L, ExecConfig& C) {
       C.step_group.push_back(-1);
       C.step_hoist.push_back(L.hoist[bi]);
       C.kp.push_back(k);
-      C.kshape.push_back({prog.buckets[bi].k, k.G > 8 ? 12 : 8});
+      // 2^12 entries per block only when that still gives >= 1024 blocks
+      C.kshape.push_back({prog.buckets[bi].k, k.G >= 22 ? 12 : 8});
       double by = tbytes(prog.buckets[bi].output);
       for (int t : prog.buckets[bi].inputs) by += tbytes(t);
       C.step_bytes.push_back(by);
