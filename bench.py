@@ -126,14 +126,10 @@ class ClockSampler:
 # slices of a batch; item-invariant operands are read once per batch, so this
 # slightly overstates it).
 MEASURED_TRAFFIC = {"k_group": [
-    {"kernel_sha1": "5f1d625d9404814f53a890ed81173b9e98775fee", "tuning": [4, 64], "bytes_one_slice": 105871360.0,
+    {"kernel_sha1": "6be92c4138b46c2c820ed7087910766360e0d71e", "tuning": [4, 64], "bytes_one_slice": 106107904.0,
      "launches": 12,
      "capture": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:k_group -s 12 -c 12 on a one-slice "
                 "batch of the tuned default plan (tuning 2^4 / 64)"},
-    {"kernel_sha1": "5f1d625d9404814f53a890ed81173b9e98775fee", "tuning": [3, 64], "bytes_one_slice": 105639680.0,
-     "launches": 11,
-     "capture": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:k_group -s 11 -c 11 on a one-slice "
-                "batch of the tuned default plan (tuning 2^3 / 64)"},
 ]}
 
 
@@ -243,7 +239,8 @@ def launch_roofline(L, plan, bits, ws, B, n_sl, stream, peaks, info):
     if gem:
         # split precision: 3 BF16/TF32 MMA passes over the real embedding (4x the complex flops)
         gem_tfs = sum(fl[i] for i in gem) / (t_gem / 1e3) / 1e12 if t_gem > 0 else None
-        out["gemm_buckets"] = {"kernel": "k_gemm_pack + k_gemm_tc", "launches": len(gem), "time_share": t_gem / tot,
+        out["gemm_buckets"] = {"kernel": "k_gemm_pack + k_gemm_tc (k_gemm_tc_fa: B pack only)", "launches": len(gem),
+                               "time_share": t_gem / tot,
                                "algorithmic_tflops": gem_tfs}
     out["top_launches"] = [{"kind": ("gemm" if kind[i] >= 100 else "group") if kind[i] else "bucket",
                             "buckets": max(1, kind[i] % 100), "bag": bag[i],
