@@ -216,7 +216,7 @@ __device__ __forceinline__ void atomic_max_pos(unsigned* p, float v) {
 // 2^LT consecutive g: bits >= 8 of g go through a shared table per input, bits
 // < 8 through a per-thread offset, so each element costs one add per input.
 template <int NIN, int LT>
-__global__ void __launch_bounds__(TPB) k_bucket(const __grid_constant__ KParams P) {
+__global__ void __launch_bounds__(TPB, 5) k_bucket(const __grid_constant__ KParams P) {
   constexpr int ITER = (LT > 8) ? (1 << (LT - 8)) : 1;
   __shared__ long long sh_off[NIN][ITER];
   __shared__ float sh_red[TPB / 32];
