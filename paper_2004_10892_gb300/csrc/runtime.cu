@@ -540,6 +540,7 @@ struct GSt {
   int ustride[KMAX];           // stride of the eliminated variable, per input
   int q0;                      // offset table of varying input j is pair q0 + j
   int pd;                      // 1: input 0 is the previous stage's buffer at offset 2c (u at bit 0)
+  int kinv;                    // 1: the constant inputs n_var.. hold no tile bit (their pair is per item)
 };
 
 struct GParams {
@@ -832,6 +833,29 @@ __device__ __forceinline__ void run_stage(bool with_k, const GSt& S, int t, cons
                                           tmax);
 }
 
+// Product of the power-of-two scales of a stage's memory inputs for an item.
+__device__ __forceinline__ float stage_scale(const GParams& P, const GSt& S, long long item) {
+  float f = 1.f;
+  for (int j = 0; j < S.n_in; ++j) {
+    if (S.src[j] < 0) continue;
+    const GIn& g = P.gin[S.src[j]];
+    if (g.meta < 0) continue;
+    int m;
+    f *= scale_of_max(P.meta_m[(long long)g.meta * P.B + (g.dep ? item : 0ll)], &m);
+  }
+  return f;
+}
+
+// The (u = 0, u = 1) product of a stage's constant inputs n_var.., starting
+// from (k0, k1) (the stage's power-of-two scale), in input order.
+__device__ __forceinline__ void tail_const_pair(const GSt& S, const float2* const* s_ptr, float2* k0, float2* k1) {
+  for (int j = S.n_var; j < S.n_in; ++j) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(s_ptr[S.src[j]]));
+    *k0 = cmul(*k0, make_float2(v.x, v.y));
+    *k1 = cmul(*k1, make_float2(v.z, v.w));
+  }
+}
+
 // Stages 1..M of a group in registers. Every one of them reads the previous
 // stage densely (operand 0, entry c at 2c: the pair over u_s) and has at most
 // one other varying operand; so the last stage's entry cm depends on the
@@ -844,7 +868,7 @@ __device__ __forceinline__ void run_stage(bool with_k, const GSt& S, int t, cons
 template <int M>
 __device__ __forceinline__ void group_tail(const GParams& P, int t, const float2* buf, const float2* const* s_ptr,
                                            const float* s_F, const int (*s_tab)[TABW], const int* s_out_hi,
-                                           long long out_base, int out_lo, float* tmax) {
+                                           long long out_base, int out_lo, float* tmax, const float4* s_K) {
   float2 K0[M], K1[M];
   const float2* op[M];
   int row[M];
@@ -852,14 +876,14 @@ __device__ __forceinline__ void group_tail(const GParams& P, int t, const float2
 #pragma unroll
   for (int s = 0; s < M; ++s) {
     const GSt& S = P.st[s + 1];
-    float2 k0 = make_float2(s_F[s + 1], 0.f), k1 = k0;
-    for (int j = S.n_var; j < S.n_in; ++j) {
-      const float4 v = __ldg(reinterpret_cast<const float4*>(s_ptr[S.src[j]]));
-      k0 = cmul(k0, make_float2(v.x, v.y));
-      k1 = cmul(k1, make_float2(v.z, v.w));
+    if (S.kinv) {  // the same for every tile of the item: computed once per item
+      const float4 k = s_K[s + 1];
+      K0[s] = make_float2(k.x, k.y);
+      K1[s] = make_float2(k.z, k.w);
+    } else {
+      K0[s] = K1[s] = make_float2(s_F[s + 1], 0.f);
+      tail_const_pair(S, s_ptr, &K0[s], &K1[s]);
     }
-    K0[s] = k0;
-    K1[s] = k1;
     two[s] = S.n_var > 1;
     op[s] = two[s] ? s_ptr[S.src[1]] : nullptr;
     row[s] = S.q0 + 1;
@@ -932,6 +956,7 @@ __global__ void __launch_bounds__(GTPB, TK ? 5 : 4) k_group(const __grid_constan
   __shared__ int s_out_hi[1 << (GL_MAX - 1 - GTB)];
   __shared__ long long s_out_base;
   __shared__ float s_red[GTPB / 32];
+  __shared__ float4 s_K[GM_MAX];  // register-tail stages with per-item constant pairs (kinv)
   const int t = threadIdx.x;
   // tables shared by every tile
   for (int e = t; e < (GIN_MAX + 1) * GH_MAX; e += GTPB) {
@@ -1018,16 +1043,21 @@ __global__ void __launch_bounds__(GTPB, TK ? 5 : 4) k_group(const __grid_constan
           s_e[t] = P.meta_e[row] + m;
         }
       } else if (t < P.n_gin + P.n_st) {
-        const GSt& S = P.st[t - P.n_gin];
-        float f = 1.f;
-        for (int j = 0; j < S.n_in; ++j) {
-          if (S.src[j] < 0) continue;
+        s_F[t - P.n_gin] = stage_scale(P, P.st[t - P.n_gin], item);
+      }
+      // the register-tail stages' constant pairs when their inputs hold no
+      // tile bit: the same for every tile of the item
+      if (TK && t >= 1 && t <= P.tail && P.st[t].kinv) {
+        const GSt& S = P.st[t];
+        const float f = stage_scale(P, S, item);
+        float2 k0 = make_float2(f, 0.f), k1 = k0;
+        for (int j = S.n_var; j < S.n_in; ++j) {
           const GIn& g = P.gin[S.src[j]];
-          if (g.meta < 0) continue;
-          int m;
-          f *= scale_of_max(P.meta_m[(long long)g.meta * P.B + (g.dep ? item : 0ll)], &m);
+          const float4 v = __ldg(reinterpret_cast<const float4*>(g.ptr + (g.dep ? item * g.istride : 0ll)));
+          k0 = cmul(k0, make_float2(v.x, v.y));
+          k1 = cmul(k1, make_float2(v.z, v.w));
         }
-        s_F[t - P.n_gin] = f;
+        s_K[t] = make_float4(k0.x, k0.y, k1.x, k1.y);
       }
       meta_item = item;
     }
@@ -1050,9 +1080,9 @@ __global__ void __launch_bounds__(GTPB, TK ? 5 : 4) k_group(const __grid_constan
       }
       __syncthreads();
       switch (P.tail) {  // stage 0's buffer is region A
-        case 2: group_tail<2>(P, t, cur, s_ptr, s_F, s_tab, s_out_hi, s_out_base, out_lo, &tmax); break;
-        case 3: group_tail<3>(P, t, cur, s_ptr, s_F, s_tab, s_out_hi, s_out_base, out_lo, &tmax); break;
-        default: group_tail<4>(P, t, cur, s_ptr, s_F, s_tab, s_out_hi, s_out_base, out_lo, &tmax); break;
+        case 2: group_tail<2>(P, t, cur, s_ptr, s_F, s_tab, s_out_hi, s_out_base, out_lo, &tmax, s_K); break;
+        case 3: group_tail<3>(P, t, cur, s_ptr, s_F, s_tab, s_out_hi, s_out_base, out_lo, &tmax, s_K); break;
+        default: group_tail<4>(P, t, cur, s_ptr, s_F, s_tab, s_out_hi, s_out_base, out_lo, &tmax, s_K); break;
       }
     }
     const int n_run = TK ? 0 : P.n_st;  // stages run in shared memory
@@ -1626,6 +1656,13 @@ static GParams group_gparams(const tnq_plan& P, const Layout& L, const FusedGrou
         S.ustride[j] = 1 << pu;
       }
     }
+  }
+  for (int s = 0; s < G.n_st; ++s) {  // constant inputs that hold no tile bit
+    GSt& S = G.st[s];
+    bool inv = true;
+    for (int j = S.n_var; inv && j < S.n_in; ++j)
+      for (int i = 0; inv && i < G.n_h; ++i) inv = S.src[j] >= 0 && G.gin[S.src[j]].hstride[i] == 0;
+    S.kinv = inv ? 1 : 0;
   }
   for (int s = 0; s < G.n_st; ++s) {  // dense previous-stage operand (offset 2c, u at bit 0)
     GSt& S = G.st[s];
