@@ -1657,11 +1657,13 @@ static GParams group_gparams(const tnq_plan& P, const Layout& L, const FusedGrou
       }
     }
   }
-  for (int s = 0; s < G.n_st; ++s) {  // constant inputs that hold no tile bit
+  for (int s = 0; s < G.n_st; ++s) {  // constant inputs, all from memory, that hold no tile bit
     GSt& S = G.st[s];
     bool inv = true;
-    for (int j = S.n_var; inv && j < S.n_in; ++j)
-      for (int i = 0; inv && i < G.n_h; ++i) inv = S.src[j] >= 0 && G.gin[S.src[j]].hstride[i] == 0;
+    for (int j = S.n_var; inv && j < S.n_in; ++j) {
+      inv = S.src[j] >= 0;
+      for (int i = 0; inv && i < G.n_h; ++i) inv = G.gin[S.src[j]].hstride[i] == 0;
+    }
     S.kinv = inv ? 1 : 0;
   }
   for (int s = 0; s < G.n_st; ++s) {  // dense previous-stage operand (offset 2c, u at bit 0)
@@ -2016,6 +2018,11 @@ static std::string validate_config(const tnq_plan& P, int mode, int B) {
         if (j >= S.n_var)
           for (int b = 0; b < S.nbits; ++b)
             if (S.cstride[j][b]) return "group " + std::to_string(gi) + ": constant input varies";
+        if (j >= S.n_var && S.kinv) {  // a per-item constant pair: read from memory at the item's base
+          if (S.src[j] < 0) return "group " + std::to_string(gi) + ": per-item constant from the chain";
+          for (int i = 0; i < G.n_h; ++i)
+            if (G.gin[S.src[j]].hstride[i]) return "group " + std::to_string(gi) + ": per-item constant varies";
+        }
         for (int b = 0; b < S.nbits; ++b)
           if (S.cstride[j][b] & 1) return "group " + std::to_string(gi) + ": odd local stride";
         if (S.src[j] >= 0) {

@@ -113,7 +113,10 @@ def test_launch_bounds_hold_on_host(tnq_lib):
                   (I.ghz(5), {}), (I.all_h(3), {}), (I.random_small_circuit(9, 90, 2), dict(min_p=2, max_p=2)),
                   (I.random_grid_circuit(6, 6, 24, 3), dict(max_bag_log2=24, min_p=4, max_p=4, precision=1,
                                                             gemm_min_k_log2=3)),
-                  (I.random_grid_circuit(5, 5, 20, 2), dict(precision=2, gemm_min_k_log2=3, fuse_min_rank=4))]:
+                  (I.random_grid_circuit(5, 5, 20, 2), dict(precision=2, gemm_min_k_log2=3, fuse_min_rank=4))] + [
+                  (I.random_grid_circuit(rows, cols, cyc, 20 + seed), dict(min_p=p, max_p=p, fuse_min_rank=fuse))
+                  for seed, (rows, cols, cyc, p) in enumerate([(4, 4, 16, 2), (5, 5, 20, 3), (4, 5, 24, 4)])
+                  for fuse in (1, 4, 8)]:  # tiny fused chains (no tile variable, constants from the chain)
         plan = tnq_lib.Plan(c, **kw)
         for mode in (0, 1):
             for B in (1, 2, 8, 64, 1024):
