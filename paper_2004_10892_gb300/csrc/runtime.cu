@@ -553,6 +553,7 @@ struct GParams {
   int n_st, n_gin, n_h, out_meta, out_dep, B;
   int n_pairs;
   int tail;                    // > 0: stages 1..tail run in registers (group_tail) after stage 0
+  int lean2;                   // 1: two stages, stage 1 reads stage 0 densely and writes the output (k_group<2>)
   int* meta_e;
   unsigned* meta_m;
 };
@@ -821,6 +822,25 @@ __device__ __forceinline__ void stage0_pf(const GSt& S, int t, float2* cur, cons
 #undef TNQ_PF0
 }
 
+// Stage 1 of a two-stage chain (k_group<2>): operand 0 is stage 0's buffer
+// read densely, the stage writes the group's output.
+template <int NV, bool K>
+__device__ __forceinline__ void stage_last_pd(const GSt& S, int t, const float2* prev, float2* out,
+                                              const float2* const* s_ptr, float F, const int (*tab)[TABW],
+                                              const int* s_out_hi, long long out_base, int out_lo, float* tmax) {
+#define TNQ_PFL(n) \
+  stage_pf<NV, K, n, true, true>(S, t, prev, nullptr, out, s_ptr, F, tab, s_out_hi, out_base, out_lo, tmax)
+  switch (S.nbits - GTB) {
+    case 5: TNQ_PFL(32); break;
+    case 4: TNQ_PFL(16); break;
+    case 3: TNQ_PFL(8); break;
+    case 2: TNQ_PFL(4); break;
+    case 1: TNQ_PFL(2); break;
+    default: TNQ_PFL(1); break;
+  }
+#undef TNQ_PFL
+}
+
 template <int NV>
 __device__ __forceinline__ void run_stage(bool with_k, const GSt& S, int t, const float2* prev, float2* cur,
                                           float2* out, bool last, const float2* const* s_ptr, float F,
@@ -942,10 +962,13 @@ __device__ __forceinline__ void group_tail(const GParams& P, int t, const float2
 }
 
 // Persistent fused-group kernel: every block builds the stage tables once,
-// (TK: chains with a register tail -- stage 0 in shared memory, then
-// group_tail; fewer code paths, so five blocks fit per SM)
 // then loops over tiles (item, H assignment) tile = blockIdx.x + k*gridDim.x.
-template <bool TK>
+// TK = 0: every stage through the stage loops (both shared-memory regions);
+// TK = 1: chains with a register tail -- stage 0 in shared memory, then
+// group_tail; TK = 2: two-stage chains whose stage 1 reads stage 0 densely
+// and writes the output. The last two need region A only and fewer code
+// paths, so five blocks fit per SM.
+template <int TK>
 __global__ void __launch_bounds__(GTPB, TK ? 5 : 4) k_group(const __grid_constant__ GParams P, long long n_tiles) {
   extern __shared__ float2 g_stage[];  // stage regions A (2^(GL_MAX-1) entries) and B (half of A)
   __shared__ int s_hstr[GIN_MAX + 1][GH_MAX];  // row GIN_MAX: the output (within-item offsets < 2^31)
@@ -1047,7 +1070,7 @@ __global__ void __launch_bounds__(GTPB, TK ? 5 : 4) k_group(const __grid_constan
       }
       // the register-tail stages' constant pairs when their inputs hold no
       // tile bit: the same for every tile of the item
-      if (TK && t >= 1 && t <= P.tail && P.st[t].kinv) {
+      if (TK == 1 && t >= 1 && t <= P.tail && P.st[t].kinv) {
         const GSt& S = P.st[t];
         const float f = stage_scale(P, S, item);
         float2 k0 = make_float2(f, 0.f), k1 = k0;
@@ -1079,10 +1102,26 @@ __global__ void __launch_bounds__(GTPB, TK ? 5 : 4) k_group(const __grid_constan
         default: stage0_pf<3, true>(S, t, cur, s_ptr, F, s_tab + S.q0); break;
       }
       __syncthreads();
-      switch (P.tail) {  // stage 0's buffer is region A
-        case 2: group_tail<2>(P, t, cur, s_ptr, s_F, s_tab, s_out_hi, s_out_base, out_lo, &tmax, s_K); break;
-        case 3: group_tail<3>(P, t, cur, s_ptr, s_F, s_tab, s_out_hi, s_out_base, out_lo, &tmax, s_K); break;
-        default: group_tail<4>(P, t, cur, s_ptr, s_F, s_tab, s_out_hi, s_out_base, out_lo, &tmax, s_K); break;
+      if constexpr (TK == 1) {
+        switch (P.tail) {  // stage 0's buffer is region A
+          case 2: group_tail<2>(P, t, cur, s_ptr, s_F, s_tab, s_out_hi, s_out_base, out_lo, &tmax, s_K); break;
+          case 3: group_tail<3>(P, t, cur, s_ptr, s_F, s_tab, s_out_hi, s_out_base, out_lo, &tmax, s_K); break;
+          default: group_tail<4>(P, t, cur, s_ptr, s_F, s_tab, s_out_hi, s_out_base, out_lo, &tmax, s_K); break;
+        }
+      } else {
+        const GSt& S1 = P.st[1];
+        const float F1 = s_F[1];
+        const int (*tab1)[TABW] = s_tab + S1.q0;
+#define TNQ_L(nv, k) stage_last_pd<nv, k>(S1, t, cur, P.out, s_ptr, F1, tab1, s_out_hi, s_out_base, out_lo, &tmax)
+        switch (S1.n_var * 2 + (S1.n_in > S1.n_var ? 1 : 0)) {
+          case 2: TNQ_L(1, false); break;
+          case 3: TNQ_L(1, true); break;
+          case 4: TNQ_L(2, false); break;
+          case 5: TNQ_L(2, true); break;
+          case 6: TNQ_L(3, false); break;
+          default: TNQ_L(3, true); break;
+        }
+#undef TNQ_L
       }
     }
     const int n_run = TK ? 0 : P.n_st;  // stages run in shared memory
@@ -1687,6 +1726,17 @@ static GParams group_gparams(const tnq_plan& P, const Layout& L, const FusedGrou
     }
     G.tail = ok ? G.n_st - 1 : 0;
   }
+  // two stages: stage 0 from memory (as above), stage 1 reading it densely
+  // with at most two other varying operands, all from memory
+  if (!G.tail && G.n_st == 2) {
+    const GSt& S0 = G.st[0];
+    const GSt& S1 = G.st[1];
+    bool ok = S0.n_var >= 1 && S0.n_var <= 3 && S0.nbits > 0 && S1.pd && S1.n_var >= 1 && S1.n_var <= 3 &&
+              S1.nbits <= GTB + 5;
+    for (int j = 0; ok && j < S0.n_in; ++j) ok = S0.src[j] >= 0;
+    for (int j = 1; ok && j < S1.n_in; ++j) ok = S1.src[j] >= 0;
+    G.lean2 = ok ? 1 : 0;
+  }
   const auto& last = sv[G.n_st - 1];
   for (size_t b = 0; b < last.size(); ++b) {
     const int p = index_in(o.vars, last[b]);
@@ -1695,7 +1745,10 @@ static GParams group_gparams(const tnq_plan& P, const Layout& L, const FusedGrou
   }
   if (last.size() + g.tile_vars.size() != o.vars.size()) return G;
   // with the register tail only stage 0's buffer (region A) is used
-  *smem = G.tail ? (int)sizeof(float2) << G.st[0].nbits : GROUP_SMEM_BYTES;
+  // (k_group<2>'s dense stage-1 reads cover pairs 0..GTPB-1 even when stage 0
+  // has fewer entries: its threads past the end compute an entry they do not store)
+  *smem = G.tail ? (int)sizeof(float2) << G.st[0].nbits
+                 : (G.lean2 ? (int)sizeof(float2) * std::max(1 << G.st[0].nbits, 2 * GTPB) : GROUP_SMEM_BYTES);
   (void)maxbits;
   *ok = true;
   return G;
@@ -2050,6 +2103,8 @@ static std::string validate_config(const tnq_plan& P, int mode, int B) {
     for (int b = 0; b < G.st[G.n_st - 1].nbits; ++b) om += G.out_cstride[b];
     if (om >= alloc(g.output)) return "group " + std::to_string(gi) + ": output overflows";
     if (C.gsmem[gi] > 200 * 1024) return "group shared memory";
+    if (G.lean2 && (C.gsmem[gi] < 2 * GTPB * (int)sizeof(float2) || C.gsmem[gi] < (8 << G.st[0].nbits)))
+      return "group " + std::to_string(gi) + ": shared memory below the dense stage's reads";
   }
   for (size_t gi = 0; gi < C.gb.size(); ++gi) {
     const GemmBucketArgs& G = C.gb[gi];
@@ -2101,18 +2156,20 @@ static std::string validate_config(const tnq_plan& P, int mode, int B) {
 }
 
 static cudaError_t allow_group_smem() {
-  const cudaError_t e = cudaFuncSetAttribute(k_group<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             GROUP_SMEM_BYTES);
+  cudaError_t e = cudaFuncSetAttribute(k_group<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, GROUP_SMEM_BYTES);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_group<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, GROUP_SMEM_BYTES);
+  e = cudaFuncSetAttribute(k_group<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, GROUP_SMEM_BYTES);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_group<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, GROUP_SMEM_BYTES);
 }
 
-static tnq_status group_grid_size(int* out, int smem = GROUP_SMEM_BYTES, bool tail = false) {
+static tnq_status group_grid_size(int* out, int smem = GROUP_SMEM_BYTES, int kind = 0) {
   int dev = 0, sms = 0, per_sm = 0;
   CU(cudaGetDevice(&dev));
   CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  if (tail) CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_group<true>, GTPB, smem));
-  else CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_group<false>, GTPB, smem));
+  if (kind == 1) CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_group<1>, GTPB, smem));
+  else if (kind == 2) CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_group<2>, GTPB, smem));
+  else CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_group<0>, GTPB, smem));
   *out = std::max(1, sms * std::max(1, per_sm));
   return TNQ_OK;
 }
@@ -2164,7 +2221,7 @@ static tnq_status build_config(const tnq_plan& P, int mode, int B, ExecConfig** 
   if (!build_steps(P, C->L, *C)) return fail(TNQ_EUNSUPPORTED);
   for (size_t i = 0; i < C->gsmem.size(); ++i) {  // chains with a register tail: more blocks may fit
     int g = 0;
-    if ((gst = group_grid_size(&g, C->gsmem[i], C->gp[i].tail > 0)) != TNQ_OK) return fail(gst);
+    if ((gst = group_grid_size(&g, C->gsmem[i], C->gp[i].tail > 0 ? 1 : (C->gp[i].lean2 ? 2 : 0))) != TNQ_OK) return fail(gst);
     C->ggrid.push_back(g);
   }
   if ((e = up((void**)&C->d_hoist, C->hoist_dev.data(), C->hoist_dev.size() * sizeof(HoistDev))) != cudaSuccess) {
@@ -2236,8 +2293,9 @@ static void launch_step(const ExecConfig& C, int i, float2* arena, int* me, unsi
     const long long tiles = (g.out_dep ? (long long)g.B : 1ll) << g.n_h;
     const long long grid =
         std::min<long long>(tiles, (long long)(C.ggrid.empty() ? C.group_grid : C.ggrid[st.second]));
-    if (g.tail) k_group<true><<<(unsigned)grid, GTPB, C.gsmem[st.second], s>>>(g, tiles);
-    else k_group<false><<<(unsigned)grid, GTPB, C.gsmem[st.second], s>>>(g, tiles);
+    if (g.tail) k_group<1><<<(unsigned)grid, GTPB, C.gsmem[st.second], s>>>(g, tiles);
+    else if (g.lean2) k_group<2><<<(unsigned)grid, GTPB, C.gsmem[st.second], s>>>(g, tiles);
+    else k_group<0><<<(unsigned)grid, GTPB, C.gsmem[st.second], s>>>(g, tiles);
   }
 }
 
@@ -3415,7 +3473,7 @@ static tnq_status get_noalloc_config(const tnq_plan& P, uint64_t cap, char* scra
   if (!build_steps(P, C.L, C)) return TNQ_EUNSUPPORTED;
   for (size_t i = 0; i < C.gsmem.size(); ++i) {  // per-chain persistent grids, as build_config sizes them
     int g = 0;
-    if ((st = group_grid_size(&g, C.gsmem[i], C.gp[i].tail > 0)) != TNQ_OK) return st;
+    if ((st = group_grid_size(&g, C.gsmem[i], C.gp[i].tail > 0 ? 1 : (C.gp[i].lean2 ? 2 : 0))) != TNQ_OK) return st;
     C.ggrid.push_back(g);
   }
   size_t o = 0;
