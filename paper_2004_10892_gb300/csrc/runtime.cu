@@ -2579,7 +2579,8 @@ int tnq_internal_group_text(const tnq_plan* plan, int mode, uint32_t batch, char
   for (size_t gi = 0; gi < C.gp.size(); ++gi) {
     const GParams& G = C.gp[gi];
     out += "group " + std::to_string(gi) + " stages " + std::to_string(G.n_st) + " tail " + std::to_string(G.tail) +
-           " n_h " + std::to_string(G.n_h) + " gin " + std::to_string(G.n_gin) + "\n";
+           " n_h " + std::to_string(G.n_h) + " gin " + std::to_string(G.n_gin) + " lean2 " + std::to_string(G.lean2) +
+           " smem " + std::to_string(C.gsmem[gi]) + "\n";
     for (int j = 0; j < G.n_gin; ++j) {
       int nh = 0;
       for (int i = 0; i < G.n_h; ++i) nh += G.gin[j].hstride[i] != 0;
