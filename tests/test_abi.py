@@ -357,3 +357,29 @@ def test_tuning_roundtrip_and_validation(tnq_lib):
         with pytest.raises(tnq_lib.TnqError) as e:
             plan.set_tuning(*bad)
         assert e.value.status == tnq_lib.EINVAL
+
+
+def test_bench_plan_chain_kernels(tnq_lib):
+    """Host-only: in the 7x7 depth 1+32+1 plan every fused chain runs in a
+    specialised instantiation -- the 5-stage chains with a register tail
+    (k_group<1>), the 2-stage chains as stage 0 plus one dense last stage
+    (k_group<2>, region A of shared memory only)."""
+    L = tnq_lib.lib()
+    txt = L.tnq_internal_group_text
+    txt.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32, ctypes.c_char_p, ctypes.c_size_t]
+    plan = tnq_lib.Plan(I.random_grid_circuit(7, 7, 32, 0), max_bag_log2=28, max_p=40, precision=1, gemm_min_k_log2=4,
+                        reorder_every=1, order_trials=32, fuse_min_rank=12)
+    tb = ctypes.create_string_buffer(1 << 22)
+    assert txt(plan.handle, 0, 32, tb, 1 << 22) == 0
+    heads = [l.split() for l in tb.value.decode().splitlines() if l.startswith("group ")]
+    assert heads
+    kinds = []
+    for h in heads:
+        f = dict(zip(h[2::2], h[3::2]))  # "stages 2 tail 0 ... lean2 1 smem 32768"
+        stages, tail, lean2, smem = int(f["stages"]), int(f["tail"]), int(f["lean2"]), int(f["smem"])
+        if stages == 2:
+            assert lean2 == 1 and tail == 0
+        if tail or lean2:
+            assert smem <= 32768
+        kinds.append(1 if tail else (2 if lean2 else 0))
+    assert 1 in kinds and 2 in kinds and 0 not in kinds
