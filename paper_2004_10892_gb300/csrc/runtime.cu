@@ -541,6 +541,7 @@ struct GSt {
   int q0;                      // offset table of varying input j is pair q0 + j
   int pd;                      // 1: input 0 is the previous stage's buffer at offset 2c (u at bit 0)
   int kinv;                    // 1: the constant inputs n_var.. hold no tile bit (their pair is per item)
+  int n_tc;                    // varying inputs n_var-n_tc..n_var-1 hold thread bits only: one pair per thread
 };
 
 struct GParams {
@@ -679,9 +680,10 @@ __device__ __forceinline__ void stage_pf(const GSt& S, int t, const float2* prev
   constexpr int U = NHI < 4 ? NHI : 4;  // entries per block (a multiple of PF)
   constexpr int NB = NHI / U;
   float2 k0 = make_float2(F, 0.f), k1 = make_float2(F, 0.f);
-  if (K) {
+  if (K) {  // the thread's pairs of inputs NV..n_var-1 (thread bits only), then the block's constants
     for (int j = NV; j < S.n_in; ++j) {
-      const float4 v = __ldg(reinterpret_cast<const float4*>(s_ptr[S.src[j]]));
+      const int o = j < S.n_var ? tab[j][t & 15] + tab[j][GT_MID + (t >> 4)] : 0;
+      const float4 v = __ldg(reinterpret_cast<const float4*>(s_ptr[S.src[j]] + o));
       k0 = cmul(k0, make_float2(v.x, v.y));
       k1 = cmul(k1, make_float2(v.z, v.w));
     }
@@ -1091,9 +1093,10 @@ __global__ void __launch_bounds__(GTPB, TK ? 5 : 4) k_group(const __grid_constan
     float2* cur = g_stage;
     if constexpr (TK) {
       const GSt& S = P.st[0];
-      const bool with_k = S.n_in > S.n_var;
+      const int nv = S.n_var - S.n_tc;  // operands loaded per entry
+      const bool with_k = S.n_in > nv;
       const float F = s_F[0];
-      switch (S.n_var * 2 + (with_k ? 1 : 0)) {
+      switch (nv * 2 + (with_k ? 1 : 0)) {
         case 2: stage0_pf<1, false>(S, t, cur, s_ptr, F, s_tab + S.q0); break;
         case 3: stage0_pf<1, true>(S, t, cur, s_ptr, F, s_tab + S.q0); break;
         case 4: stage0_pf<2, false>(S, t, cur, s_ptr, F, s_tab + S.q0); break;
@@ -1113,7 +1116,8 @@ __global__ void __launch_bounds__(GTPB, TK ? 5 : 4) k_group(const __grid_constan
         const float F1 = s_F[1];
         const int (*tab1)[TABW] = s_tab + S1.q0;
 #define TNQ_L(nv, k) stage_last_pd<nv, k>(S1, t, cur, P.out, s_ptr, F1, tab1, s_out_hi, s_out_base, out_lo, &tmax)
-        switch (S1.n_var * 2 + (S1.n_in > S1.n_var ? 1 : 0)) {
+        const int nv1 = S1.n_var - S1.n_tc;
+        switch (nv1 * 2 + (S1.n_in > nv1 ? 1 : 0)) {
           case 2: TNQ_L(1, false); break;
           case 3: TNQ_L(1, true); break;
           case 4: TNQ_L(2, false); break;
@@ -1737,6 +1741,38 @@ static GParams group_gparams(const tnq_plan& P, const Layout& L, const FusedGrou
     for (int j = 1; ok && j < S1.n_in; ++j) ok = S1.src[j] >= 0;
     G.lean2 = ok ? 1 : 0;
   }
+  // stages run by the prefetching loop of k_group<1> / <2> (stage 0, and
+  // stage 1 of a two-stage chain): varying inputs that hold thread bits only
+  // (local bits below GTB, the same for all entries of a thread) move behind
+  // the others; the loop multiplies their per-thread pairs into its constant
+  // pair once instead of loading them per entry
+  auto move_thread_const = [&](GSt& S, int first) {
+    auto tc = [&](int j) {
+      if (S.src[j] < 0) return false;
+      bool any = false;
+      for (int b = 0; b < S.nbits; ++b) {
+        if (!S.cstride[j][b]) continue;
+        if (b >= GTB) return false;
+        any = true;
+      }
+      return any;
+    };
+    std::vector<int> keep, moved;
+    for (int j = 0; j < S.n_var; ++j) (j >= first && tc(j) ? moved : keep).push_back(j);
+    if (moved.empty() || keep.empty()) return;
+    std::vector<int> perm(keep);
+    perm.insert(perm.end(), moved.begin(), moved.end());
+    GSt T = S;
+    for (int k = 0; k < S.n_var; ++k) {
+      T.src[k] = S.src[perm[k]];
+      T.ustride[k] = S.ustride[perm[k]];
+      for (int b = 0; b < GL_MAX; ++b) T.cstride[k][b] = S.cstride[perm[k]][b];
+    }
+    T.n_tc = (int)moved.size();
+    S = T;
+  };
+  if (G.tail || G.lean2) move_thread_const(G.st[0], 0);
+  if (G.lean2) move_thread_const(G.st[1], 1);
   const auto& last = sv[G.n_st - 1];
   for (size_t b = 0; b < last.size(); ++b) {
     const int p = index_in(o.vars, last[b]);
@@ -2071,6 +2107,11 @@ static std::string validate_config(const tnq_plan& P, int mode, int B) {
         if (j >= S.n_var)
           for (int b = 0; b < S.nbits; ++b)
             if (S.cstride[j][b]) return "group " + std::to_string(gi) + ": constant input varies";
+        if (j < S.n_var && j >= S.n_var - S.n_tc) {  // a per-thread pair: thread bits only, from memory
+          if (S.src[j] < 0 || S.n_tc >= S.n_var) return "group " + std::to_string(gi) + ": per-thread pair";
+          for (int b = GTB; b < S.nbits; ++b)
+            if (S.cstride[j][b]) return "group " + std::to_string(gi) + ": per-thread pair varies per entry";
+        }
         if (j >= S.n_var && S.kinv) {  // a per-item constant pair: read from memory at the item's base
           if (S.src[j] < 0) return "group " + std::to_string(gi) + ": per-item constant from the chain";
           for (int i = 0; i < G.n_h; ++i)
@@ -2590,7 +2631,7 @@ int tnq_internal_group_text(const tnq_plan* plan, int mode, uint32_t batch, char
     for (int st = 0; st < G.n_st; ++st) {
       const GSt& S = G.st[st];
       out += "  stage " + std::to_string(st) + " nbits " + std::to_string(S.nbits) + " n_in " + std::to_string(S.n_in) +
-             " n_var " + std::to_string(S.n_var) + " pd " + std::to_string(S.pd) + "\n";
+             " n_var " + std::to_string(S.n_var) + " n_tc " + std::to_string(S.n_tc) + " pd " + std::to_string(S.pd) + "\n";
       for (int j = 0; j < S.n_in; ++j) {
         out += "    in src " + std::to_string(S.src[j]) + " ustride " + std::to_string(S.ustride[j]) + " local:";
         for (int b = 0; b < S.nbits; ++b) out += S.cstride[j][b] ? " " + std::to_string(S.cstride[j][b]) : " .";
