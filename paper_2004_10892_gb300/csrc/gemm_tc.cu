@@ -8,7 +8,9 @@
 // warps read the other accumulator with tcgen05.ld and write the previous
 // tile. Every wait is bounded by %globaltimer: on a timeout the kernel
 // records a status, waits (bounded) for the copies and MMAs it issued, frees
-// its tensor memory and returns.
+// its tensor memory and returns. A second form (k_gemm_tc_fa) reads the A
+// operand straight from its complex64 tensor: producer warps split it into
+// hi/lo in shared memory, so A needs no packed copy.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
