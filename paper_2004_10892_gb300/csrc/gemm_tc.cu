@@ -343,10 +343,11 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_gemm_tc(const GemmArgs a) {
       const int ct = (int)(tile % a.row_tiles_b);
       const int rt = (int)((tile / a.row_tiles_b) % a.row_tiles_a);
       const long long b = tile / ((long long)a.row_tiles_b * a.row_tiles_a);
-      const char* A_hi = (const char*)a.a_hi + (size_t)(b * a.row_tiles_a + rt) * a.k_tiles * tb;
-      const char* A_lo = (const char*)a.a_lo + (size_t)(b * a.row_tiles_a + rt) * a.k_tiles * tb;
-      const char* B_hi = (const char*)a.b_hi + (size_t)(b * a.row_tiles_b + ct) * a.k_tiles * tb;
-      const char* B_lo = (const char*)a.b_lo + (size_t)(b * a.row_tiles_b + ct) * a.k_tiles * tb;
+      const long long ba = b & a.a_bmask, bb = b & a.b_bmask;
+      const char* A_hi = (const char*)a.a_hi + (size_t)(ba * a.row_tiles_a + rt) * a.k_tiles * tb;
+      const char* A_lo = (const char*)a.a_lo + (size_t)(ba * a.row_tiles_a + rt) * a.k_tiles * tb;
+      const char* B_hi = (const char*)a.b_hi + (size_t)(bb * a.row_tiles_b + ct) * a.k_tiles * tb;
+      const char* B_lo = (const char*)a.b_lo + (size_t)(bb * a.row_tiles_b + ct) * a.k_tiles * tb;
       for (int kt = 0; kt < a.k_tiles; ++kt, ++g) {
         const int s = (int)(g % N_STAGES);
         if (fills[s] > 0 && !mbar_wait(&empty_bar[s], (fills[s] - 1) & 1)) {  // the MMAs released stage s
@@ -615,8 +616,9 @@ __global__ void __launch_bounds__(GEMM_THREADS_FA, 1) k_gemm_tc_fa(const GemmArg
     for (long long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
       const int ct = (int)(tile % a.row_tiles_b);
       const long long b = tile / ((long long)a.row_tiles_b * a.row_tiles_a);
-      const char* B_hi = (const char*)a.b_hi + (size_t)(b * a.row_tiles_b + ct) * kth * HB;
-      const char* B_lo = (const char*)a.b_lo + (size_t)(b * a.row_tiles_b + ct) * kth * HB;
+      const long long bb = b & a.b_bmask;
+      const char* B_hi = (const char*)a.b_hi + (size_t)(bb * a.row_tiles_b + ct) * kth * HB;
+      const char* B_lo = (const char*)a.b_lo + (size_t)(bb * a.row_tiles_b + ct) * kth * HB;
       for (int q = 0; q < a.k_tiles; ++q, ++g) {
         const int s = (int)(g % N_STAGES);
         if (fills[s] > 0 && !mbar_wait(&empty_bar[s], (fills[s] - 1) & 1)) {
@@ -747,7 +749,7 @@ constexpr int PK_BITS = 3 * GB_BITS;
 constexpr int PK_TABS = PK_BITS / 8;   // byte tables of operand 0's offset (W bits 8q .. 8q+7)
 constexpr int PK_ITEMS = 64;           // items whose operand scales are kept in shared memory
 template <int KIND, bool HALF>
-__global__ void k_gemm_pack(const GemmBucketArgs g, int side) {
+__global__ void k_gemm_pack(const GemmBucketArgs g, int side, int pack_items) {
   __shared__ int s_nz[GB_SIDE];
   __shared__ unsigned char s_pos[GB_SIDE][PK_BITS];
   __shared__ long long s_str[GB_SIDE][PK_BITS];
@@ -763,7 +765,7 @@ __global__ void k_gemm_pack(const GemmBucketArgs g, int side) {
   const int nops = side == 0 ? g.na : g.nb;
   const int nr = side == 0 ? g.nx : g.ny;
   const long long rows = side == 0 ? g.m_pad : g.n_pad;  // complex rows
-  const long long batch = (long long)g.items << g.ns;
+  const long long batch = (long long)pack_items << g.ns;  // 1 item when the side does not depend on it
   const int kch = g.k_pad / CH;  // chunks per row (k_pad is a multiple of 64 / ES)
   const long long n = batch * rows * kch;
   constexpr int KB = HALF ? GT_KBYTES_H : GT_KBYTES;  // bytes of K per tile row
@@ -826,7 +828,8 @@ __global__ void k_gemm_pack(const GemmBucketArgs g, int side) {
     }
   __syncthreads();
   if ((side == 0 || HALF) && blockIdx.x == 0) {
-    // output exponent per item (by the A pack, or by the B pack when A is fused): sum over every operand of its exponent and scale shift
+    // output exponent per item (by the A pack, or by the B pack when A is
+    // fused): sum over every operand of its exponent and scale shift
     for (int it = threadIdx.x; it < g.items; it += blockDim.x) {
       int e = 0;
       for (int j = 0; j < g.na + g.nb; ++j) {
@@ -1004,9 +1007,18 @@ bool gemm_fused_a(const GemmBucketArgs& g) {
 void gemm_bucket_launch(const GemmBucketArgs& g, const GemmEpilogue& ep, int* status, void* stream) {
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int esize = g.kind == GEMM_BF16 ? 2 : 4;
+  // a side whose operands are all item-invariant is packed once and shared by every item
+  auto invariant = [](const GemmOperand* o, int n) {
+    for (int j = 0; j < n; ++j)
+      if (o[j].dep) return false;
+    return true;
+  };
+  const bool inv_a = g.items > 1 && invariant(g.a, g.na), inv_b = g.items > 1 && invariant(g.b, g.nb);
+  const int items_a = inv_a ? 1 : g.items, items_b = inv_b ? 1 : g.items;
   const long long batch = (long long)g.items << g.ns;
   const int ch = 16 / esize;  // K values per thread of k_gemm_pack
-  const long long na = batch * g.m_pad * (g.k_pad / ch), nb = batch * g.n_pad * (g.k_pad / ch);
+  const long long na = ((long long)items_a << g.ns) * g.m_pad * (g.k_pad / ch);
+  const long long nb = ((long long)items_b << g.ns) * g.n_pad * (g.k_pad / ch);
   const long long cap = 16ll * device_sms();  // grid-stride pack: 16 blocks of 256 threads per SM
   const int blocks_a = (int)std::max<long long>(1, std::min<long long>((na + 255) / 256, cap));
   const int blocks_b = (int)std::max<long long>(1, std::min<long long>((nb + 255) / 256, cap));
@@ -1015,11 +1027,13 @@ void gemm_bucket_launch(const GemmBucketArgs& g, const GemmEpilogue& ep, int* st
   a.row_tiles_a = g.m_pad / GT_ROWS;
   a.row_tiles_b = 2 * g.n_pad / GT_ROWS;
   a.batch = (int)batch;
+  a.a_bmask = inv_a ? (1ll << g.ns) - 1 : -1ll;
+  a.b_bmask = inv_b ? (1ll << g.ns) - 1 : -1ll;
   a.status = status;
   a.out_c = nullptr;
   a.ep = ep;
   if (gemm_fused_a(g)) {
-    k_gemm_pack<GEMM_BF16, true><<<blocks_b, 256, 0, s>>>(g, 1);
+    k_gemm_pack<GEMM_BF16, true><<<blocks_b, 256, 0, s>>>(g, 1, items_b);
     a.b_hi = g.b_hi;
     a.b_lo = g.b_lo;
     a.k_tiles = g.k_pad / 32;  // K steps of 32 complex values
@@ -1037,11 +1051,11 @@ void gemm_bucket_launch(const GemmBucketArgs& g, const GemmEpilogue& ep, int* st
     return;
   }
   if (g.kind == GEMM_BF16) {
-    k_gemm_pack<GEMM_BF16, false><<<blocks_a, 256, 0, s>>>(g, 0);
-    k_gemm_pack<GEMM_BF16, false><<<blocks_b, 256, 0, s>>>(g, 1);
+    k_gemm_pack<GEMM_BF16, false><<<blocks_a, 256, 0, s>>>(g, 0, items_a);
+    k_gemm_pack<GEMM_BF16, false><<<blocks_b, 256, 0, s>>>(g, 1, items_b);
   } else {
-    k_gemm_pack<GEMM_TF32, false><<<blocks_a, 256, 0, s>>>(g, 0);
-    k_gemm_pack<GEMM_TF32, false><<<blocks_b, 256, 0, s>>>(g, 1);
+    k_gemm_pack<GEMM_TF32, false><<<blocks_a, 256, 0, s>>>(g, 0, items_a);
+    k_gemm_pack<GEMM_TF32, false><<<blocks_b, 256, 0, s>>>(g, 1, items_b);
   }
   a.a_hi = g.a_hi;
   a.a_lo = g.a_lo;
@@ -1114,6 +1128,7 @@ extern "C" int tnq_internal_gemm_selftest(int kind, int batch, int M, int N, int
   }
   GemmArgs g;
   std::memset(&g, 0, sizeof(g));
+  g.a_bmask = g.b_bmask = -1ll;
   g.a_hi = ah;
   g.a_lo = al;
   g.b_hi = bh;

@@ -91,6 +91,9 @@ struct GemmArgs {
   int row_tiles_b;   // rows of B / 128 (columns of C / 128)
   int k_tiles;       // Kr bytes / 128
   int batch;
+  // batch index of an operand's tiles: b & mask (all ones; or 2^ns - 1 when
+  // the operand does not depend on the item, packed once for all items)
+  long long a_bmask, b_bmask;
   int* status;
   // epilogue: C written as FP32 rows x cols per batch (ldc floats per row) when
   // `out_c` is set; the bucket path supplies its own epilogue data instead
