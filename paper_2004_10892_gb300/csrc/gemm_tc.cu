@@ -748,6 +748,7 @@ __global__ void k_pack_real(const float* __restrict__ X, int rows, int K, int ba
 constexpr int PK_BITS = 3 * GB_BITS;
 constexpr int PK_TABS = PK_BITS / 8;   // byte tables of operand 0's offset (W bits 8q .. 8q+7)
 constexpr int PK_ITEMS = 64;           // items whose operand scales are kept in shared memory
+constexpr int PK_SIDE = 512;           // entries of the folded-tensor product table (rows x K values of a chunk)
 template <int KIND, bool HALF>
 __global__ void k_gemm_pack(const GemmBucketArgs g, int side, int pack_items) {
   __shared__ int s_nz[GB_SIDE];
@@ -758,6 +759,11 @@ __global__ void k_gemm_pack(const GemmBucketArgs g, int side, int pack_items) {
   __shared__ int s_kvec[GB_SIDE];          // 1: the chunk's K values are consecutive entries (vector loads)
   __shared__ long long s_tab0[PK_TABS][256];  // operand 0: offset of each value of W's byte q
   __shared__ float s_f[GB_SIDE][PK_ITEMS];    // power-of-two scale of operand j for item it
+  // the folded tensors' product (operands 1.., item-invariant) for every
+  // value of the W bits they hold (row) and every K value of a chunk
+  __shared__ float2 s_side[PK_SIDE];
+  __shared__ unsigned char s_upos[16];
+  __shared__ int s_nu, s_use_side;
   constexpr int ES = KIND == GEMM_BF16 ? 2 : 4;
   constexpr int CH = 16 / ES;
   constexpr int CHB = KIND == GEMM_BF16 ? 3 : 2;  // log2 CH
@@ -843,6 +849,57 @@ __global__ void k_gemm_pack(const GemmBucketArgs g, int side, int pack_items) {
       g.meta_e[(long long)g.out_meta * g.B + (g.out_dep ? it : 0)] = e;
     }
   }
+  // with three or more operands whose folded tensors (1..) are all
+  // item-invariant and hold few W bits: their product once per block, in a
+  // table indexed by those bits and the K value within the chunk, so that an
+  // element multiplies operand 0 by one table entry per K value
+  if (threadIdx.x == 0) {
+    unsigned long long um = 0;
+    bool ok = nops >= 3;
+    for (int j = 1; ok && j < nops; ++j) {
+      ok = !ops[j].dep;
+      for (int i = 0; i < s_nz[j]; ++i) um |= 1ull << s_pos[j][i];
+    }
+    int nu = 0;
+    for (int p = 0; p < 64 && ok; ++p)
+      if ((um >> p) & 1ull) {
+        if (nu == 16) ok = false;
+        else s_upos[nu++] = (unsigned char)p;
+      }
+    ok = ok && ((CH << nu) <= PK_SIDE);
+    s_nu = nu;
+    s_use_side = ok ? 1 : 0;
+  }
+  __syncthreads();
+  const bool use_side = s_use_side != 0;
+  if (use_side) {
+    const int nu = s_nu;
+    for (int e = threadIdx.x; e < (CH << nu); e += blockDim.x) {
+      const int row = e >> CHB, q = e & (CH - 1);
+      unsigned long long Wp = 0;
+      for (int i = 0; i < nu; ++i)
+        if ((row >> i) & 1) Wp |= 1ull << s_upos[i];
+      float sr = 1.f, si = 0.f;
+      for (int j = 1; j < nops; ++j) {
+        const GemmOperand& o = ops[j];
+        float f = 1.f;
+        if (o.meta >= 0) {
+          int m;
+          f = pack_scale(g.meta_m[(long long)o.meta * g.B], &m);
+        }
+        long long off = s_klo[j][q];
+        for (int i = 0; i < s_nz[j]; ++i)
+          if ((Wp >> s_pos[j][i]) & 1ull) off += s_str[j][i];
+        const float2 v = o.ptr[off];
+        const float vx = v.x * f, vy = v.y * f;
+        const float nr_ = sr * vx - si * vy, ni = sr * vy + si * vx;
+        sr = nr_;
+        si = ni;
+      }
+      s_side[e] = make_float2(sr, si);
+    }
+    __syncthreads();
+  }
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     // 8 consecutive threads: the 8 rows of one core matrix (one 128-byte
     // store each); then the next K chunks of the same rows (contiguous reads
@@ -864,7 +921,7 @@ __global__ void k_gemm_pack(const GemmBucketArgs g, int side, int pack_items) {
     if (row_ok && k0 < (1 << g.nk)) {
       const unsigned long long W = (unsigned long long)sidx | ((unsigned long long)r << g.ns) |
                                    ((unsigned long long)(k0 >> CHB) << (g.ns + nr));
-      for (int j = 0; j < nops; ++j) {
+      for (int j = 0; j < (use_side ? 1 : nops); ++j) {
         const GemmOperand& o = ops[j];
         float f = 1.f;
         if (f_tab) {
@@ -913,6 +970,18 @@ __global__ void k_gemm_pack(const GemmBucketArgs g, int side, int pack_items) {
             re[q] = nre;
             im[q] = nim;
           }
+        }
+      }
+      if (use_side) {  // times the folded tensors' product (K values past the end stay 0)
+        int row = 0;
+        for (int i = 0; i < s_nu; ++i) row |= (int)((W >> s_upos[i]) & 1ull) << i;
+        const float2* sv = s_side + (row << CHB);
+#pragma unroll
+        for (int q = 0; q < CH; ++q) {
+          const float2 v = sv[q];
+          const float nre = re[q] * v.x - im[q] * v.y, nim = re[q] * v.y + im[q] * v.x;
+          re[q] = nre;
+          im[q] = nim;
         }
       }
     }
